@@ -1,0 +1,212 @@
+"""Seeded synthetic curve generators (inputs only).
+
+This module produces the curves that the CUDA library and the CPU oracle are
+both fed with.  It holds none of the alignment method's arithmetic: no
+correlation, no FFT, no Kabsch step and no spline.  Curves come from the
+Fourier-series family r(phi) = 1 + sum_k a_k cos(k phi + phi_k) with
+a_k ~ N(0, (0.15/k)^2) and phi_k ~ U(0, 2 pi), a stand-in for the paper's
+synthetic and cell-boundary test curves (Sec. 2, validation experiments),
+which are not available.
+
+Two workloads:
+
+* ``aligned_pairs``: pairs that are already uniform in arc length, centred and
+  of unit length (the inputs of the alignment step alone).  Curve 2 is curve 1
+  rotated by theta_g, cyclically relabelled by s_g, optionally with Gaussian
+  noise, then re-centred and re-scaled.  With z2[k] = e^{i theta_g}
+  z1[(k - s_g) mod N] the optimal alignment is shift s_g and counter-clockwise
+  angle -theta_g.
+* ``raw_pairs``: pairs given as ragged, non-uniformly sampled point lists (the
+  inputs of the arc-length resampling step).  Node parameters are jittered by
+  up to +-40% of the mean spacing and every curve has its own node count.
+
+Arc-length-uniform sampling here is done by dense sampling plus linear
+interpolation of the cumulative chord length -- deliberately a different
+construction from the method's cubic-spline resampling.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+TWO_PI = 2.0 * np.pi
+
+
+@dataclass
+class Harmonics:
+    """Coefficients of r(phi) = 1 + scale * sum_k a_k cos(k phi + phi_k)."""
+
+    a: np.ndarray
+    ph: np.ndarray
+    scale: float = 1.0
+
+    def radius(self, phi: np.ndarray) -> np.ndarray:
+        k = np.arange(1, self.a.size + 1)
+        pert = np.cos(np.multiply.outer(phi, k) + self.ph) @ self.a
+        return 1.0 + self.scale * pert
+
+
+def random_harmonics(rng: np.random.Generator, n_harm: int, sigma0: float = 0.15,
+                     min_radius: float = 0.25) -> Harmonics:
+    """Draw a_k ~ N(0, (sigma0/k)^2), phi_k ~ U(0, 2 pi).
+
+    If the perturbation would bring r below ``min_radius`` anywhere, it is
+    scaled down so that the curve stays star-shaped and simple.
+    """
+    k = np.arange(1, n_harm + 1)
+    h = Harmonics(a=rng.normal(0.0, sigma0 / k), ph=rng.uniform(0.0, TWO_PI, n_harm))
+    phi = np.linspace(0.0, TWO_PI, 4096, endpoint=False)
+    pert_min = float(np.min(h.radius(phi) - 1.0))
+    if 1.0 + pert_min < min_radius:
+        h.scale = (1.0 - min_radius) / (-pert_min)
+    return h
+
+
+def _normalise(z: np.ndarray) -> np.ndarray:
+    """Input preparation: subtract the node mean, divide by the closed-polygon
+    perimeter (so that a generated pair starts centred and of unit length)."""
+    z = z - z.mean()
+    per = np.abs(np.roll(z, -1) - z).sum()
+    return z / per
+
+
+def uniform_arclength_nodes(h: Harmonics, N: int, oversample: int = 64,
+                            phase: float = 0.0) -> np.ndarray:
+    """N nodes of the polar curve, equally spaced in arc length.
+
+    The curve is sampled at oversample*N equally spaced angles starting at
+    ``phase``; the cumulative chord length of that dense polygon is inverted
+    by linear interpolation.  The result is centred and of unit perimeter.
+    """
+    M = oversample * N
+    phi = phase + TWO_PI * np.arange(M + 1) / M
+    w = h.radius(phi) * np.exp(1j * phi)
+    seg = np.abs(np.diff(w))
+    cum = np.concatenate([[0.0], np.cumsum(seg)])
+    target = cum[-1] * np.arange(N) / N
+    x = np.interp(target, cum, w.real)
+    y = np.interp(target, cum, w.imag)
+    return _normalise(x + 1j * y)
+
+
+@dataclass
+class AlignedPairs:
+    z1: np.ndarray          # complex128 [P, N]
+    z2: np.ndarray          # complex128 [P, N]
+    shift_true: np.ndarray  # int32 [P]   optimal shift of the noise-free pair
+    theta_true: np.ndarray  # float64 [P] optimal CCW angle (= -theta_g) in (-pi, pi]
+
+
+def aligned_pairs(seed: int, P: int = 64, N: int = 256, n_harm: int = 8,
+                  noise: float = 1e-3) -> AlignedPairs:
+    """Pairs already uniform in arc length, centred and of unit length.
+
+    Default sizes are the 64-pair, N = 256 parity workload.  ``noise`` is the
+    standard deviation of the i.i.d. Gaussian noise added to each coordinate of
+    curve 2 before it is re-centred and re-scaled (0 gives exact copies).
+    """
+    rng = np.random.default_rng(seed)
+    z1 = np.empty((P, N), np.complex128)
+    z2 = np.empty((P, N), np.complex128)
+    s_true = np.empty(P, np.int32)
+    th_true = np.empty(P, np.float64)
+    for p in range(P):
+        h = random_harmonics(rng, n_harm)
+        a = uniform_arclength_nodes(h, N)
+        th_g = rng.uniform(0.0, TWO_PI)
+        s_g = int(rng.integers(0, N))
+        b = np.exp(1j * th_g) * np.roll(a, s_g)  # b[k] = e^{i th} a[(k - s_g) mod N]
+        if noise > 0.0:
+            b = b + noise * (rng.standard_normal(N) + 1j * rng.standard_normal(N))
+            b = _normalise(b)
+        z1[p] = a
+        z2[p] = b
+        s_true[p] = s_g
+        th_true[p] = np.angle(np.exp(-1j * th_g))
+    return AlignedPairs(z1, z2, s_true, th_true)
+
+
+@dataclass
+class RawPairs:
+    pts: np.ndarray      # complex128 [sum n]: curves 0..P-1 are the first members,
+                         # curves P..2P-1 the second members of the pairs
+    offsets: np.ndarray  # int64 [2P + 1]  CSR offsets into pts
+    theta_g: np.ndarray  # float64 [P] rotation applied to the second member
+
+    @property
+    def n_curves(self) -> int:
+        return self.offsets.size - 1
+
+
+def _jittered_polar(rng: np.random.Generator, h: Harmonics, n: int, phase: float,
+                    jitter: float) -> np.ndarray:
+    delta = rng.uniform(-jitter, jitter, n)
+    phi = phase + TWO_PI * (np.arange(n) + delta) / n
+    return h.radius(phi) * np.exp(1j * phi)
+
+
+def raw_pairs(seed: int, P: int = 4096, n_min: int = 500, n_max: int = 2000,
+              max_harm: int = 16, jitter: float = 0.4, noise: float = 1e-3,
+              transform: bool = True) -> RawPairs:
+    """Ragged, non-uniformly sampled pairs (inputs of the resampling step).
+
+    Defaults are the 4096-pair workload: n_in ~ U{n_min..n_max} per curve, node
+    parameters phi_l = phase + 2 pi (l + delta_l)/n_in with delta_l ~
+    U(-jitter, jitter), harmonic count ~ U{1..max_harm}.  The second member is
+    the same shape rotated by theta_g ~ U(0, 2 pi), with its parameter origin
+    offset by U(0, 2 pi), its own node count and jitter, and Gaussian noise of
+    standard deviation ``noise`` per coordinate.  With ``transform`` each curve
+    is also given a random scale in [0.5, 2] and offset in [-2, 2]^2, which
+    the resampling step's centring and scaling must remove.
+    """
+    rng = np.random.default_rng(seed)
+    first, second, th = [], [], np.empty(P)
+    for p in range(P):
+        h = random_harmonics(rng, int(rng.integers(1, max_harm + 1)))
+        n1 = int(rng.integers(n_min, n_max + 1))
+        n2 = int(rng.integers(n_min, n_max + 1))
+        c1 = _jittered_polar(rng, h, n1, 0.0, jitter)
+        th_g = rng.uniform(0.0, TWO_PI)
+        c2 = np.exp(1j * th_g) * _jittered_polar(rng, h, n2, rng.uniform(0.0, TWO_PI), jitter)
+        if noise > 0.0:
+            c2 = c2 + noise * (rng.standard_normal(n2) + 1j * rng.standard_normal(n2))
+        if transform:
+            c1 = rng.uniform(0.5, 2.0) * c1 + complex(*rng.uniform(-2.0, 2.0, 2))
+            c2 = rng.uniform(0.5, 2.0) * c2 + complex(*rng.uniform(-2.0, 2.0, 2))
+        first.append(c1)
+        second.append(c2)
+        th[p] = th_g
+    curves = first + second
+    counts = np.array([c.size for c in curves], np.int64)
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    pts = np.concatenate(curves).astype(np.complex128)
+    return RawPairs(pts, offsets, th)
+
+
+def raw_curves(seed: int, C: int, n_min: int, n_max: int, max_harm: int = 16,
+               jitter: float = 0.4) -> tuple[np.ndarray, np.ndarray]:
+    """C independent ragged curves (no pairing), returned as (pts, offsets)."""
+    rng = np.random.default_rng(seed)
+    curves = []
+    for _ in range(C):
+        h = random_harmonics(rng, int(rng.integers(1, max_harm + 1)))
+        n = int(rng.integers(n_min, n_max + 1))
+        c = _jittered_polar(rng, h, n, rng.uniform(0.0, TWO_PI), jitter)
+        curves.append(rng.uniform(0.5, 2.0) * c + complex(*rng.uniform(-2.0, 2.0, 2)))
+    counts = np.array([c.size for c in curves], np.int64)
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return np.concatenate(curves).astype(np.complex128), offsets
+
+
+def template_pair(h: Harmonics, N: int, start: float = 0.25,
+                  rotation: float = np.pi / 3) -> tuple[np.ndarray, np.ndarray]:
+    """The paper's validation template (Sec. 2): the reference curve with its
+    starting point moved from 0 to ``start`` (a fraction of the length) and
+    rotated counter-clockwise by ``rotation``.  Both curves share the same
+    uniform arc-length parametrisation.  With N*start an integer q, the
+    template is z2[k] = e^{i rotation} z1[(k + q) mod N]."""
+    z1 = uniform_arclength_nodes(h, N)
+    q = int(round(start * N))
+    z2 = np.exp(1j * rotation) * np.roll(z1, -q)
+    return z1, z2
