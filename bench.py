@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Benchmark: aligned curve pairs/s at N = 1024 on one GB300 (per rank).
+
+Workload (one "step"): 4096 curve pairs given as raw, non-uniformly sampled
+point lists (N_in ~ U{500..2000} nodes per curve, node parameters jittered by
++-40% of the mean spacing, Fourier-series shapes with up to 16 harmonics);
+both curves of every pair are resampled on the GPU to N = 1024 nodes uniform
+in arc length (fa_resample_arclength), then every pair is aligned over all
+cyclic shifts and rotations with the FFT method (fa_align_pairs, FA_FFT),
+all in FP64.  Inputs are resident in HBM when the timed region starts; the
+raw nodes (~164 MB) exceed the 129 MB L2, so no extra flush is needed.
+
+The JSON line also carries: the direct O(N^2) GPU baseline on the same
+curves, the roofline of the dominant kernel (FP64 pipe: algorithmic FP64
+flops per launch / CUDA-event time, against this GPU's FP64 FMA peak measured
+in the same run), the end-to-end number through fa_align_curves_host with
+pinned host buffers (copies inside the timed region), SM clocks sampled during
+the timed region, and the CPU oracle timed on a bounded sample.
+
+--impl reference times the CPU oracle (the plain O(N^2) Kabsch search plus the
+periodic-spline resampling, FP64, OpenMP over pairs) on a bounded sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+P_PAIRS = 4096
+N_NODES = 1024
+N_MIN, N_MAX = 500, 2000
+SEED = 1002
+METRIC = "aligned curve pairs/s at N=1024 (FFT vs direct O(N²), 1 GB300); roofline fraction"
+WORKLOAD = ("4096 pairs of raw curves (N_in ~ U{500..2000}, +-40% node jitter, <=16 harmonics), "
+            "GPU arc-length resampling to N=1024 + FFT alignment over all shifts, FP64")
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+# ----------------------------------------------------- algorithmic counts ---
+def fft_flops(logn: int) -> int:
+    """FP64 flops (FMA = 2) of one forward transform in the kernel's algorithm:
+    an optional radix-2 stage (4 real adds per butterfly), then radix-4
+    Stockham stages: 16 adds per butterfly, plus 3 complex twiddle products
+    (2 mul + 2 fma = 6 flops each) in every stage after the first."""
+    N = 1 << logn
+    q = N // 4
+    fl = 0
+    stages4 = logn // 2
+    first_twiddled = False
+    if logn & 1:
+        fl += (N // 2) * 4
+        first_twiddled = True
+    for i in range(stages4):
+        fl += q * (16 + (18 if (i > 0 or first_twiddled) else 0))
+    return fl
+
+
+def align_fft_flops_per_pair(logn: int) -> int:
+    N = 1 << logn
+    # 3 transforms; spectrum product 6/bin; |c|^2 3/shift; c(s*) 8/node; energy 12/node
+    return 3 * fft_flops(logn) + 6 * N + 3 * N + 8 * N + 12 * N
+
+
+def resample_flops(n_in: np.ndarray, N: int) -> int:
+    """FP64 flops of fa_resample_arclength (sqrt and division count 1):
+    48 per input node (chords, knots, spline equations, Thomas elimination,
+    two backward sweeps) and 42 per output node (evaluation, centring,
+    perimeter, scaling)."""
+    return int(48 * int(n_in.sum()) + 42 * N * n_in.size)
+
+
+def direct_flops_per_pair(N: int) -> int:
+    return 8 * N * N + 3 * N + 12 * N
+
+
+# ------------------------------------------------------------- clocks ------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- helpers ----
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_workload(rank: int, P: int = P_PAIRS):
+    from paper_2501_17779_gb300 import synth
+
+    return synth.raw_pairs(SEED + 1000 * rank, P=P, n_min=N_MIN, n_max=N_MAX)
+
+
+def oracle_sample(rp, n_pairs: int, N: int, nthreads: int):
+    """Run the oracle (resampling + exhaustive alignment) on the first
+    n_pairs pairs of a workload; returns seconds of wall time."""
+    import oracle
+
+    P = rp.offsets.size // 2
+    idx = list(range(n_pairs)) + list(range(P, P + n_pairs))
+    curves = [rp.pts[rp.offsets[i]:rp.offsets[i + 1]] for i in idx]
+    offs = np.concatenate([[0], np.cumsum([c.size for c in curves])]).astype(np.int64)
+    pts = np.concatenate(curves)
+    t0 = time.perf_counter()
+    z, st = oracle.resample(pts, offs, N, nthreads=nthreads)
+    oracle.align_pairs(z[:n_pairs], z[n_pairs:], nthreads=nthreads)
+    return time.perf_counter() - t0
+
+
+# ------------------------------------------------------------ reference ----
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    nthreads = os.cpu_count() or 1
+    rp = make_workload(0, P=max(args.ref_pairs, 8))
+    for _ in range(args.warmup):
+        oracle_sample(rp, min(8, args.ref_pairs), N_NODES, nthreads)
+    times = [oracle_sample(rp, args.ref_pairs, N_NODES, nthreads) for _ in range(args.steps)]
+    tot = sum(times)
+    value = args.ref_pairs * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs": P_PAIRS, "N": N_NODES,
+                   "sample_pairs_per_step": args.ref_pairs},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": nthreads, "kind": "oracle",
+                         "sample": f"{args.ref_pairs} pairs of the 4096-pair workload per step "
+                                   "(resampling + O(N^2) Kabsch search)"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU ------
+def run_gpu(args):
+    import torch
+
+    from paper_2501_17779_gb300 import _lib, api, build as pbuild
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    pbuild.build()
+    L = _lib.load()
+    h = api.handle(local)
+
+    rp = make_workload(rank)
+    P, N = P_PAIRS, N_NODES
+    C = 2 * P
+    n_in = np.diff(rp.offsets)
+    pts = torch.from_numpy(rp.pts).to(dev)
+    offs = torch.from_numpy(rp.offsets).to(dev)
+    n_pts = pts.numel()
+    z = torch.empty((C, N), dtype=torch.complex128, device=dev)
+    rst = torch.empty(C, dtype=torch.int8, device=dev)
+    ws_bytes = int(L.fa_resample_workspace_size(C, n_pts, N, _lib.CENTER | _lib.UNIT_LENGTH))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    shift = torch.empty(P, dtype=torch.int32, device=dev)
+    theta = torch.empty(P, dtype=torch.float64, device=dev)
+    energy = torch.empty(P, dtype=torch.float64, device=dev)
+    ast = torch.empty(P, dtype=torch.int8, device=dev)
+    stream = torch.cuda.Stream(dev)
+    sptr = stream.cuda_stream
+    z1p = z.data_ptr()
+    z2p = z1p + P * N * 16
+    flags = _lib.CENTER | _lib.UNIT_LENGTH
+
+    def resample():
+        _lib.check(L.fa_resample_arclength(h, pts.data_ptr(), offs.data_ptr(), C, n_pts, N, flags,
+                                           z.data_ptr(), rst.data_ptr(), ws.data_ptr(), ws_bytes,
+                                           sptr))
+
+    def align(method=_lib.FFT):
+        _lib.check(L.fa_align_pairs(h, z1p, z2p, P, N, _lib.Z_F64, method, _lib.PREC_FP64,
+                                    shift.data_ptr(), theta.data_ptr(), energy.data_ptr(),
+                                    ast.data_ptr(), sptr))
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up (also validates statuses once)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            resample()
+            align()
+    torch.cuda.synchronize(dev)
+    assert int((rst != 0).sum()) == 0 and int((ast != 0).sum()) == 0, "bad status in workload"
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            t_start.record(stream)
+            for k in range(K):
+                ev[k][0].record(stream)
+                resample()
+                ev[k][1].record(stream)
+                align()
+                ev[k][2].record(stream)
+            t_end.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    rs_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    al_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    if pg is not None:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * P * K / (total_ms * 1e-3)
+
+    # direct O(N^2) baseline on the same resampled curves (align step only)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        align(_lib.DIRECT)
+        e0.record(stream)
+        reps = max(1, args.direct_reps)
+        for _ in range(reps):
+            align(_lib.DIRECT)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    direct_ms = e0.elapsed_time(e1) / reps
+
+    # FP64 peak measured in this run (denominator of the roofline)
+    peak_lib = ctypes.CDLL(str(pbuild.build_probe()))
+    peak_lib.fa_probe_fp64_fma_tflops.restype = ctypes.c_double
+    peak_lib.fa_probe_fp64_fma_tflops.argtypes = [ctypes.c_int]
+    fp64_peak = float(peak_lib.fa_probe_fp64_fma_tflops(5))
+
+    # roofline of the dominant kernel
+    rs_avg = statistics.mean(rs_ms)
+    al_avg = statistics.mean(al_ms)
+    fl_rs = resample_flops(n_in, N)
+    fl_al = align_fft_flops_per_pair(10) * P
+    kernels = {
+        "resample_kernel": {"ms": rs_avg, "tflops": fl_rs / (rs_avg * 1e-3) / 1e12,
+                            "flops_per_launch": fl_rs},
+        "align_fft_kernel": {"ms": al_avg, "tflops": fl_al / (al_avg * 1e-3) / 1e12,
+                             "flops_per_launch": fl_al},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    roof = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["tflops"], "peak": fp64_peak,
+            "unit": "TFLOP/s", "frac": kernels[dom]["tflops"] / fp64_peak,
+            "traffic": args.traffic, "peak_kind": "FP64 FMA throughput measured in this run "
+            f"(nominal {FP64_NOMINAL_TFLOPS})", "of": "measured"}
+
+    # end to end through the C ABI with pinned host buffers
+    pts_h = torch.from_numpy(rp.pts).pin_memory()
+    offs_h = torch.from_numpy(rp.offsets).pin_memory()
+    outs_h = (torch.empty(P, dtype=torch.int32).pin_memory(),
+              torch.empty(P, dtype=torch.float64).pin_memory(),
+              torch.empty(P, dtype=torch.float64).pin_memory(),
+              torch.empty(P, dtype=torch.int8).pin_memory())
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            api.align_curves_host(pts_h, offs_h, N, out=outs_h, device=local)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            api.align_curves_host(pts_h, offs_h, N, out=outs_h, device=local)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    if pg is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+
+            oracle.build()
+            nthreads = os.cpu_count() or 1
+            secs = oracle_sample(rp, args.cpu_pairs, N, nthreads)
+            cpu = {"value": args.cpu_pairs / secs, "unit": "pairs/s", "cores": nthreads,
+                   "kind": "oracle", "sample": f"first {args.cpu_pairs} of the 4096 pairs "
+                   "(resampling + O(N^2) Kabsch search), one pass, "
+                   f"{secs * nthreads:.1f} core-seconds"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs": P, "N": N, "curves": C,
+                       "input_nodes": int(n_in.sum()), "l2": "inputs larger than L2 "
+                       f"({rp.pts.nbytes / 1e6:.0f} MB raw nodes), no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "kernels": kernels,
+            "direct": {"align_ms": direct_ms, "pairs_per_s": P / (direct_ms * 1e-3),
+                       "fft_align_speedup": direct_ms / al_avg,
+                       "end_to_end_speedup": (rs_avg + direct_ms) / (rs_avg + al_avg),
+                       "direct_tflops": direct_flops_per_pair(N) * P / (direct_ms * 1e-3) / 1e12},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * P / (e2e_ms * 1e-3), "unit": "pairs/s",
+                    "h2d_bytes_per_step": int(rp.pts.nbytes + rp.offsets.nbytes),
+                    "d2h_bytes_per_step": int(P * (4 + 8 + 8 + 1)), "ms_per_step": e2e_ms},
+            "gpu_launches": 2 * K,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-pairs", type=int, default=4096)
+    ap.add_argument("--ref-pairs", type=int, default=512)
+    ap.add_argument("--direct-reps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * fftalign.h -- C ABI of libfftalign.so: GB300 (sm_103a) kernels for the
+ * O(N log N) FFT-based rigid alignment of closed planar curves
+ * (Dogan, Bernal & Hagwood, "FFT-based Alignment of 2d Closed Curves with
+ * Application to Elastic Shape Analysis", arXiv 2501.17779).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Curves.  A curve is a list of n DISTINCT nodes p_0..p_{n-1} in counter-
+ *   clockwise order; closure is implicit (the paper lists N points with first
+ *   = last, Sec. 2, i.e. N-1 distinct nodes).  Points are interleaved doubles
+ *   (x0, y0, x1, y1, ...) -- numpy/torch complex128 layout -- or, where a
+ *   function says so, interleaved floats (complex64 layout).
+ * Shift.  shift s in [0, N) is the cyclic start point t0 = s/N of Eq. energy:
+ *   curve 2 is read at node k+s (mod N).  (The paper's m = s+1, t0 = t_m.)
+ * Angle.  theta is the COUNTER-clockwise angle of the optimal rotation applied
+ *   to curve 2, in (-pi, pi]: e^{i theta} z2[(k+s) mod N] best matches z1[k].
+ *   The paper's R(theta) (Sec. 2) is clockwise, so its theta is -theta here.
+ * Energy.  E = h sum_k |z1[k] - e^{i theta} z2[(k+s) mod N]|^2, h = 1/N
+ *   (Eq. disc-energy, uniform trapezoid rule over the N distinct nodes).
+ * Memory.  Every array argument is a DEVICE pointer owned by the caller unless
+ *   the function says otherwise.  Calls are asynchronous on `stream` (a
+ *   cudaStream_t passed as void*; NULL is the legacy default stream) and
+ *   return once the work is enqueued.  The library keeps no state outside the
+ *   handle; a handle is tied to one device.
+ * Errors.  Entry points return FA_OK (0) or a negative FA_ERR_* code and
+ *   never abort or trap.  fa_last_error() gives a message for the calling
+ *   thread's last failure.  Problems with one item's DATA never fail a call:
+ *   they set that item's status byte and write NaN outputs for it.
+ */
+#ifndef FFTALIGN_H
+#define FFTALIGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fa_handle fa_handle;
+
+/* return codes */
+#define FA_OK 0
+#define FA_ERR_INVALID_ARG (-1) /* null pointer, negative count, bad enum      */
+#define FA_ERR_UNSUPPORTED (-2) /* size outside the supported set              */
+#define FA_ERR_CUDA (-3)        /* CUDA runtime error (message in fa_last_error) */
+#define FA_ERR_WORKSPACE (-4)   /* caller workspace smaller than required      */
+
+/* per-item status bytes */
+#define FA_STATUS_OK 0
+#define FA_STATUS_DEGENERATE 1 /* fewer than 4 nodes, a zero-length segment,
+                                  zero perimeter                               */
+#define FA_STATUS_NONFINITE 2  /* a NaN or Inf coordinate in the input        */
+
+/* resampling flags */
+#define FA_CENTER 1      /* subtract the mean of the N resampled nodes         */
+#define FA_UNIT_LENGTH 2 /* divide by the closed-polygon perimeter of the nodes */
+#define FA_STORE_FP32 4  /* write complex64 (float2) instead of complex128     */
+
+/* storage type of aligned curves */
+#define FA_Z_F64 0 /* complex128: interleaved doubles */
+#define FA_Z_F32 1 /* complex64: interleaved floats (widened to FP64 on load) */
+
+/* alignment method */
+#define FA_FFT 0    /* Algorithm 2 with the convolution theorem: O(N log N)   */
+#define FA_DIRECT 1 /* every shift by its O(N) definition: O(N^2) baseline    */
+
+/* arithmetic of the shift search */
+#define FA_PREC_FP64 0 /* every step in FP64                                   */
+
+/* Create a handle bound to CUDA device `device` (its twiddle tables are built
+ * here, synchronously).  *h receives the handle.  Not thread-safe with
+ * respect to the same handle being destroyed concurrently. */
+int fa_create(fa_handle** h, int device);
+
+/* Release a handle and the device memory it owns.  Waits for nothing: the
+ * caller must make sure no work that uses the handle is still in flight. */
+int fa_destroy(fa_handle* h);
+
+/* Message for the calling thread's last non-zero return code (static
+ * storage, thread-local; "" if none). */
+const char* fa_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int fa_version(void);
+
+/*
+ * Arc-length resampling (Sec. 2: Eq. arc-length-param, then cubic-spline
+ * interpolation at uniform parameters t_k = k/N_out).
+ *
+ * For each of C curves given in CSR form -- nodes pts[offsets[i] ..
+ * offsets[i+1]) -- the knot of node l is its cumulative chord length divided
+ * by the closed-polygon perimeter (u_0 = 0, u_n = 1 closing the curve), a
+ * periodic C2 cubic spline is fitted through (u_l, p_l) for x and y, and it
+ * is evaluated at t_k = k/N_out, k = 0..N_out-1.  With FA_CENTER the node
+ * mean of the N_out outputs is subtracted; with FA_UNIT_LENGTH the outputs
+ * are divided by their closed-polygon perimeter (applied after centring).
+ * An explicit closing duplicate (last node == first node) is ignored.
+ *
+ *   pts        double[2*n_pts]  interleaved x,y of all curves (device)
+ *   offsets    int64[C+1]       CSR offsets, non-decreasing, offsets[C] <= n_pts (device)
+ *   C          number of curves (>= 0)
+ *   n_pts      length of pts in points (>= offsets[C]); sizes the workspace
+ *   N_out      nodes per resampled curve, in [4, 1<<20]
+ *   flags      FA_CENTER | FA_UNIT_LENGTH | FA_STORE_FP32
+ *   z_out      [C][N_out] complex128, or complex64 with FA_STORE_FP32 (device)
+ *   status     int8[C] per-curve status (device): FA_STATUS_OK, _DEGENERATE
+ *              (fewer than 4 distinct nodes, a repeated node, zero perimeter)
+ *              or _NONFINITE; the curve's outputs are NaN unless OK
+ *   workspace  device scratch of at least fa_resample_workspace_size() bytes,
+ *              256-byte aligned, or NULL to let the handle provide it (the
+ *              handle's buffer then grows with cudaMalloc when needed, and
+ *              calls on different streams sharing one handle must not overlap)
+ */
+size_t fa_resample_workspace_size(int64_t C, int64_t n_pts, int32_t N_out, int32_t flags);
+int fa_resample_arclength(fa_handle* h, const double* pts, const int64_t* offsets, int64_t C,
+                          int64_t n_pts, int32_t N_out, int32_t flags, void* z_out,
+                          int8_t* status, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Rigid alignment of P pairs (Algorithm 2; Algorithm 1 in closed form).
+ *
+ * Pair p is z1[p][0..N) and z2[p][0..N), both assumed centred and of unit
+ * length (Sec. 2).  For every shift s the optimal rotation has the closed form
+ * theta(s) = arg c(s) with the cyclic cross-correlation
+ *     c(s) = sum_k z1[k] conj(z2[(k+s) mod N]),
+ * the complex form of A(t_m) in Eq. A-mtx (Re c = A11 + A22, Im c = A21 - A12),
+ * and max over R of tr(R A^T) = |c(s)|, so the best shift maximises |c(s)|.
+ * FA_FFT evaluates c for all s with three FFTs (forward transforms of z1 and
+ * z2, then c = DFT(Z1 * conj(Z2)) / N -- the convolution theorem of Sec. 2);
+ * FA_DIRECT evaluates the O(N) sum for every s (the O(N^2) search the paper
+ * compares against).  Exact ties go to the smallest s.  At the winning shift
+ * c(s*) is recomputed by its O(N) sum, theta = atan2(Im c, Re c) and the
+ * energy is evaluated directly from its definition (no cancellation).
+ *
+ *   z1, z2   [P][N] complex128 (FA_Z_F64) or complex64 (FA_Z_F32) (device)
+ *   P        number of pairs (>= 0)
+ *   N        nodes per curve: a power of two in [4, 4096] for FA_FFT,
+ *            any value in [1, 4096] for FA_DIRECT
+ *   ztype    FA_Z_F64 | FA_Z_F32
+ *   method   FA_FFT | FA_DIRECT
+ *   prec     FA_PREC_FP64
+ *   shift    int32[P]   best shift (-1 when status != 0)
+ *   theta    double[P]  CCW angle applied to curve 2 (NaN when status != 0)
+ *   energy   double[P]  energy at the optimum (NaN when status != 0)
+ *   status   int8[P]    FA_STATUS_OK or FA_STATUS_NONFINITE
+ */
+int fa_align_pairs(fa_handle* h, const void* z1, const void* z2, int64_t P, int32_t N,
+                   int32_t ztype, int32_t method, int32_t prec, int32_t* shift, double* theta,
+                   double* energy, int8_t* status, void* stream);
+
+/*
+ * End-to-end convenience call on HOST buffers: arc-length resampling of 2P
+ * raw curves to N nodes (centred, unit length; fa_resample_arclength), then
+ * rigid alignment of curve p with curve P+p (fa_align_pairs).
+ *
+ *   pts, offsets  HOST arrays: CSR of 2P curves, offsets[0] = 0; curves
+ *                 0..P-1 are the first members of the pairs, P..2P-1 the
+ *                 second.  Pinned (page-locked) memory gives asynchronous
+ *                 copies; pageable memory works but copies synchronously.
+ *   N             resampled nodes per curve (a power of two in [4, 4096] for
+ *                 FA_FFT, [4, 4096] for FA_DIRECT)
+ *   flags         0 or FA_STORE_FP32 (the resampled curves are kept as
+ *                 complex64 between the two steps)
+ *   method, prec  as for fa_align_pairs
+ *   shift, theta, energy, status   HOST arrays of P entries; a pair whose
+ *                 curve fails resampling gets that curve's status and NaNs
+ *
+ * Uses the handle's device buffer (grown with cudaMalloc when needed), so
+ * calls sharing a handle must not run concurrently.  Returns after the
+ * results are in the host arrays (the stream is synchronised).
+ */
+int fa_align_curves_host(fa_handle* h, const double* pts, const int64_t* offsets, int64_t P,
+                         int32_t N, int32_t flags, int32_t method, int32_t prec, int32_t* shift,
+                         double* theta, double* energy, int8_t* status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTALIGN_H */

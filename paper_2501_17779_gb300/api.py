@@ -1,0 +1,171 @@
+"""Python binding of libfftalign.so: argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; PyTorch supplies
+device memory and the current CUDA stream.  Functions mirror the C ABI of
+include/fftalign.h:
+
+* ``resample_arclength``  -> fa_resample_arclength
+* ``align_pairs``         -> fa_align_pairs
+* ``align_curves_host``   -> fa_align_curves_host (host buffers in and out)
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _lib
+
+_handles: dict[int, int] = {}
+_hlock = threading.Lock()
+
+
+def handle(device: int | None = None) -> int:
+    """The process-wide library handle for a CUDA device (created on first use)."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("libfftalign needs a CUDA device; none is available")
+    dev = torch.cuda.current_device() if device is None else int(device)
+    with _hlock:
+        h = _handles.get(dev)
+        if h is None:
+            L = _lib.load()
+            hp = ctypes.c_void_p()
+            _lib.check(L.fa_create(ctypes.byref(hp), dev))
+            h = _handles[dev] = hp.value
+    return h
+
+
+def _stream_ptr(device: torch.device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _need_cuda(name: str, t: torch.Tensor, dtype=None) -> None:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def resample_workspace_size(C: int, n_pts: int, N_out: int, fp32: bool = False) -> int:
+    L = _lib.load()
+    flags = _lib.CENTER | _lib.UNIT_LENGTH | (_lib.STORE_FP32 if fp32 else 0)
+    return int(L.fa_resample_workspace_size(C, n_pts, N_out, flags))
+
+
+def resample_arclength(pts: torch.Tensor, offsets: torch.Tensor, N_out: int, *,
+                       center: bool = True, unit_length: bool = True, fp32: bool = False,
+                       out: torch.Tensor | None = None, status: torch.Tensor | None = None,
+                       workspace: torch.Tensor | None = None):
+    """Arc-length resampling of C ragged curves (Sec. 2 of the paper).
+
+    pts: complex128 CUDA tensor [n_pts] (all curves' distinct nodes);
+    offsets: int64 CUDA tensor [C+1].  Returns (z [C, N_out] complex128 or
+    complex64, status int8 [C]).  A workspace (uint8 CUDA tensor of at least
+    resample_workspace_size() bytes) is allocated through torch when not given.
+    """
+    _need_cuda("pts", pts, torch.complex128)
+    _need_cuda("offsets", offsets, torch.int64)
+    C = offsets.numel() - 1
+    if C < 0:
+        raise ValueError("offsets must have at least one entry")
+    dev = pts.device
+    flags = (_lib.CENTER if center else 0) | (_lib.UNIT_LENGTH if unit_length else 0) | \
+            (_lib.STORE_FP32 if fp32 else 0)
+    zdt = torch.complex64 if fp32 else torch.complex128
+    if out is None:
+        out = torch.empty((C, N_out), dtype=zdt, device=dev)
+    else:
+        _need_cuda("out", out, zdt)
+    if status is None:
+        status = torch.empty(C, dtype=torch.int8, device=dev)
+    L = _lib.load()
+    n_pts = pts.numel()
+    need = int(L.fa_resample_workspace_size(C, n_pts, N_out, flags))
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    h = handle(dev.index)
+    rc = L.fa_resample_arclength(h, _ptr(pts), _ptr(offsets), C, n_pts, N_out, flags,
+                                 _ptr(out), _ptr(status), _ptr(workspace), workspace.numel(),
+                                 _stream_ptr(dev))
+    _lib.check(rc)
+    return out, status
+
+
+_METHODS = {"fft": _lib.FFT, "direct": _lib.DIRECT}
+_PRECS = {"fp64": _lib.PREC_FP64}
+
+
+def align_pairs(z1: torch.Tensor, z2: torch.Tensor, *, method: str = "fft", prec: str = "fp64",
+                out: tuple | None = None):
+    """Optimal start point and rotation for P pairs of curves (Algorithm 2).
+
+    z1, z2: [P, N] complex128 or complex64 CUDA tensors (centred, unit length).
+    Returns (shift int32 [P], theta float64 [P], energy float64 [P],
+    status int8 [P]); theta is the counter-clockwise angle applied to curve 2.
+    """
+    if z1.dtype not in (torch.complex128, torch.complex64):
+        raise ValueError("z1 must be complex128 or complex64")
+    _need_cuda("z1", z1, z1.dtype)
+    _need_cuda("z2", z2, z1.dtype)
+    if z1.dim() != 2 or z1.shape != z2.shape:
+        raise ValueError("z1 and z2 must both be [P, N]")
+    P, N = z1.shape
+    dev = z1.device
+    if out is None:
+        shift = torch.empty(P, dtype=torch.int32, device=dev)
+        theta = torch.empty(P, dtype=torch.float64, device=dev)
+        energy = torch.empty(P, dtype=torch.float64, device=dev)
+        status = torch.empty(P, dtype=torch.int8, device=dev)
+    else:
+        shift, theta, energy, status = out
+    ztype = _lib.Z_F64 if z1.dtype == torch.complex128 else _lib.Z_F32
+    L = _lib.load()
+    h = handle(dev.index)
+    rc = L.fa_align_pairs(h, _ptr(z1), _ptr(z2), P, N, ztype, _METHODS[method], _PRECS[prec],
+                          _ptr(shift), _ptr(theta), _ptr(energy), _ptr(status), _stream_ptr(dev))
+    _lib.check(rc)
+    return shift, theta, energy, status
+
+
+def align_curves_host(pts: torch.Tensor, offsets: torch.Tensor, N: int, *, method: str = "fft",
+                      prec: str = "fp64", fp32_storage: bool = False, out: tuple | None = None,
+                      device: int | None = None):
+    """Resample 2P raw curves to N nodes and align curve p with curve P+p,
+    from host buffers to host buffers (fa_align_curves_host).
+
+    pts: complex128 CPU tensor (pinned memory for asynchronous copies);
+    offsets: int64 CPU tensor [2P+1].  Returns CPU tensors (shift, theta,
+    energy, status) of P entries; blocks until they are filled.
+    """
+    if pts.is_cuda or offsets.is_cuda:
+        raise ValueError("align_curves_host takes host (CPU) tensors")
+    if pts.dtype != torch.complex128 or offsets.dtype != torch.int64:
+        raise ValueError("pts must be complex128 and offsets int64")
+    C = offsets.numel() - 1
+    if C % 2:
+        raise ValueError("offsets must describe an even number of curves (2P)")
+    P = C // 2
+    if out is None:
+        pin = torch.cuda.is_available()
+        shift = torch.empty(P, dtype=torch.int32, pin_memory=pin)
+        theta = torch.empty(P, dtype=torch.float64, pin_memory=pin)
+        energy = torch.empty(P, dtype=torch.float64, pin_memory=pin)
+        status = torch.empty(P, dtype=torch.int8, pin_memory=pin)
+    else:
+        shift, theta, energy, status = out
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    L = _lib.load()
+    h = handle(dev.index)
+    flags = _lib.STORE_FP32 if fp32_storage else 0
+    rc = L.fa_align_curves_host(h, _ptr(pts), _ptr(offsets), P, N, flags, _METHODS[method],
+                                _PRECS[prec], _ptr(shift), _ptr(theta), _ptr(energy),
+                                _ptr(status), _stream_ptr(dev))
+    _lib.check(rc)
+    return shift, theta, energy, status

@@ -1,0 +1,297 @@
+// api.cu -- the extern "C" entry points of libfftalign.so (declared, with
+// their contracts, in include/fftalign.h): argument validation, device
+// selection, twiddle tables and workspace management.  All arithmetic of the
+// method runs in the kernels of align_fft.cu, align_direct.cu and resample.cu.
+#include <cuda_runtime.h>
+
+#include <new>
+#include <string>
+
+#include "fa_internal.cuh"
+
+namespace fa {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char* where)
+{
+    if (e == cudaSuccess) return FA_OK;
+    return set_error(FA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// W_N[k] = exp(-2 pi i k / N) = cospi(2k/N) - i sinpi(2k/N); 2k/N is exact in binary.
+__global__ void twiddle_kernel(double2* w64, float2* w32, int N)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)N, &s, &c);
+    w64[k] = make_double2(c, -s);
+    w32[k] = make_float2((float)c, (float)-s);
+}
+
+int build_twiddles(fa_handle* h)
+{
+    for (int L = kMinLogN; L <= kMaxLogN; ++L) {
+        const int N = 1 << L;
+        cudaError_t e = cudaMalloc(&h->tw64[L], N * sizeof(double2));
+        if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
+        e = cudaMalloc(&h->tw32[L], N * sizeof(float2));
+        if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
+        twiddle_kernel<<<(N + 255) / 256, 256>>>(h->tw64[L], h->tw32[L], N);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(e, "fa_create: twiddle kernel");
+    }
+    return cuda_error(cudaDeviceSynchronize(), "fa_create: twiddle build");
+}
+
+// Makes the handle's device current for the lifetime of the object and
+// restores the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    int rc = FA_OK;
+    explicit DeviceGuard(int dev)
+    {
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e == cudaSuccess && prev != dev) e = cudaSetDevice(dev);
+        if (e != cudaSuccess) rc = cuda_error(e, "cudaSetDevice");
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static int ensure_ws(fa_handle* h, size_t bytes)
+{
+    if (h->ws_bytes >= bytes) return FA_OK;
+    if (h->ws) {
+        cudaError_t e = cudaFree(h->ws);  // implicit device synchronisation
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+        if (e != cudaSuccess) return cuda_error(e, "workspace cudaFree");
+    }
+    cudaError_t e = cudaMalloc(&h->ws, bytes);
+    if (e != cudaSuccess) {
+        h->ws = nullptr;
+        return cuda_error(e, "workspace cudaMalloc");
+    }
+    h->ws_bytes = bytes;
+    return FA_OK;
+}
+
+// A pair inherits the resampling status of its curves: a curve that could not
+// be resampled makes the pair's outputs NaN with that status.
+__global__ void merge_status_kernel(const int8_t* __restrict__ rst, int64_t P,
+                                    int32_t* __restrict__ shift, double* __restrict__ theta,
+                                    double* __restrict__ energy, int8_t* __restrict__ status)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int8_t s = rst[p] != FA_STATUS_OK ? rst[p] : rst[P + p];
+    if (s != FA_STATUS_OK) {
+        shift[p] = -1;
+        theta[p] = __longlong_as_double(0x7ff8000000000000LL);
+        energy[p] = __longlong_as_double(0x7ff8000000000000LL);
+        status[p] = s;
+    }
+}
+
+}  // namespace fa
+
+using namespace fa;
+
+extern "C" {
+
+const char* fa_last_error(void) { return g_last_error.c_str(); }
+
+int fa_version(void) { return 10000; }
+
+int fa_create(fa_handle** out, int device)
+{
+    if (!out) return set_error(FA_ERR_INVALID_ARG, "fa_create: null handle pointer");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaGetDeviceCount");
+    if (device < 0 || device >= count)
+        return set_error(FA_ERR_INVALID_ARG, "fa_create: no such device");
+    fa_handle* h = new (std::nothrow) fa_handle();
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_create: out of host memory");
+    h->device = device;
+    DeviceGuard g(device);
+    if (g.rc != FA_OK) { delete h; return g.rc; }
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) { delete h; return cuda_error(e, "fa_create: attributes"); }
+    int rc = build_twiddles(h);
+    if (rc != FA_OK) { fa_destroy(h); return rc; }
+    *out = h;
+    return FA_OK;
+}
+
+int fa_destroy(fa_handle* h)
+{
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_destroy: null handle");
+    DeviceGuard g(h->device);
+    for (int L = 0; L <= kMaxLogN; ++L) {
+        if (h->tw64[L]) cudaFree(h->tw64[L]);
+        if (h->tw32[L]) cudaFree(h->tw32[L]);
+    }
+    if (h->ws) cudaFree(h->ws);
+    delete h;
+    return FA_OK;
+}
+
+size_t fa_resample_workspace_size(int64_t C, int64_t n_pts, int32_t N_out, int32_t flags)
+{
+    if (C < 0 || n_pts < 0 || N_out <= 0) return 0;
+    return resample_ws_bytes(C, n_pts, N_out, flags);
+}
+
+int fa_resample_arclength(fa_handle* h, const double* pts, const int64_t* offsets, int64_t C,
+                          int64_t n_pts, int32_t N_out, int32_t flags, void* z_out,
+                          int8_t* status, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_resample_arclength: null handle");
+    if (C < 0 || n_pts < 0)
+        return set_error(FA_ERR_INVALID_ARG, "fa_resample_arclength: negative size");
+    if (N_out < 4 || N_out > (1 << 20))
+        return set_error(FA_ERR_UNSUPPORTED, "fa_resample_arclength: N_out outside [4, 2^20]");
+    if (flags & ~(FA_CENTER | FA_UNIT_LENGTH | FA_STORE_FP32))
+        return set_error(FA_ERR_INVALID_ARG, "fa_resample_arclength: unknown flag");
+    if (C == 0) return FA_OK;
+    if (!offsets || !z_out || !status || (n_pts > 0 && !pts))
+        return set_error(FA_ERR_INVALID_ARG, "fa_resample_arclength: null pointer");
+    if (C > (int64_t)1 << 40 || n_pts > (int64_t)1 << 40)
+        return set_error(FA_ERR_UNSUPPORTED, "fa_resample_arclength: size too large");
+    DeviceGuard g(h->device);
+    if (g.rc != FA_OK) return g.rc;
+    const size_t need = resample_ws_bytes(C, n_pts, N_out, flags);
+    void* ws = workspace;
+    if (ws) {
+        if (workspace_bytes < need)
+            return set_error(FA_ERR_WORKSPACE, "fa_resample_arclength: workspace too small");
+        if (reinterpret_cast<uintptr_t>(ws) & 255)
+            return set_error(FA_ERR_INVALID_ARG, "fa_resample_arclength: workspace not 256-aligned");
+    } else {
+        const int rc = ensure_ws(h, need);
+        if (rc != FA_OK) return rc;
+        ws = h->ws;
+    }
+    return launch_resample(h, pts, offsets, C, n_pts, N_out, flags, z_out, status, ws,
+                           static_cast<cudaStream_t>(stream));
+}
+
+int fa_align_pairs(fa_handle* h, const void* z1, const void* z2, int64_t P, int32_t N,
+                   int32_t ztype, int32_t method, int32_t prec, int32_t* shift, double* theta,
+                   double* energy, int8_t* status, void* stream)
+{
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs: null handle");
+    if (P < 0) return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs: negative pair count");
+    if (ztype != FA_Z_F64 && ztype != FA_Z_F32)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs: unknown ztype");
+    if (method != FA_FFT && method != FA_DIRECT)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs: unknown method");
+    if (prec != FA_PREC_FP64)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs: unknown precision");
+    int logn = -1;
+    if (method == FA_FFT) {
+        for (int L = kMinLogN; L <= kMaxLogN; ++L)
+            if (N == (1 << L)) logn = L;
+        if (logn < 0)
+            return set_error(FA_ERR_UNSUPPORTED,
+                             "fa_align_pairs: FA_FFT needs N a power of two in [4, 4096]");
+    } else if (N < 1 || N > kMaxDirectN) {
+        return set_error(FA_ERR_UNSUPPORTED, "fa_align_pairs: FA_DIRECT needs N in [1, 4096]");
+    }
+    if (P == 0) return FA_OK;
+    if (P > (int64_t)1 << 31)
+        return set_error(FA_ERR_UNSUPPORTED, "fa_align_pairs: more than 2^31 pairs");
+    if (!z1 || !z2 || !shift || !theta || !energy || !status)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs: null pointer");
+    DeviceGuard g(h->device);
+    if (g.rc != FA_OK) return g.rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (method == FA_FFT)
+        return launch_align_fft(h, z1, z2, P, logn, ztype, shift, theta, energy, status, st);
+    return launch_align_direct(h, z1, z2, P, N, ztype, shift, theta, energy, status, st);
+}
+
+}  // extern "C"
+
+extern "C" int fa_align_curves_host(fa_handle* h, const double* pts, const int64_t* offsets,
+                                    int64_t P, int32_t N, int32_t flags, int32_t method,
+                                    int32_t prec, int32_t* shift, double* theta, double* energy,
+                                    int8_t* status, void* stream)
+{
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_align_curves_host: null handle");
+    if (P < 0) return set_error(FA_ERR_INVALID_ARG, "fa_align_curves_host: negative pair count");
+    if (flags & ~FA_STORE_FP32)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_curves_host: unknown flag");
+    if (P == 0) return FA_OK;
+    if (!pts && offsets && offsets[2 * P] > 0)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_curves_host: null pointer");
+    if (!offsets || !shift || !theta || !energy || !status)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_curves_host: null pointer");
+    const int64_t C = 2 * P;
+    if (offsets[0] != 0)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_curves_host: offsets[0] must be 0");
+    for (int64_t i = 0; i < C; ++i)
+        if (offsets[i + 1] < offsets[i])
+            return set_error(FA_ERR_INVALID_ARG, "fa_align_curves_host: decreasing offsets");
+    const int64_t n_pts = offsets[C];
+    const int ztype = (flags & FA_STORE_FP32) ? FA_Z_F32 : FA_Z_F64;
+    const size_t zb = (flags & FA_STORE_FP32) ? sizeof(float2) : sizeof(double2);
+    auto a256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const int rflags = FA_CENTER | FA_UNIT_LENGTH | (flags & FA_STORE_FP32);
+    const size_t b_off = a256((size_t)(C + 1) * sizeof(int64_t));
+    const size_t b_pts = a256((size_t)n_pts * sizeof(double2));
+    const size_t b_z = a256((size_t)C * (size_t)N * zb);
+    const size_t b_rst = a256((size_t)C);
+    const size_t b_sh = a256((size_t)P * sizeof(int32_t));
+    const size_t b_th = a256((size_t)P * sizeof(double));
+    const size_t b_st = a256((size_t)P);
+    const size_t b_ws = a256(resample_ws_bytes(C, n_pts, N, rflags));
+    if (N < 4 || N > (1 << 20))
+        return set_error(FA_ERR_UNSUPPORTED, "fa_align_curves_host: N outside [4, 2^20]");
+    DeviceGuard g(h->device);
+    if (g.rc != FA_OK) return g.rc;
+    int rc = ensure_ws(h, b_off + b_pts + b_z + b_rst + b_sh + 2 * b_th + b_st + b_ws);
+    if (rc != FA_OK) return rc;
+    char* w = static_cast<char*>(h->ws);
+    int64_t* d_off = reinterpret_cast<int64_t*>(w); w += b_off;
+    double* d_pts = reinterpret_cast<double*>(w); w += b_pts;
+    void* d_z = w; w += b_z;
+    int8_t* d_rst = reinterpret_cast<int8_t*>(w); w += b_rst;
+    int32_t* d_sh = reinterpret_cast<int32_t*>(w); w += b_sh;
+    double* d_th = reinterpret_cast<double*>(w); w += b_th;
+    double* d_en = reinterpret_cast<double*>(w); w += b_th;
+    int8_t* d_st = reinterpret_cast<int8_t*>(w); w += b_st;
+    void* d_ws = w;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(d_off, offsets, (size_t)(C + 1) * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_pts > 0)
+        e = cudaMemcpyAsync(d_pts, pts, (size_t)n_pts * sizeof(double2), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "fa_align_curves_host: upload");
+    rc = fa_resample_arclength(h, d_pts, d_off, C, n_pts, N, rflags, d_z, d_rst, d_ws, b_ws, stream);
+    if (rc != FA_OK) return rc;
+    const char* z2 = static_cast<const char*>(d_z) + (size_t)P * (size_t)N * zb;
+    rc = fa_align_pairs(h, d_z, z2, P, N, ztype, method, prec, d_sh, d_th, d_en, d_st, stream);
+    if (rc != FA_OK) return rc;
+    merge_status_kernel<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(d_rst, P, d_sh, d_th, d_en, d_st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(shift, d_sh, (size_t)P * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(theta, d_th, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(energy, d_en, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status, d_st, (size_t)P, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_error(e, "fa_align_curves_host");
+}

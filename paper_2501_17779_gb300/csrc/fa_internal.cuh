@@ -1,0 +1,79 @@
+// fa_internal.cuh -- shared declarations of the CUDA side of libfftalign.so.
+// Device helpers here are used only by the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "fftalign.h"
+
+struct fa_handle {
+    int device = 0;
+    int num_sms = 0;
+    // twiddle tables W_N[k] = exp(-2 pi i k / N), k = 0..N-1, for N = 2^logn, logn in [2, 12]
+    double2* tw64[13] = {};
+    float2* tw32[13] = {};
+    // handle-owned scratch, used when the caller passes no workspace
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+namespace fa {
+
+constexpr int kMinLogN = 2;
+constexpr int kMaxLogN = 12;
+constexpr int kMaxDirectN = 4096;
+
+// error reporting (thread-local message for fa_last_error)
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* where);
+
+// ---------------------------------------------------------------- device ----
+__device__ __forceinline__ bool finite2(double2 v)
+{
+    // exponent field all ones <=> Inf or NaN; integer test, no FP64 instruction
+    const unsigned long long ex = 0x7ff0000000000000ULL;
+    return ((__double_as_longlong(v.x) & ex) != ex) && ((__double_as_longlong(v.y) & ex) != ex);
+}
+
+__device__ __forceinline__ double2 ld_z(const double2* __restrict__ p, int64_t i) { return __ldg(p + i); }
+__device__ __forceinline__ double2 ld_z(const float2* __restrict__ p, int64_t i)
+{
+    const float2 v = __ldg(p + i);
+    return make_double2((double)v.x, (double)v.y);
+}
+
+// (a.x + i a.y)(b.x + i b.y): 2 DMUL + 2 DFMA
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+
+// argmax key order: larger |c|^2 first, then the smaller shift.  |c|^2 >= 0,
+// so its IEEE bit pattern orders like the value (integer compare).
+__device__ __forceinline__ bool key_better(long long ka, int ia, long long kb, int ib)
+{
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+// ------------------------------------------------------------- launchers ----
+int launch_align_fft(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
+                     int ztype, int32_t* shift, double* theta, double* energy, int8_t* status,
+                     cudaStream_t st);
+int launch_align_direct(const fa_handle* h, const void* z1, const void* z2, int64_t P, int N,
+                        int ztype, int32_t* shift, double* theta, double* energy, int8_t* status,
+                        cudaStream_t st);
+int launch_resample(const fa_handle* h, const double* pts, const int64_t* offsets, int64_t C,
+                    int64_t n_pts, int N_out, int flags, void* z_out, int8_t* status, void* ws,
+                    cudaStream_t st);
+size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags);
+int build_twiddles(fa_handle* h);
+
+}  // namespace fa

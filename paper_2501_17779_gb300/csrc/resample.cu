@@ -1,0 +1,378 @@
+// resample.cu -- arc-length resampling (Sec. 2: Eq. arc-length-param, then a
+// cubic spline through (s^l, beta^l) evaluated at uniform parameters), FP64.
+//
+// One warp per curve.  Lane j owns a contiguous chunk of nodes
+// [s_j, s_{j+1}) (P chunks, P = 32 for n >= 64).  Steps:
+//   A. chord lengths d_l = |p_{l+1} - p_l| and their sum per chunk; a warp scan
+//      gives each chunk's starting arc length and the perimeter L.
+//   B. forward sweep over each chunk's interior nodes (all but its last):
+//      knots u_l, the periodic-spline equations
+//          h_{l-1} M_{l-1} + 2(h_{l-1}+h_l) M_l + h_l M_{l+1}
+//              = 6[(p_{l+1}-p_l)/h_l - (p_l-p_{l-1})/h_{l-1}],   h_l = d_l / L,
+//      and the Thomas elimination of the interior with the chunk's two
+//      neighbouring interface nodes (the last node of the previous chunk and
+//      of this chunk) kept as unknowns: M_i = y_i - I_{j-1} g_i - I_j k_i.
+//   C. a backward sweep without stores gives y, g, k at the first interior
+//      node; eliminating the interiors leaves a cyclic tridiagonal system in
+//      the P interface values, solved by parallel cyclic reduction with warp
+//      shuffles.
+//   D. a second backward sweep writes M for every node.
+//   E. the spline is evaluated at t_k = k/N_out (each lane a contiguous block
+//      of outputs; interval search by integer compares on the knots), then
+//      the outputs are centred at their mean and divided by the closed-polygon
+//      perimeter of the resampled nodes.
+// Per-node intermediates live in a caller- or handle-provided workspace
+// (global memory, L1/L2 resident while a warp works on its curve).
+#include "fa_internal.cuh"
+
+namespace fa {
+namespace {
+
+constexpr int kWarps = 4;  // curves per CTA
+
+struct Ws {
+    double* U;     // knots u_l                         [n_pts]
+    double* D;     // chord lengths d_l                 [n_pts]
+    double* IH;    // 1/h_l = L/d_l                     [n_pts]
+    double2* F0;   // forward sweep (c'_l, g'_l)        [n_pts]
+    double2* F1;   // forward sweep y'_l (x, y)         [n_pts]
+    double2* M;    // spline second derivatives M_l     [n_pts]
+    double2* Z;    // raw outputs before normalisation  [C*N_out] (FP32 output only)
+};
+
+__device__ __forceinline__ double2 d2(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return d2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return d2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 scl2(double2 a, double s) { return d2(a.x * s, a.y * s); }
+
+__device__ __forceinline__ double shfl_d(double v, int src, int width)
+{
+    return __shfl_sync(0xffffffffu, v, src, width);
+}
+__device__ __forceinline__ double2 shfl_d2(double2 v, int src, int width)
+{
+    return d2(__shfl_sync(0xffffffffu, v.x, src, width), __shfl_sync(0xffffffffu, v.y, src, width));
+}
+
+template <bool F32OUT>
+__device__ __forceinline__ void store_out(void* zout, int64_t i, double2 v)
+{
+    if constexpr (F32OUT)
+        static_cast<float2*>(zout)[i] = make_float2((float)v.x, (float)v.y);
+    else
+        static_cast<double2*>(zout)[i] = v;
+}
+
+template <bool F32OUT>
+__device__ void fill_nan(void* zout, int64_t base, int Nout, int lane)
+{
+    const double q = __longlong_as_double(0x7ff8000000000000LL);
+    for (int k = lane; k < Nout; k += 32) store_out<F32OUT>(zout, base + k, d2(q, q));
+}
+
+template <bool F32OUT>
+__global__ void __launch_bounds__(kWarps * 32)
+    resample_kernel(const double2* __restrict__ pts, const int64_t* __restrict__ offsets,
+                    int64_t C, int Nout, int flags, void* __restrict__ zout,
+                    int8_t* __restrict__ status, Ws ws)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t curve = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    if (curve >= C) return;  // whole warp leaves together
+    const int64_t o = offsets[curve];
+    int n = (int)(offsets[curve + 1] - o);
+    const double2* p = pts + o;
+    const int64_t zbase = curve * (int64_t)Nout;
+
+    // ---- input checks (whole warp) ----------------------------------------
+    bool nf = false;
+    for (int l = lane; l < n; l += 32) nf |= !finite2(__ldg(p + l));
+    if (__any_sync(0xffffffffu, nf)) {
+        fill_nan<F32OUT>(zout, zbase, Nout, lane);
+        if (lane == 0) status[curve] = FA_STATUS_NONFINITE;
+        return;
+    }
+    if (n >= 2) {
+        const double2 a = __ldg(p), b = __ldg(p + n - 1);
+        if (a.x == b.x && a.y == b.y) n -= 1;  // explicit closing duplicate (first = last)
+    }
+    if (n < 4) {
+        fill_nan<F32OUT>(zout, zbase, Nout, lane);
+        if (lane == 0) status[curve] = FA_STATUS_DEGENERATE;
+        return;
+    }
+
+    // ---- chunking -----------------------------------------------------------
+    int P = 32;
+    while (2 * P > n) P >>= 1;  // every chunk has >= 2 nodes (>= 1 interior)
+    const bool act = lane < P;
+    const int sj = (int)((int64_t)lane * n / P);
+    const int sj1 = (int)((int64_t)(lane + 1) * n / P);
+    const int ej = sj1 - 1;  // this chunk's interface node
+
+    double* U = ws.U + o;
+    double* D = ws.D + o;
+    double* IH = ws.IH + o;
+    double2* F0 = ws.F0 + o;
+    double2* F1 = ws.F1 + o;
+    double2* M = ws.M + o;
+
+    // ---- A: chords, chunk sums, warp scan -------------------------------------
+    double csum = 0.0;
+    bool zero = false;
+    if (act) {
+        double2 pl = __ldg(p + sj);
+        for (int l = sj; l < sj1; ++l) {
+            const int ln = (l + 1 == n) ? 0 : l + 1;
+            const double2 pn = __ldg(p + ln);
+            const double dx = pn.x - pl.x, dy = pn.y - pl.y;
+            const double d = sqrt(fma(dx, dx, dy * dy));
+            zero |= !(d > 0.0);
+            D[l] = d;
+            csum += d;
+            pl = pn;
+        }
+    }
+    if (__any_sync(0xffffffffu, zero)) {
+        fill_nan<F32OUT>(zout, zbase, Nout, lane);
+        if (lane == 0) status[curve] = FA_STATUS_DEGENERATE;
+        return;
+    }
+    double incl = csum;  // inclusive scan over lanes (lanes >= P hold 0)
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const double L = __shfl_sync(0xffffffffu, incl, 31);
+    const double base = incl - csum;  // arc length before node s_j
+    const double invL = 1.0 / L;
+    __syncwarp();
+
+    // ---- B: forward sweep over the interior ---------------------------------
+    // interface-node equation data kept for the reduced system
+    double Ae = 0, Be = 0, Ce = 0;
+    double2 Re = d2(0, 0), yL = d2(0, 0);
+    double gL = 0, kL = 0;
+    if (act) {
+        const int lp = (sj == 0) ? n - 1 : sj - 1;
+        const double dprev = D[lp];
+        double hprev = dprev * invL;
+        double2 pcur = __ldg(p + sj);
+        double2 gprev = scl2(sub2(pcur, __ldg(p + lp)), L / dprev);
+        double S = base;
+        double cp = 0, gp = 0;
+        double2 yp = d2(0, 0);
+        for (int i = sj; i < ej; ++i) {
+            const double d = D[i];
+            const double h = d * invL;
+            const double ih = L / d;
+            IH[i] = ih;
+            U[i] = S * invL;
+            S += d;
+            const double2 pn = __ldg(p + i + 1);  // i + 1 <= ej < n
+            const double2 g = scl2(sub2(pn, pcur), ih);
+            const double2 R = scl2(sub2(g, gprev), 6.0);
+            const double B = 2.0 * (hprev + h);
+            const bool first = (i == sj);
+            const double den = first ? B : fma(-hprev, cp, B);
+            const double r = 1.0 / den;
+            const double ncp = h * r;
+            const double2 nyp = first ? scl2(R, r)
+                                      : d2((R.x - hprev * yp.x) * r, (R.y - hprev * yp.y) * r);
+            const double ngp = first ? hprev * r : -hprev * gp * r;
+            F0[i] = d2(ncp, ngp);
+            F1[i] = nyp;
+            cp = ncp; gp = ngp; yp = nyp;
+            hprev = h; gprev = g; pcur = pn;
+        }
+        // last interior node's values: M_L = y'_L - I_{j-1} g'_L - I_j c'_L
+        yL = yp; gL = gp; kL = cp;
+        // interface node e_j
+        const double d = D[ej];
+        const double h = d * invL;
+        const double ih = L / d;
+        IH[ej] = ih;
+        U[ej] = S * invL;
+        const int en = (ej + 1 == n) ? 0 : ej + 1;
+        const double2 g = scl2(sub2(__ldg(p + en), pcur), ih);
+        Re = scl2(sub2(g, gprev), 6.0);
+        Ae = hprev;
+        Ce = h;
+        Be = 2.0 * (hprev + h);
+    }
+
+    // ---- C: backward sweep (no stores) for the first interior node ----------
+    double2 yF = yL;
+    double gF = gL, kF = kL;
+    if (act) {
+        for (int i = ej - 2; i >= sj; --i) {
+            const double2 f0 = F0[i];
+            const double2 f1 = F1[i];
+            yF = d2(fma(-f0.x, yF.x, f1.x), fma(-f0.x, yF.y, f1.y));
+            gF = fma(-f0.x, gF, f0.y);
+            kF = -f0.x * kF;
+        }
+    }
+    // reduced cyclic system over the P interfaces:
+    //   al I_{j-1} + be I_j + ga I_{j+1} = de
+    const int nxt = (lane + 1) & (P - 1);
+    const int prv = (lane + P - 1) & (P - 1);
+    const double2 yFn = shfl_d2(yF, nxt, P);
+    const double gFn = shfl_d(gF, nxt, P);
+    const double kFn = shfl_d(kF, nxt, P);
+    double al = -Ae * gL;
+    double be = Be - Ae * kL - Ce * gFn;
+    double ga = -Ce * kFn;
+    double2 de = d2(Re.x - Ae * yL.x - Ce * yFn.x, Re.y - Ae * yL.y - Ce * yFn.y);
+    // parallel cyclic reduction: strides 1, 2, .., P/4 leave each equation
+    // coupled only to the one at distance P/2
+    for (int s = 1; 2 * s < P; s <<= 1) {
+        const int lm = (lane + P - s) & (P - 1), lq = (lane + s) & (P - 1);
+        const double al_m = shfl_d(al, lm, P), be_m = shfl_d(be, lm, P), ga_m = shfl_d(ga, lm, P);
+        const double2 de_m = shfl_d2(de, lm, P);
+        const double al_p = shfl_d(al, lq, P), be_p = shfl_d(be, lq, P), ga_p = shfl_d(ga, lq, P);
+        const double2 de_p = shfl_d2(de, lq, P);
+        const double k1 = al / be_m, k2 = ga / be_p;
+        be = be - ga_m * k1 - al_p * k2;
+        de = d2(de.x - de_m.x * k1 - de_p.x * k2, de.y - de_m.y * k1 - de_p.y * k2);
+        al = -al_m * k1;
+        ga = -ga_p * k2;
+    }
+    double2 I;
+    {
+        const int pm = (lane + P / 2) & (P - 1);
+        const double off_j = al + ga;
+        const double off_m = shfl_d(al, pm, P) + shfl_d(ga, pm, P);
+        const double be_m = shfl_d(be, pm, P);
+        const double2 de_m = shfl_d2(de, pm, P);
+        const double det = be * be_m - off_j * off_m;
+        I = d2((de.x * be_m - off_j * de_m.x) / det, (de.y * be_m - off_j * de_m.y) / det);
+    }
+    const double2 Iprev = shfl_d2(I, prv, P);
+
+    // ---- D: second backward sweep writes M ----------------------------------
+    if (act) {
+        M[ej] = I;
+        double2 Mi = d2(yL.x - Iprev.x * gL - I.x * kL, yL.y - Iprev.y * gL - I.y * kL);
+        M[ej - 1] = Mi;
+        for (int i = ej - 2; i >= sj; --i) {
+            const double2 f0 = F0[i];
+            const double2 f1 = F1[i];
+            Mi = d2(fma(-f0.x, Mi.x, fma(-Iprev.x, f0.y, f1.x)),
+                    fma(-f0.x, Mi.y, fma(-Iprev.y, f0.y, f1.y)));
+            M[i] = Mi;
+        }
+    }
+    __syncwarp();
+
+    // ---- E: evaluation at t_k = k / N_out ------------------------------------
+    const bool pow2 = (Nout & (Nout - 1)) == 0;
+    const double invN = 1.0 / (double)Nout;
+    const int per = (Nout + 31) / 32;
+    const int k0 = lane * per;
+    const int k1 = min(k0 + per, Nout);
+    double2* raw = F32OUT ? (ws.Z + zbase) : (static_cast<double2*>(zout) + zbase);
+    double2 ssum = d2(0, 0);
+    if (k0 < k1) {
+        const double t0 = pow2 ? k0 * invN : (double)k0 / (double)Nout;
+        const long long tb0 = __double_as_longlong(t0);
+        // last l with u_l <= t0 (u_0 = 0 <= t0); knots are >= 0 so their bits order like values
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__double_as_longlong(U[mid]) <= tb0) lo = mid; else hi = mid - 1;
+        }
+        int l = lo;
+        for (int k = k0; k < k1; ++k) {
+            const double t = pow2 ? k * invN : (double)k / (double)Nout;
+            const long long tb = __double_as_longlong(t);
+            while (l + 1 < n && __double_as_longlong(U[l + 1]) <= tb) ++l;
+            const int ln = (l + 1 == n) ? 0 : l + 1;
+            const double2 pl = __ldg(p + l), pn = __ldg(p + ln);
+            const double2 Ml = M[l], Mn = M[ln];
+            const double h = D[l] * invL;
+            const double b = (t - U[l]) * IH[l];
+            const double a = 1.0 - b;
+            const double h6 = h * h * (1.0 / 6.0);
+            const double ca = a * fma(a, a, -1.0) * h6;
+            const double cb = b * fma(b, b, -1.0) * h6;
+            const double2 S = d2(fma(ca, Ml.x, fma(cb, Mn.x, fma(b, pn.x - pl.x, pl.x))),
+                                 fma(ca, Ml.y, fma(cb, Mn.y, fma(b, pn.y - pl.y, pl.y))));
+            raw[k] = S;
+            ssum = add2(ssum, S);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ssum.x += __shfl_xor_sync(0xffffffffu, ssum.x, off);
+        ssum.y += __shfl_xor_sync(0xffffffffu, ssum.y, off);
+    }
+    __syncwarp();
+    const double2 mean = (flags & FA_CENTER) ? d2(ssum.x * invN, ssum.y * invN) : d2(0, 0);
+    double scale = 1.0;
+    if (flags & FA_UNIT_LENGTH) {
+        double per_len = 0.0;
+        for (int k = lane; k < Nout; k += 32) {
+            const double2 a = raw[k], b = raw[(k + 1 == Nout) ? 0 : k + 1];
+            const double dx = b.x - a.x, dy = b.y - a.y;
+            per_len += sqrt(fma(dx, dx, dy * dy));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) per_len += __shfl_xor_sync(0xffffffffu, per_len, off);
+        if (!(per_len > 0.0)) {
+            __syncwarp();
+            fill_nan<F32OUT>(zout, zbase, Nout, lane);
+            if (lane == 0) status[curve] = FA_STATUS_DEGENERATE;
+            return;
+        }
+        scale = 1.0 / per_len;
+    }
+    const double2 off = d2(-mean.x * scale, -mean.y * scale);
+    for (int k = lane; k < Nout; k += 32) {
+        const double2 S = raw[k];
+        store_out<F32OUT>(zout, zbase + k, d2(fma(S.x, scale, off.x), fma(S.y, scale, off.y)));
+    }
+    if (lane == 0) status[curve] = FA_STATUS_OK;
+}
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags)
+{
+    const size_t np = (size_t)(n_pts > 0 ? n_pts : 0);
+    size_t b = 3 * align256(np * sizeof(double)) + 3 * align256(np * sizeof(double2));
+    if (flags & FA_STORE_FP32) b += align256((size_t)C * (size_t)N_out * sizeof(double2));
+    return b;
+}
+
+int launch_resample(const fa_handle* h, const double* pts, const int64_t* offsets, int64_t C,
+                    int64_t n_pts, int N_out, int flags, void* z_out, int8_t* status, void* wsp,
+                    cudaStream_t st)
+{
+    (void)h;
+    if (C == 0) return FA_OK;
+    const size_t np = (size_t)(n_pts > 0 ? n_pts : 0);
+    char* b = static_cast<char*>(wsp);
+    Ws ws;
+    ws.U = reinterpret_cast<double*>(b); b += align256(np * sizeof(double));
+    ws.D = reinterpret_cast<double*>(b); b += align256(np * sizeof(double));
+    ws.IH = reinterpret_cast<double*>(b); b += align256(np * sizeof(double));
+    ws.F0 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
+    ws.F1 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
+    ws.M = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
+    ws.Z = (flags & FA_STORE_FP32) ? reinterpret_cast<double2*>(b) : nullptr;
+    const int64_t blocks = (C + kWarps - 1) / kWarps;
+    const double2* p = reinterpret_cast<const double2*>(pts);
+    if (flags & FA_STORE_FP32)
+        resample_kernel<true><<<(unsigned)blocks, kWarps * 32, 0, st>>>(p, offsets, C, N_out, flags,
+                                                                       z_out, status, ws);
+    else
+        resample_kernel<false><<<(unsigned)blocks, kWarps * 32, 0, st>>>(p, offsets, C, N_out,
+                                                                        flags, z_out, status, ws);
+    return cuda_error(cudaGetLastError(), "resample launch");
+}
+
+}  // namespace fa

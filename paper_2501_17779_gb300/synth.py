@@ -99,7 +99,7 @@ class AlignedPairs:
 
 
 def aligned_pairs(seed: int, P: int = 64, N: int = 256, n_harm: int = 8,
-                  noise: float = 1e-3) -> AlignedPairs:
+                  noise: float = 1e-3, oversample: int = 64) -> AlignedPairs:
     """Pairs already uniform in arc length, centred and of unit length.
 
     Default sizes are the 64-pair, N = 256 parity workload.  ``noise`` is the
@@ -113,7 +113,7 @@ def aligned_pairs(seed: int, P: int = 64, N: int = 256, n_harm: int = 8,
     th_true = np.empty(P, np.float64)
     for p in range(P):
         h = random_harmonics(rng, n_harm)
-        a = uniform_arclength_nodes(h, N)
+        a = uniform_arclength_nodes(h, N, oversample)
         th_g = rng.uniform(0.0, TWO_PI)
         s_g = int(rng.integers(0, N))
         b = np.exp(1j * th_g) * np.roll(a, s_g)  # b[k] = e^{i th} a[(k - s_g) mod N]

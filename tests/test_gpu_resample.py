@@ -1,0 +1,146 @@
+"""GPU parity of fa_resample_arclength and of the end-to-end path against
+the FP64 oracle (C ABI via paper_2501_17779_gb300.api)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2501_17779_gb300 import api, synth
+
+from _parity import check_align
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+TOL = 1e-12  # max |dz| of resampled, normalised nodes (FP64)
+
+
+def _gpu_resample(pts, offs, N, fp32=False, center=True, unit_length=True):
+    z, st = api.resample_arclength(torch.from_numpy(pts).to(DEV), torch.from_numpy(offs).to(DEV),
+                                   N, fp32=fp32, center=center, unit_length=unit_length)
+    torch.cuda.synchronize()
+    return z.cpu().numpy(), st.cpu().numpy()
+
+
+def _csr(curves):
+    offs = np.concatenate([[0], np.cumsum([c.size for c in curves])]).astype(np.int64)
+    return np.concatenate(curves).astype(np.complex128), offs
+
+
+@pytest.mark.parametrize("N", [256, 1024, 1000, 37])
+def test_resample_parity(N):
+    pts, offs = synth.raw_curves(N, C=40, n_min=500, n_max=2000)
+    z, st = _gpu_resample(pts, offs, N)
+    zo, sto = oracle.resample(pts, offs, N)
+    np.testing.assert_array_equal(st, sto)
+    assert np.abs(z - zo).max() <= TOL
+
+
+def test_resample_raw_spline_without_normalisation():
+    pts, offs = synth.raw_curves(3, C=16, n_min=40, n_max=400)
+    z, _ = _gpu_resample(pts, offs, 512, center=False, unit_length=False)
+    zo, _ = oracle.resample(pts, offs, 512, flags=0)
+    scale = np.abs(pts).max()
+    assert np.abs(z - zo).max() <= TOL * scale
+
+
+@pytest.mark.parametrize("n", [4, 5, 7, 8, 15, 31, 63, 64, 65, 127, 4001, 20000])
+def test_resample_chunking_edge_sizes(n):
+    """Node counts that give 2..32 chunks, single-node interiors and long
+    chunks."""
+    rng = np.random.default_rng(n)
+    phi = 2 * np.pi * (np.arange(n) + rng.uniform(-0.3, 0.3, n)) / n
+    c = (1 + 0.2 * np.cos(3 * phi)) * np.exp(1j * phi)
+    pts, offs = _csr([c, 2 * c + 1])
+    z, st = _gpu_resample(pts, offs, 256)
+    zo, sto = oracle.resample(pts, offs, 256)
+    np.testing.assert_array_equal(st, sto)
+    assert np.abs(z - zo).max() <= TOL
+
+
+def test_resample_degenerate_and_empty():
+    good = np.exp(2j * np.pi * np.arange(50) / 50)
+    rep = good.copy()
+    rep[7] = rep[6]
+    nan = good.copy()
+    nan[3] = np.nan + 0j
+    closed = np.concatenate([good, good[:1]])
+    pts, offs = _csr([good, good[:3], rep, nan, good[:0], closed])
+    z, st = _gpu_resample(pts, offs, 64)
+    zo, sto = oracle.resample(pts, offs, 64)
+    assert list(st) == [0, 1, 1, 2, 1, 0]
+    np.testing.assert_array_equal(st, sto)
+    assert np.isnan(z[1:5]).all()
+    assert np.abs(z[[0, 5]] - zo[[0, 5]]).max() <= TOL
+    # no curves at all
+    zz, ss = api.resample_arclength(torch.zeros(0, dtype=torch.complex128, device=DEV),
+                                    torch.zeros(1, dtype=torch.int64, device=DEV), 64)
+    assert zz.shape == (0, 64)
+
+
+def test_resample_fp32_storage():
+    pts, offs = synth.raw_curves(8, C=32, n_min=500, n_max=2000)
+    z, st = _gpu_resample(pts, offs, 1024, fp32=True)
+    zo, _ = oracle.resample(pts, offs, 1024)
+    assert z.dtype == np.complex64
+    # FP64 compute, one rounding to float at the store (relative error <= 2^-24)
+    for part in (np.real, np.imag):
+        d = np.abs(part(z).astype(np.float64) - part(zo))
+        assert (d <= 2.0 ** -24 * np.abs(part(zo)) + TOL).all()
+
+
+def test_end_to_end_pairs():
+    """Raw ragged pairs -> GPU resampling -> GPU alignment.  The alignment is
+    checked against the oracle on the GPU's resampled curves (FP64 bounds),
+    and the whole pipeline against the oracle pipeline."""
+    rp = synth.raw_pairs(2024, P=96)
+    z, st = _gpu_resample(rp.pts, rp.offsets, 1024)
+    assert (st == 0).all()
+    P = 96
+    t = torch.from_numpy(z).to(DEV)
+    s, th, e, ast = api.align_pairs(t[:P].contiguous(), t[P:].contiguous())
+    out = [x.cpu().numpy() for x in (s, th, e, ast)]
+    check_align(z[:P], z[P:], *out)
+    zo, _ = oracle.resample(rp.pts, rp.offsets, 1024)
+    check_align(zo[:P], zo[P:], *out, theta_tol=1e-9, e_rel=1e-9)
+
+
+def test_host_pipeline_matches_device_path():
+    rp = synth.raw_pairs(7, P=64)
+    P = 64
+    pts = torch.from_numpy(rp.pts).pin_memory()
+    offs = torch.from_numpy(rp.offsets).pin_memory()
+    hs = api.align_curves_host(pts, offs, 1024)
+    z, st = _gpu_resample(rp.pts, rp.offsets, 1024)
+    t = torch.from_numpy(z).to(DEV)
+    ds = api.align_pairs(t[:P].contiguous(), t[P:].contiguous())
+    for a, b in zip(hs, ds):
+        np.testing.assert_array_equal(a.numpy(), b.cpu().numpy())
+
+
+def test_host_pipeline_fp32_storage_bounds():
+    """complex64 storage between resampling and alignment: shift agreement
+    >= 99.9% (beyond FP64 ties), |dtheta| <= 1e-5, relative dE <= 1e-5."""
+    P = 1024
+    rp = synth.raw_pairs(8, P=P)
+    s, th, e, st = api.align_curves_host(torch.from_numpy(rp.pts), torch.from_numpy(rp.offsets),
+                                         1024, fp32_storage=True)
+    zo, _ = oracle.resample(rp.pts, rp.offsets, 1024)
+    check_align(zo[:P], zo[P:], s.numpy(), th.numpy(), e.numpy(), st.numpy(), theta_tol=1e-5,
+                e_rel=1e-5, e_abs=1e-7, shift_frac=0.999)
+
+
+def test_full_size_resample_properties_and_sample():
+    """8192 raw curves (4096 pairs, 500..2000 nodes) -> N = 1024, the
+    benchmark's launch; the oracle checks a sample, properties hold for all."""
+    rp = synth.raw_pairs(1000 + 2, P=4096)
+    z, st = _gpu_resample(rp.pts, rp.offsets, 1024)
+    assert (st == 0).all()
+    assert np.abs(z.mean(axis=1)).max() < 1e-15
+    per = np.abs(np.roll(z, -1, axis=1) - z).sum(axis=1)
+    assert np.abs(per - 1.0).max() < 1e-13
+    idx = np.random.default_rng(1).choice(8192, 64, replace=False)
+    sub = [rp.pts[rp.offsets[i]:rp.offsets[i + 1]] for i in idx]
+    pts, offs = _csr(sub)
+    zo, _ = oracle.resample(pts, offs, 1024)
+    assert np.abs(z[idx] - zo).max() <= TOL
