@@ -175,6 +175,38 @@ int fa_align_curves_host(fa_handle* h, const double* pts, const int64_t* offsets
                          int32_t N, int32_t flags, int32_t method, int32_t prec, int32_t* shift,
                          double* theta, double* energy, int8_t* status, void* stream);
 
+/*
+ * Arc-length resampling that allocates nothing (the paper has no counterpart:
+ * this is a deployment variant of fa_resample_arclength).
+ *
+ * For callers that cannot call cudaMalloc -- host applications that reserve
+ * all device memory up front and do not let libraries allocate, and
+ * latency-critical loops that cannot afford the implicit synchronisation of an
+ * allocation.  Such callers cannot create a handle either (fa_create
+ * allocates), so this call takes none and runs on the CURRENT device.  It
+ * computes exactly what fa_resample_arclength computes, with the same
+ * arguments except the handle and the workspace.
+ *
+ * Scratch: a fixed device array of FA_NOALLOC_SCRATCH_BYTES (64 MiB) that
+ * every GPU which loads the library holds until the process exits.  A batch
+ * needs fa_resample_workspace_size(C, n_pts, N_out, flags) bytes of it (72
+ * bytes per input node, plus 16 bytes per output node with FA_STORE_FP32:
+ * about 930,000 input nodes per call); larger batches are rejected with
+ * FA_ERR_UNSUPPORTED and a message giving both sizes.  Nothing is allocated,
+ * freed or zeroed.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device); make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last call's
+ * contents (every value a call reads it has written itself first): calls
+ * whose work overlaps on the GPU -- on different streams, or from different
+ * host threads -- race on it and must be serialised by the caller.
+ */
+#define FA_NOALLOC_SCRATCH_BYTES (64u << 20)
+int fa_resample_arclength_noalloc(const double* pts, const int64_t* offsets, int64_t C,
+                                  int64_t n_pts, int32_t N_out, int32_t flags, void* z_out,
+                                  int8_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

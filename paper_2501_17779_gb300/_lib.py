@@ -34,8 +34,9 @@ PREC_FP64 = 0
 EXPORTS = (
     "fa_create", "fa_destroy", "fa_last_error", "fa_version",
     "fa_resample_workspace_size", "fa_resample_arclength", "fa_align_pairs",
-    "fa_align_curves_host",
+    "fa_align_curves_host", "fa_resample_arclength_noalloc",
 )
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
 
@@ -81,6 +82,8 @@ def load(build_if_missing: bool = False):
     L.fa_align_pairs.restype = ctypes.c_int
     L.fa_align_curves_host.argtypes = [vp, vp, vp, i64, i32, i32, i32, i32, vp, vp, vp, vp, vp]
     L.fa_align_curves_host.restype = ctypes.c_int
+    L.fa_resample_arclength_noalloc.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp]
+    L.fa_resample_arclength_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
