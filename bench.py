@@ -49,8 +49,8 @@ FP64_NOMINAL_TFLOPS = 1.25
 def fft_flops(logn: int) -> int:
     """FP64 flops (FMA = 2) of one forward transform in the kernel's algorithm:
     an optional radix-2 stage (4 real adds per butterfly), then radix-4
-    Stockham stages: 16 adds per butterfly, plus 3 complex twiddle products
-    (2 mul + 2 fma = 6 flops each) in every stage after the first."""
+    Stockham stages: 16 adds per butterfly in an untwiddled stage, four FMA-form
+    butterflies (24 DFMA = 48 flops) per twiddled radix-4 butterfly."""
     N = 1 << logn
     q = N // 4
     fl = 0
@@ -60,7 +60,7 @@ def fft_flops(logn: int) -> int:
         fl += (N // 2) * 4
         first_twiddled = True
     for i in range(stages4):
-        fl += q * (16 + (18 if (i > 0 or first_twiddled) else 0))
+        fl += q * (48 if (i > 0 or first_twiddled) else 16)
     return fl
 
 
@@ -71,11 +71,11 @@ def align_fft_flops_per_pair(logn: int) -> int:
 
 
 def resample_flops(n_in: np.ndarray, N: int) -> int:
-    """FP64 flops of fa_resample_arclength (sqrt and division count 1):
-    48 per input node (chords, knots, spline equations, Thomas elimination,
-    two backward sweeps) and 42 per output node (evaluation, centring,
-    perimeter, scaling)."""
-    return int(48 * int(n_in.sum()) + 42 * N * n_in.size)
+    """FP64 flops of fa_resample_arclength (FMA = 2; rsqrt and reciprocal
+    count 1): 49 per input node (chords, knots, spline equations, Thomas
+    elimination, two backward sweeps) and 43 per output node (evaluation,
+    centring, perimeter, scaling)."""
+    return int(49 * int(n_in.sum()) + 43 * N * n_in.size)
 
 
 def direct_flops_per_pair(N: int) -> int:

@@ -16,8 +16,9 @@
 //
 // The path is bound by the FP64 pipe (about 2 DFMA per clock per SM on this
 // part), so the design minimises FP64 instructions: twiddles come from a
-// table, index arithmetic and the argmax compare are integer, and block
-// reductions run their FP64 adds on one warp only.
+// table in FMA form (every twiddled radix-4 butterfly is 24 DFMA), index
+// arithmetic and the argmax compare are integer, and block reductions run
+// their FP64 adds on one warp only.
 #include "fa_internal.cuh"
 
 namespace fa {
@@ -33,6 +34,37 @@ __device__ __forceinline__ void bfly4(double2& v0, double2& v1, double2& v2, dou
     v2 = make_double2(a0.x - a2.x, a0.y - a2.y);
     v1 = make_double2(a1.x + a3.y, a1.y - a3.x);  // a1 - i a3
     v3 = make_double2(a1.x - a3.y, a1.y + a3.x);  // a1 + i a3
+}
+
+// Radix-4 butterfly with twiddles W^e1, W^2e1, W^3e1 on v1, v2, v3, in FMA form:
+// (A, B) = v0 +- w^2 v2, (C, D) = v1 +- w^2 v3, y0/y2 = A +- w C, y1/y3 = B -+ i w D,
+// i.e. four FMA butterflies (24 DFMA) instead of three complex products plus
+// sixteen additions (28 instructions).  -i w = W^(e1 + N/4).
+struct Tw4 {
+    double2 t1, t2, t3;
+    bool f1, f2, f3;
+};
+
+template <int N>
+__device__ __forceinline__ Tw4 load_tw4(const double2* __restrict__ T, int e1)
+{
+    Tw4 w;
+    const int e2 = 2 * e1, e3 = e1 + N / 4;
+    w.t1 = __ldg(T + e1); w.t2 = __ldg(T + e2); w.t3 = __ldg(T + e3);
+    w.f1 = tw_form_b(e1, N); w.f2 = tw_form_b(e2, N); w.f3 = tw_form_b(e3, N);
+    return w;
+}
+
+__device__ __forceinline__ void bfly4_tw(double2& v0, double2& v1, double2& v2, double2& v3,
+                                         const Tw4& w)
+{
+    fbfly(v0, v2, w.t2, w.f2);  // v0 = A, v2 = B
+    fbfly(v1, v3, w.t2, w.f2);  // v1 = C, v3 = D
+    fbfly(v0, v1, w.t1, w.f1);  // v0 = y0, v1 = y2
+    fbfly(v2, v3, w.t3, w.f3);  // v2 = y1, v3 = y3
+    const double2 t = v1;
+    v1 = v2;
+    v2 = t;
 }
 
 template <int LOGN>
@@ -73,14 +105,13 @@ __device__ __forceinline__ void stage4_two(double2* X1, double2* X2, int t,
     double2 b0 = X2[t], b1 = X2[t + Q], b2 = X2[t + 2 * Q], b3 = X2[t + 3 * Q];
     const int k = t & (NS - 1);
     if constexpr (NS > 1) {
-        constexpr int STR = N / (4 * NS);
-        const double2 w1 = __ldg(W + k * STR), w2 = __ldg(W + 2 * k * STR),
-                      w3 = __ldg(W + 3 * k * STR);
-        a1 = cmul(a1, w1); a2 = cmul(a2, w2); a3 = cmul(a3, w3);
-        b1 = cmul(b1, w1); b2 = cmul(b2, w2); b3 = cmul(b3, w3);
+        const Tw4 w = load_tw4<N>(W, k * (N / (4 * NS)));
+        bfly4_tw(a0, a1, a2, a3, w);
+        bfly4_tw(b0, b1, b2, b3, w);
+    } else {
+        bfly4(a0, a1, a2, a3);
+        bfly4(b0, b1, b2, b3);
     }
-    bfly4(a0, a1, a2, a3);
-    bfly4(b0, b1, b2, b3);
     __syncthreads();
     const int idx = (t - k) * 4 + k;
     X1[idx] = a0; X1[idx + NS] = a1; X1[idx + 2 * NS] = a2; X1[idx + 3 * NS] = a3;
@@ -123,13 +154,10 @@ __device__ __forceinline__ void stage4_one(double2* X1, const double2* X2, int t
         v2 = cmulc(v2, X2[t + 2 * Q]); v3 = cmulc(v3, X2[t + 3 * Q]);
     }
     const int k = t & (NS - 1);
-    if constexpr (NS > 1) {
-        constexpr int STR = N / (4 * NS);
-        v1 = cmul(v1, __ldg(W + k * STR));
-        v2 = cmul(v2, __ldg(W + 2 * k * STR));
-        v3 = cmul(v3, __ldg(W + 3 * k * STR));
-    }
-    bfly4(v0, v1, v2, v3);
+    if constexpr (NS > 1)
+        bfly4_tw(v0, v1, v2, v3, load_tw4<N>(W, k * (N / (4 * NS))));
+    else
+        bfly4(v0, v1, v2, v3);
     if constexpr (LAST) {
         y[0] = v0; y[1] = v1; y[2] = v2; y[3] = v3;
     } else {
@@ -357,7 +385,7 @@ int launch_one(const fa_handle* h, const void* z1, const void* z2, int64_t P, in
     }
     const int64_t blocks = (P + Gm::G - 1) / Gm::G;
     kern<<<(unsigned)blocks, Gm::T, smem, st>>>(static_cast<const ZT*>(z1),
-                                                static_cast<const ZT*>(z2), P, h->tw64[LOGN],
+                                                static_cast<const ZT*>(z2), P, h->tf64[LOGN],
                                                 shift, theta, energy, status);
     return cuda_error(cudaGetLastError(), "align_fft launch");
 }

@@ -36,6 +36,17 @@ __global__ void twiddle_kernel(double2* w64, float2* w32, int N)
     w32[k] = make_float2((float)c, (float)-s);
 }
 
+// FMA-form twiddles (m, rho) for e in [0, N/2): W = m (1 + i rho) or m (rho + i).
+__global__ void fma_twiddle_kernel(double2* tf, int N)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N / 2) return;
+    double s, c;
+    sincospi(2.0 * (double)e / (double)N, &s, &c);
+    const double wr = c, wi = -s;
+    tf[e] = tw_form_b(e, N) ? make_double2(wi, wr / wi) : make_double2(wr, wi / wr);
+}
+
 int build_twiddles(fa_handle* h)
 {
     for (int L = kMinLogN; L <= kMaxLogN; ++L) {
@@ -44,6 +55,9 @@ int build_twiddles(fa_handle* h)
         if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
         e = cudaMalloc(&h->tw32[L], N * sizeof(float2));
         if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
+        e = cudaMalloc(&h->tf64[L], (N / 2) * sizeof(double2));
+        if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
+        fma_twiddle_kernel<<<(N / 2 + 255) / 256, 256>>>(h->tf64[L], N);
         twiddle_kernel<<<(N + 255) / 256, 256>>>(h->tw64[L], h->tw32[L], N);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(e, "fa_create: twiddle kernel");
@@ -143,6 +157,7 @@ int fa_destroy(fa_handle* h)
     for (int L = 0; L <= kMaxLogN; ++L) {
         if (h->tw64[L]) cudaFree(h->tw64[L]);
         if (h->tw32[L]) cudaFree(h->tw32[L]);
+        if (h->tf64[L]) cudaFree(h->tf64[L]);
     }
     if (h->ws) cudaFree(h->ws);
     delete h;

@@ -15,6 +15,9 @@ struct fa_handle {
     // twiddle tables W_N[k] = exp(-2 pi i k / N), k = 0..N-1, for N = 2^logn, logn in [2, 12]
     double2* tw64[13] = {};
     float2* tw32[13] = {};
+    // FMA-form twiddles for e in [0, N/2): (m, rho) with W_N^e = m (1 + i rho) when
+    // |cos| >= |sin| (e <= N/8 or e >= 3N/8), else W_N^e = m (rho + i); |rho| <= 1
+    double2* tf64[13] = {};
     // handle-owned scratch, used when the caller passes no workspace
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -54,6 +57,24 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 __device__ __forceinline__ double2 cmulc(double2 a, double2 b)
 {
     return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+
+// Which form a FMA twiddle W_N^e (0 <= e < N/2) is stored in (see fa_handle::tf64).
+__host__ __device__ __forceinline__ bool tw_form_b(int e, int N) { return 8 * e > N && 8 * e < 3 * N; }
+
+// (a, b) <- (a + w b, a - w b) with w = (m, rho) in FMA form: 6 DFMA, no other FP64
+// instruction (the form selects operands and flips a sign bit with integer ops).
+__device__ __forceinline__ void fbfly(double2& a, double2& b, double2 t, bool fb)
+{
+    const double m = t.x, rho = t.y;
+    const double U = fb ? b.x : b.y;
+    const double V = fb ? b.y : b.x;
+    const double tx = fma(-rho, U, V);
+    const double ty = fma(rho, V, U);
+    const double mx =
+        __longlong_as_double(__double_as_longlong(m) ^ ((unsigned long long)fb << 63));
+    b = make_double2(fma(-mx, tx, a.x), fma(-m, ty, a.y));
+    a = make_double2(fma(mx, tx, a.x), fma(m, ty, a.y));
 }
 
 // argmax key order: larger |c|^2 first, then the smaller shift.  |c|^2 >= 0,

@@ -118,6 +118,8 @@ __global__ void __launch_bounds__(kWarps * 32)
     double2* M = ws.M + o;
 
     // ---- A: chords, chunk sums, warp scan -------------------------------------
+    // d = q * rsqrt(q) and 1/d = rsqrt(q) from one reciprocal square root
+    // (q = |p_{l+1} - p_l|^2 >= 0, so its bit pattern tests > 0 as an integer)
     double csum = 0.0;
     bool zero = false;
     if (act) {
@@ -126,9 +128,13 @@ __global__ void __launch_bounds__(kWarps * 32)
             const int ln = (l + 1 == n) ? 0 : l + 1;
             const double2 pn = __ldg(p + ln);
             const double dx = pn.x - pl.x, dy = pn.y - pl.y;
-            const double d = sqrt(fma(dx, dx, dy * dy));
-            zero |= !(d > 0.0);
+            const double q = fma(dx, dx, dy * dy);
+            const bool pos = __double_as_longlong(q) > 0;
+            const double rs = rsqrt(q);
+            const double d = pos ? q * rs : 0.0;
+            zero |= !pos;
             D[l] = d;
+            IH[l] = rs;  // becomes L/d = 1/h in the forward sweep
             csum += d;
             pl = pn;
         }
@@ -156,17 +162,18 @@ __global__ void __launch_bounds__(kWarps * 32)
     double gL = 0, kL = 0;
     if (act) {
         const int lp = (sj == 0) ? n - 1 : sj - 1;
-        const double dprev = D[lp];
-        double hprev = dprev * invL;
+        double hprev = D[lp] * invL;
         double2 pcur = __ldg(p + sj);
-        double2 gprev = scl2(sub2(pcur, __ldg(p + lp)), L / dprev);
+        // (IH[lp] belongs to the previous lane, which rescales it concurrently;
+        //  one division per chunk avoids reading it)
+        double2 gprev = scl2(sub2(pcur, __ldg(p + lp)), L / D[lp]);
         double S = base;
         double cp = 0, gp = 0;
         double2 yp = d2(0, 0);
         for (int i = sj; i < ej; ++i) {
             const double d = D[i];
             const double h = d * invL;
-            const double ih = L / d;
+            const double ih = L * IH[i];
             IH[i] = ih;
             U[i] = S * invL;
             S += d;
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(kWarps * 32)
             const double B = 2.0 * (hprev + h);
             const bool first = (i == sj);
             const double den = first ? B : fma(-hprev, cp, B);
-            const double r = 1.0 / den;
+            const double r = __drcp_rn(den);
             const double ncp = h * r;
             const double2 nyp = first ? scl2(R, r)
                                       : d2((R.x - hprev * yp.x) * r, (R.y - hprev * yp.y) * r);
@@ -191,7 +198,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         // interface node e_j
         const double d = D[ej];
         const double h = d * invL;
-        const double ih = L / d;
+        const double ih = L * IH[ej];
         IH[ej] = ih;
         U[ej] = S * invL;
         const int en = (ej + 1 == n) ? 0 : ej + 1;
@@ -316,7 +323,8 @@ __global__ void __launch_bounds__(kWarps * 32)
         for (int k = lane; k < Nout; k += 32) {
             const double2 a = raw[k], b = raw[(k + 1 == Nout) ? 0 : k + 1];
             const double dx = b.x - a.x, dy = b.y - a.y;
-            per_len += sqrt(fma(dx, dx, dy * dy));
+            const double q = fma(dx, dx, dy * dy);
+            per_len += __double_as_longlong(q) > 0 ? q * rsqrt(q) : 0.0;
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) per_len += __shfl_xor_sync(0xffffffffu, per_len, off);
