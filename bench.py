@@ -72,10 +72,10 @@ def align_fft_flops_per_pair(logn: int) -> int:
 
 def resample_flops(n_in: np.ndarray, N: int) -> int:
     """FP64 flops of fa_resample_arclength (FMA = 2; rsqrt and reciprocal
-    count 1): 49 per input node (chords, knots, spline equations, Thomas
-    elimination, two backward sweeps) and 43 per output node (evaluation,
-    centring, perimeter, scaling)."""
-    return int(49 * int(n_in.sum()) + 43 * N * n_in.size)
+    count 1): 46 per input node (chords 8, arc lengths and spline equations
+    with the Thomas elimination 23, two backward sweeps 15) and 42 per output
+    node (evaluation 30, perimeter 8, centring and scaling 4)."""
+    return int(46 * int(n_in.sum()) + 42 * N * n_in.size)
 
 
 def direct_flops_per_pair(N: int) -> int:
@@ -249,8 +249,8 @@ def run_gpu(args):
                                            z.data_ptr(), rst.data_ptr(), ws.data_ptr(), ws_bytes,
                                            sptr))
 
-    def align(method=_lib.FFT):
-        _lib.check(L.fa_align_pairs(h, z1p, z2p, P, N, _lib.Z_F64, method, _lib.PREC_FP64,
+    def align(method=_lib.FFT, prec=_lib.PREC_FP64):
+        _lib.check(L.fa_align_pairs(h, z1p, z2p, P, N, _lib.Z_F64, method, prec,
                                     shift.data_ptr(), theta.data_ptr(), energy.data_ptr(),
                                     ast.data_ptr(), sptr))
 
@@ -306,6 +306,24 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     direct_ms = e0.elapsed_time(e1) / reps
 
+    # FA_PREC_MIXED variant of the alignment step on the same curves (FP32
+    # transforms, FP64 re-score of the shifts FP32 cannot rule out, FP64
+    # theta/energy); also checks it picks the FP64 search's shifts
+    with torch.cuda.stream(stream):
+        align()
+        ref_shift = shift.clone()
+        ref_energy = energy.clone()
+        align(prec=_lib.PREC_MIXED)
+        e0.record(stream)
+        for _ in range(K):
+            align(prec=_lib.PREC_MIXED)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    mixed_ms = e0.elapsed_time(e1) / K
+    same = shift == ref_shift
+    mixed_agree = float(same.double().mean().item())
+    mixed_tie_ok = bool(((energy - ref_energy).abs()[~same] <= 1e-9).all().item())
+
     # FP64 peak measured in this run (denominator of the roofline)
     peak_lib = ctypes.CDLL(str(pbuild.build_probe()))
     peak_lib.fa_probe_fp64_fma_tflops.restype = ctypes.c_double
@@ -351,6 +369,34 @@ def run_gpu(args):
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    # all-pairs alignment matrix: M = 2048 curves at N = 512 (fa_align_all_pairs)
+    allp = None
+    if not args.no_all_pairs:
+        from paper_2501_17779_gb300 import synth
+
+        Ma, Na = 2048, 512
+        ap = synth.aligned_pairs(SEED + 7, P=Ma // 2, N=Na, n_harm=12, oversample=16)
+        za = torch.from_numpy(np.concatenate([ap.z1, ap.z2])).to(dev)
+        with torch.cuda.stream(stream):
+            api.align_all_pairs(za)  # warm-up (allocates outputs and workspace)
+            outs = api.align_all_pairs(za)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            reps = 3
+            for _ in range(reps):
+                api.align_all_pairs(za)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        all_ms = e0.elapsed_time(e1) / reps
+        npairs = Ma * (Ma - 1) // 2
+        fl_all = npairs * (fft_flops(9) + 29 * Na) + Ma * fft_flops(9)
+        allp = {"workload": "2048 curves, N=512, every ordered pair (FP64)",
+                "ms": all_ms, "ordered_pairs_per_s": Ma * (Ma - 1) / (all_ms * 1e-3),
+                "searched_pairs": npairs, "tflops": fl_all / (all_ms * 1e-3) / 1e12,
+                "frac_of_fp64_peak": fl_all / (all_ms * 1e-3) / 1e12 / fp64_peak,
+                "status_ok": bool((outs[3] == 0).all().item())}
+        del za, outs
+
     line = None
     if rank == 0:
         cpu = None
@@ -378,6 +424,13 @@ def run_gpu(args):
                        "fft_align_speedup": direct_ms / al_avg,
                        "end_to_end_speedup": (rs_avg + direct_ms) / (rs_avg + al_avg),
                        "direct_tflops": direct_flops_per_pair(N) * P / (direct_ms * 1e-3) / 1e12},
+            "variants": {"fft_mixed": {
+                "align_ms": mixed_ms, "pairs_per_s": world * P / ((rs_avg + mixed_ms) * 1e-3),
+                "align_speedup_vs_fp64": al_avg / mixed_ms,
+                "align_speedup_vs_direct": direct_ms / mixed_ms,
+                "shift_agreement_with_fp64": mixed_agree, "disagreements_within_tie": mixed_tie_ok,
+                "dtype": "f32 search + f64 re-score/theta/energy"}},
+            "all_pairs": allp,
             "cpu_baseline": cpu,
             "e2e": {"value": world * P / (e2e_ms * 1e-3), "unit": "pairs/s",
                     "h2d_bytes_per_step": int(rp.pts.nbytes + rp.offsets.nbytes),
@@ -403,6 +456,7 @@ def main():
     ap.add_argument("--direct-reps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-all-pairs", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()

@@ -66,8 +66,12 @@ typedef struct fa_handle fa_handle;
 #define FA_FFT 0    /* Algorithm 2 with the convolution theorem: O(N log N)   */
 #define FA_DIRECT 1 /* every shift by its O(N) definition: O(N^2) baseline    */
 
-/* arithmetic of the shift search */
-#define FA_PREC_FP64 0 /* every step in FP64                                   */
+/* arithmetic of the shift search (theta and the energy are always FP64) */
+#define FA_PREC_FP64 0  /* every step in FP64                                  */
+#define FA_PREC_MIXED 1 /* FA_FFT only: the transforms in FP32; every shift whose
+                           FP32 |c(s)| lies within a rigorous error bound of the
+                           maximum is re-scored by its FP64 sum, so the result
+                           obeys the same bounds as FA_PREC_FP64               */
 
 /* Create a handle bound to CUDA device `device` (its twiddle tables are built
  * here, synchronously).  *h receives the handle.  Not thread-safe with
@@ -140,7 +144,7 @@ int fa_resample_arclength(fa_handle* h, const double* pts, const int64_t* offset
  *            any value in [1, 4096] for FA_DIRECT
  *   ztype    FA_Z_F64 | FA_Z_F32
  *   method   FA_FFT | FA_DIRECT
- *   prec     FA_PREC_FP64
+ *   prec     FA_PREC_FP64, or FA_PREC_MIXED with FA_FFT
  *   shift    int32[P]   best shift (-1 when status != 0)
  *   theta    double[P]  CCW angle applied to curve 2 (NaN when status != 0)
  *   energy   double[P]  energy at the optimum (NaN when status != 0)
@@ -149,6 +153,34 @@ int fa_resample_arclength(fa_handle* h, const double* pts, const int64_t* offset
 int fa_align_pairs(fa_handle* h, const void* z1, const void* z2, int64_t P, int32_t N,
                    int32_t ztype, int32_t method, int32_t prec, int32_t* shift, double* theta,
                    double* energy, int8_t* status, void* stream);
+
+/*
+ * All-pairs alignment matrix of M curves (Algorithm 2 for every ordered pair).
+ *
+ * Entry (i, j) is the alignment of curve j onto curve i, i.e. fa_align_pairs
+ * with z1 = curve i and z2 = curve j: shift[i*M + j], theta[i*M + j],
+ * energy[i*M + j].  Each curve's spectrum is computed once into the
+ * workspace; the pairs i < j are searched (one transform per pair) and the
+ * pair (j, i) follows from the symmetry of the energy: shift (N - s) mod N,
+ * angle -theta, the same energy (on exact ties this may differ from a
+ * direct search of (j, i), which would report its own smallest shift).  The
+ * diagonal is shift 0, angle 0, energy 0.
+ *
+ *   z          [M][N] complex128 (FA_Z_F64) or complex64 (FA_Z_F32) (device),
+ *              centred and of unit length
+ *   M          number of curves, in [0, 65536]
+ *   N          nodes per curve, a power of two in [4, 4096]
+ *   prec       FA_PREC_FP64
+ *   shift      int32[M*M], theta double[M*M], energy double[M*M] (device)
+ *   status     int8[M] per-curve status (FA_STATUS_OK or _NONFINITE); rows and
+ *              columns of a non-finite curve get shift -1 and NaN
+ *   workspace  device scratch of fa_align_all_pairs_workspace_size(M, N)
+ *              bytes (M*N*16), 256-byte aligned, or NULL for the handle's
+ */
+size_t fa_align_all_pairs_workspace_size(int64_t M, int32_t N);
+int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_t ztype,
+                       int32_t prec, int32_t* shift, double* theta, double* energy,
+                       int8_t* status, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * End-to-end convenience call on HOST buffers: arc-length resampling of 2P

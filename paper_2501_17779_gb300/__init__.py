@@ -12,7 +12,7 @@ __version__ = "1.0.0"
 
 def __getattr__(name):
     if name in ("align_pairs", "resample_arclength", "align_curves_host", "handle",
-                "resample_workspace_size"):
+                "resample_workspace_size", "align_all_pairs"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

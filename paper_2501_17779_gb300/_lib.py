@@ -30,11 +30,13 @@ Z_F32 = 1
 FFT = 0
 DIRECT = 1
 PREC_FP64 = 0
+PREC_MIXED = 1
 
 EXPORTS = (
     "fa_create", "fa_destroy", "fa_last_error", "fa_version",
     "fa_resample_workspace_size", "fa_resample_arclength", "fa_align_pairs",
     "fa_align_curves_host", "fa_resample_arclength_noalloc",
+    "fa_align_all_pairs_workspace_size", "fa_align_all_pairs",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -82,6 +84,10 @@ def load(build_if_missing: bool = False):
     L.fa_align_pairs.restype = ctypes.c_int
     L.fa_align_curves_host.argtypes = [vp, vp, vp, i64, i32, i32, i32, i32, vp, vp, vp, vp, vp]
     L.fa_align_curves_host.restype = ctypes.c_int
+    L.fa_align_all_pairs_workspace_size.argtypes = [i64, i32]
+    L.fa_align_all_pairs_workspace_size.restype = sz
+    L.fa_align_all_pairs.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, vp, sz, vp]
+    L.fa_align_all_pairs.restype = ctypes.c_int
     L.fa_resample_arclength_noalloc.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp]
     L.fa_resample_arclength_noalloc.restype = ctypes.c_int
     _lib = L

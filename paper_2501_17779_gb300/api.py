@@ -6,6 +6,7 @@ include/fftalign.h:
 
 * ``resample_arclength``  -> fa_resample_arclength
 * ``align_pairs``         -> fa_align_pairs
+* ``align_all_pairs``     -> fa_align_all_pairs
 * ``align_curves_host``   -> fa_align_curves_host (host buffers in and out)
 """
 from __future__ import annotations
@@ -99,7 +100,7 @@ def resample_arclength(pts: torch.Tensor, offsets: torch.Tensor, N_out: int, *,
 
 
 _METHODS = {"fft": _lib.FFT, "direct": _lib.DIRECT}
-_PRECS = {"fp64": _lib.PREC_FP64}
+_PRECS = {"fp64": _lib.PREC_FP64, "mixed": _lib.PREC_MIXED}
 
 
 def align_pairs(z1: torch.Tensor, z2: torch.Tensor, *, method: str = "fft", prec: str = "fp64",
@@ -130,6 +131,36 @@ def align_pairs(z1: torch.Tensor, z2: torch.Tensor, *, method: str = "fft", prec
     h = handle(dev.index)
     rc = L.fa_align_pairs(h, _ptr(z1), _ptr(z2), P, N, ztype, _METHODS[method], _PRECS[prec],
                           _ptr(shift), _ptr(theta), _ptr(energy), _ptr(status), _stream_ptr(dev))
+    _lib.check(rc)
+    return shift, theta, energy, status
+
+
+def align_all_pairs(z: torch.Tensor, *, prec: str = "fp64", workspace: torch.Tensor | None = None):
+    """Alignment matrix of M curves (fa_align_all_pairs).
+
+    z: [M, N] complex128 or complex64 CUDA tensor.  Returns (shift int32 [M, M],
+    theta float64 [M, M], energy float64 [M, M], status int8 [M]); entry
+    (i, j) aligns curve j onto curve i.
+    """
+    if z.dtype not in (torch.complex128, torch.complex64):
+        raise ValueError("z must be complex128 or complex64")
+    _need_cuda("z", z, z.dtype)
+    if z.dim() != 2:
+        raise ValueError("z must be [M, N]")
+    M, N = z.shape
+    dev = z.device
+    shift = torch.empty((M, M), dtype=torch.int32, device=dev)
+    theta = torch.empty((M, M), dtype=torch.float64, device=dev)
+    energy = torch.empty((M, M), dtype=torch.float64, device=dev)
+    status = torch.empty(M, dtype=torch.int8, device=dev)
+    L = _lib.load()
+    need = int(L.fa_align_all_pairs_workspace_size(M, N))
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    ztype = _lib.Z_F64 if z.dtype == torch.complex128 else _lib.Z_F32
+    rc = L.fa_align_all_pairs(handle(dev.index), _ptr(z), M, N, ztype, _PRECS[prec], _ptr(shift),
+                              _ptr(theta), _ptr(energy), _ptr(status), _ptr(workspace),
+                              workspace.numel(), _stream_ptr(dev))
     _lib.check(rc)
     return shift, theta, energy, status
 

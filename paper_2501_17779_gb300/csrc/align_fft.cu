@@ -20,256 +20,15 @@
 // arithmetic and the argmax compare are integer, and block reductions run
 // their FP64 adds on one warp only.
 #include "fa_internal.cuh"
+#include "align_common.cuh"
+#include "fft_stages.cuh"
 
 namespace fa {
 namespace {
 
-__device__ __forceinline__ void bfly4(double2& v0, double2& v1, double2& v2, double2& v3)
-{
-    const double2 a0 = make_double2(v0.x + v2.x, v0.y + v2.y);
-    const double2 a1 = make_double2(v0.x - v2.x, v0.y - v2.y);
-    const double2 a2 = make_double2(v1.x + v3.x, v1.y + v3.y);
-    const double2 a3 = make_double2(v1.x - v3.x, v1.y - v3.y);
-    v0 = make_double2(a0.x + a2.x, a0.y + a2.y);
-    v2 = make_double2(a0.x - a2.x, a0.y - a2.y);
-    v1 = make_double2(a1.x + a3.y, a1.y - a3.x);  // a1 - i a3
-    v3 = make_double2(a1.x - a3.y, a1.y + a3.x);  // a1 + i a3
-}
-
-// Radix-4 butterfly with twiddles W^e1, W^2e1, W^3e1 on v1, v2, v3, in FMA form:
-// (A, B) = v0 +- w^2 v2, (C, D) = v1 +- w^2 v3, y0/y2 = A +- w C, y1/y3 = B -+ i w D,
-// i.e. four FMA butterflies (24 DFMA) instead of three complex products plus
-// sixteen additions (28 instructions).  -i w = W^(e1 + N/4).
-struct Tw4 {
-    double2 t1, t2, t3;
-    bool f1, f2, f3;
-};
-
-template <int N>
-__device__ __forceinline__ Tw4 load_tw4(const double2* __restrict__ T, int e1)
-{
-    Tw4 w;
-    const int e2 = 2 * e1, e3 = e1 + N / 4;
-    w.t1 = __ldg(T + e1); w.t2 = __ldg(T + e2); w.t3 = __ldg(T + e3);
-    w.f1 = tw_form_b(e1, N); w.f2 = tw_form_b(e2, N); w.f3 = tw_form_b(e3, N);
-    return w;
-}
-
-__device__ __forceinline__ void bfly4_tw(double2& v0, double2& v1, double2& v2, double2& v3,
-                                         const Tw4& w)
-{
-    fbfly(v0, v2, w.t2, w.f2);  // v0 = A, v2 = B
-    fbfly(v1, v3, w.t2, w.f2);  // v1 = C, v3 = D
-    fbfly(v0, v1, w.t1, w.f1);  // v0 = y0, v1 = y2
-    fbfly(v2, v3, w.t3, w.f3);  // v2 = y1, v3 = y3
-    const double2 t = v1;
-    v1 = v2;
-    v2 = t;
-}
-
-template <int LOGN>
-struct Geo {
-    static constexpr int N = 1 << LOGN;
-    static constexpr int Q = N / 4;                   // threads per pair
-    static constexpr int G = Q >= 128 ? 1 : 128 / Q;  // pairs per CTA
-    static constexpr int T = G * Q;                   // threads per CTA
-    static constexpr int W = Q >= 32 ? Q / 32 : 1;    // warps per pair
-};
-
-// Radix-2 stage (Ns = 1) on both buffers: butterflies j = t and j = t + Q.
-template <int LOGN>
-__device__ __forceinline__ void stage2_two(double2* X1, double2* X2, int t)
-{
-    constexpr int N = 1 << LOGN, Q = N / 4, H = N / 2;
-    const double2 a = X1[t], b = X1[t + H], c = X1[t + Q], d = X1[t + Q + H];
-    const double2 e = X2[t], f = X2[t + H], g = X2[t + Q], k = X2[t + Q + H];
-    __syncthreads();
-    X1[2 * t] = make_double2(a.x + b.x, a.y + b.y);
-    X1[2 * t + 1] = make_double2(a.x - b.x, a.y - b.y);
-    X1[2 * (t + Q)] = make_double2(c.x + d.x, c.y + d.y);
-    X1[2 * (t + Q) + 1] = make_double2(c.x - d.x, c.y - d.y);
-    X2[2 * t] = make_double2(e.x + f.x, e.y + f.y);
-    X2[2 * t + 1] = make_double2(e.x - f.x, e.y - f.y);
-    X2[2 * (t + Q)] = make_double2(g.x + k.x, g.y + k.y);
-    X2[2 * (t + Q) + 1] = make_double2(g.x - k.x, g.y - k.y);
-    __syncthreads();
-}
-
-// Radix-4 Stockham stage with sub-transform size NS on both buffers.
-template <int LOGN, int NS>
-__device__ __forceinline__ void stage4_two(double2* X1, double2* X2, int t,
-                                           const double2* __restrict__ W)
-{
-    constexpr int N = 1 << LOGN, Q = N / 4;
-    double2 a0 = X1[t], a1 = X1[t + Q], a2 = X1[t + 2 * Q], a3 = X1[t + 3 * Q];
-    double2 b0 = X2[t], b1 = X2[t + Q], b2 = X2[t + 2 * Q], b3 = X2[t + 3 * Q];
-    const int k = t & (NS - 1);
-    if constexpr (NS > 1) {
-        const Tw4 w = load_tw4<N>(W, k * (N / (4 * NS)));
-        bfly4_tw(a0, a1, a2, a3, w);
-        bfly4_tw(b0, b1, b2, b3, w);
-    } else {
-        bfly4(a0, a1, a2, a3);
-        bfly4(b0, b1, b2, b3);
-    }
-    __syncthreads();
-    const int idx = (t - k) * 4 + k;
-    X1[idx] = a0; X1[idx + NS] = a1; X1[idx + 2 * NS] = a2; X1[idx + 3 * NS] = a3;
-    X2[idx] = b0; X2[idx + NS] = b1; X2[idx + 2 * NS] = b2; X2[idx + 3 * NS] = b3;
-    __syncthreads();
-}
-
-template <int LOGN, int NS>
-__device__ __forceinline__ void fft_two_from(double2* X1, double2* X2, int t,
-                                             const double2* __restrict__ W)
-{
-    if constexpr (NS < (1 << LOGN)) {
-        stage4_two<LOGN, NS>(X1, X2, t, W);
-        fft_two_from<LOGN, NS * 4>(X1, X2, t, W);
-    }
-}
-
-template <int LOGN>
-__device__ __forceinline__ void fft_two(double2* X1, double2* X2, int t,
-                                        const double2* __restrict__ W)
-{
-    if constexpr (LOGN & 1) {
-        stage2_two<LOGN>(X1, X2, t);
-        fft_two_from<LOGN, 2>(X1, X2, t, W);
-    } else {
-        fft_two_from<LOGN, 1>(X1, X2, t, W);
-    }
-}
-
-// Radix-4 stage on X1 alone.  PROD: the inputs are X1 * conj(X2) (the
-// spectrum product).  LAST: outputs stay in registers (y[q] = c at s = t+qQ).
-template <int LOGN, int NS, bool PROD, bool LAST>
-__device__ __forceinline__ void stage4_one(double2* X1, const double2* X2, int t,
-                                           const double2* __restrict__ W, double2 (&y)[4])
-{
-    constexpr int N = 1 << LOGN, Q = N / 4;
-    double2 v0 = X1[t], v1 = X1[t + Q], v2 = X1[t + 2 * Q], v3 = X1[t + 3 * Q];
-    if constexpr (PROD) {
-        v0 = cmulc(v0, X2[t]); v1 = cmulc(v1, X2[t + Q]);
-        v2 = cmulc(v2, X2[t + 2 * Q]); v3 = cmulc(v3, X2[t + 3 * Q]);
-    }
-    const int k = t & (NS - 1);
-    if constexpr (NS > 1)
-        bfly4_tw(v0, v1, v2, v3, load_tw4<N>(W, k * (N / (4 * NS))));
-    else
-        bfly4(v0, v1, v2, v3);
-    if constexpr (LAST) {
-        y[0] = v0; y[1] = v1; y[2] = v2; y[3] = v3;
-    } else {
-        __syncthreads();
-        const int idx = (t - k) * 4 + k;
-        X1[idx] = v0; X1[idx + NS] = v1; X1[idx + 2 * NS] = v2; X1[idx + 3 * NS] = v3;
-        __syncthreads();
-    }
-}
-
-// Radix-2 first stage of the correlation transform, inputs X1 * conj(X2).
-template <int LOGN>
-__device__ __forceinline__ void stage2_prod(double2* X1, const double2* X2, int t)
-{
-    constexpr int N = 1 << LOGN, Q = N / 4, H = N / 2;
-    const double2 a = cmulc(X1[t], X2[t]), b = cmulc(X1[t + H], X2[t + H]);
-    const double2 c = cmulc(X1[t + Q], X2[t + Q]), d = cmulc(X1[t + Q + H], X2[t + Q + H]);
-    __syncthreads();
-    X1[2 * t] = make_double2(a.x + b.x, a.y + b.y);
-    X1[2 * t + 1] = make_double2(a.x - b.x, a.y - b.y);
-    X1[2 * (t + Q)] = make_double2(c.x + d.x, c.y + d.y);
-    X1[2 * (t + Q) + 1] = make_double2(c.x - d.x, c.y - d.y);
-    __syncthreads();
-}
-
-template <int LOGN, int NS>
-__device__ __forceinline__ void fft_one_from(double2* X, int t, const double2* __restrict__ W,
-                                             double2 (&y)[4])
-{
-    constexpr int N = 1 << LOGN;
-    if constexpr (NS * 4 == N) {
-        stage4_one<LOGN, NS, false, true>(X, nullptr, t, W, y);
-    } else {
-        stage4_one<LOGN, NS, false, false>(X, nullptr, t, W, y);
-        fft_one_from<LOGN, NS * 4>(X, t, W, y);
-    }
-}
-
-// y[q] = N c(t + qQ) with c(s) = sum_k z1[k] conj(z2[k+s]), from the spectra in X1, X2.
-template <int LOGN>
-__device__ __forceinline__ void fft_corr(double2* X1, const double2* X2, int t,
-                                         const double2* __restrict__ W, double2 (&y)[4])
-{
-    if constexpr (LOGN & 1) {
-        stage2_prod<LOGN>(X1, X2, t);
-        fft_one_from<LOGN, 2>(X1, t, W, y);
-    } else if constexpr (LOGN == 2) {
-        stage4_one<LOGN, 1, true, true>(X1, X2, t, W, y);
-    } else {
-        stage4_one<LOGN, 1, true, false>(X1, X2, t, W, y);
-        fft_one_from<LOGN, 4>(X1, t, W, y);
-    }
-}
-
-// Group-wide argmax of (key, idx); every thread of the group gets the result.
-template <int Q>
-__device__ __forceinline__ void group_argmax(long long& key, int& idx, long long* sk, int* si,
-                                             int g, int t)
-{
-    constexpr int WID = Q < 32 ? Q : 32;
-#pragma unroll
-    for (int off = WID / 2; off > 0; off >>= 1) {
-        const long long k2 = __shfl_xor_sync(0xffffffffu, key, off);
-        const int i2 = __shfl_xor_sync(0xffffffffu, idx, off);
-        if (key_better(k2, i2, key, idx)) { key = k2; idx = i2; }
-    }
-    if constexpr (Q > 32) {
-        constexpr int W = Q / 32;
-        if ((t & 31) == 0) { sk[g * W + (t >> 5)] = key; si[g * W + (t >> 5)] = idx; }
-        __syncthreads();
-        key = sk[g * W];
-        idx = si[g * W];
-#pragma unroll
-        for (int i = 1; i < W; ++i)
-            if (key_better(sk[g * W + i], si[g * W + i], key, idx)) {
-                key = sk[g * W + i];
-                idx = si[g * W + i];
-            }
-        __syncthreads();
-    }
-}
-
-// Group-wide sum of a double2: partials go to shared memory and the first
-// warp of the group adds them (FP64 adds on one warp only).  Result in out
-// (shared), valid after the trailing __syncthreads.
-template <int Q>
-__device__ __forceinline__ void group_sum(double2 v, double2* part, double2* out, int g, int t)
-{
-    part[t] = v;
-    __syncthreads();
-    if constexpr (Q <= 32) {
-        if (t == 0) {
-            double2 s = part[0];
-            for (int i = 1; i < Q; ++i) { s.x += part[i].x; s.y += part[i].y; }
-            out[g] = s;
-        }
-    } else {
-        if (t < 32) {
-            double2 s = part[t];
-            for (int i = t + 32; i < Q; i += 32) { s.x += part[i].x; s.y += part[i].y; }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
-                s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
-            }
-            if (t == 0) out[g] = s;
-        }
-    }
-    __syncthreads();
-}
-
-template <int LOGN, typename ZT>
+// RETRY: only pairs whose status is kStatusRetryFP64 (left by the mixed-
+// precision search) are processed; CTAs with none of them return at once.
+template <int LOGN, typename ZT, bool RETRY>
 __global__ void __launch_bounds__(Geo<LOGN>::T)
     align_fft_kernel(const ZT* __restrict__ z1, const ZT* __restrict__ z2, int64_t P,
                      const double2* __restrict__ W, int32_t* __restrict__ shift,
@@ -289,10 +48,15 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
 
     const int g = threadIdx.x / Q;
     const int t = threadIdx.x % Q;
-    const int64_t pair = (int64_t)blockIdx.x * G + g;
-    const bool valid = pair < P;
-    const ZT* p1 = z1 + (valid ? pair : 0) * N;
-    const ZT* p2 = z2 + (valid ? pair : 0) * N;
+    const int64_t pair0 = (int64_t)blockIdx.x * G + g;
+    bool valid = pair0 < P;
+    if constexpr (RETRY) {
+        valid = valid && status[pair0] == kStatusRetryFP64;
+        if (!__syncthreads_or(valid)) return;  // CTA-uniform
+    }
+    const int64_t pair = pair0;
+    const ZT* p1 = z1 + (pair0 < P ? pair : 0) * N;
+    const ZT* p2 = z2 + (pair0 < P ? pair : 0) * N;
 
     if (t == 0) bad[g] = 0;
     __syncthreads();
@@ -369,7 +133,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     }
 }
 
-template <int LOGN, typename ZT>
+template <int LOGN, typename ZT, bool RETRY = false>
 int launch_one(const fa_handle* h, const void* z1, const void* z2, int64_t P, int32_t* shift,
                double* theta, double* energy, int8_t* status, cudaStream_t st)
 {
@@ -377,7 +141,7 @@ int launch_one(const fa_handle* h, const void* z1, const void* z2, int64_t P, in
     const size_t smem = (size_t)Gm::G * 2 * Gm::N * sizeof(double2) + 2 * Gm::G * sizeof(double2) +
                         (size_t)Gm::G * Gm::W * (sizeof(long long) + sizeof(int)) +
                         Gm::G * sizeof(int);
-    auto kern = align_fft_kernel<LOGN, ZT>;
+    auto kern = align_fft_kernel<LOGN, ZT, RETRY>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -390,13 +154,13 @@ int launch_one(const fa_handle* h, const void* z1, const void* z2, int64_t P, in
     return cuda_error(cudaGetLastError(), "align_fft launch");
 }
 
-template <typename ZT>
+template <typename ZT, bool RETRY>
 int dispatch(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
              int32_t* shift, double* theta, double* energy, int8_t* status, cudaStream_t st)
 {
     switch (logn) {
 #define FA_CASE(L) \
-    case L: return launch_one<L, ZT>(h, z1, z2, P, shift, theta, energy, status, st);
+    case L: return launch_one<L, ZT, RETRY>(h, z1, z2, P, shift, theta, energy, status, st);
         FA_CASE(2) FA_CASE(3) FA_CASE(4) FA_CASE(5) FA_CASE(6) FA_CASE(7) FA_CASE(8) FA_CASE(9)
         FA_CASE(10) FA_CASE(11) FA_CASE(12)
 #undef FA_CASE
@@ -412,8 +176,18 @@ int launch_align_fft(const fa_handle* h, const void* z1, const void* z2, int64_t
 {
     if (P == 0) return FA_OK;
     if (ztype == FA_Z_F64)
-        return dispatch<double2>(h, z1, z2, P, logn, shift, theta, energy, status, st);
-    return dispatch<float2>(h, z1, z2, P, logn, shift, theta, energy, status, st);
+        return dispatch<double2, false>(h, z1, z2, P, logn, shift, theta, energy, status, st);
+    return dispatch<float2, false>(h, z1, z2, P, logn, shift, theta, energy, status, st);
+}
+
+int launch_align_fft_retry(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
+                           int ztype, int32_t* shift, double* theta, double* energy,
+                           int8_t* status, cudaStream_t st)
+{
+    if (P == 0) return FA_OK;
+    if (ztype == FA_Z_F64)
+        return dispatch<double2, true>(h, z1, z2, P, logn, shift, theta, energy, status, st);
+    return dispatch<float2, true>(h, z1, z2, P, logn, shift, theta, energy, status, st);
 }
 
 }  // namespace fa

@@ -37,14 +37,16 @@ __global__ void twiddle_kernel(double2* w64, float2* w32, int N)
 }
 
 // FMA-form twiddles (m, rho) for e in [0, N/2): W = m (1 + i rho) or m (rho + i).
-__global__ void fma_twiddle_kernel(double2* tf, int N)
+__global__ void fma_twiddle_kernel(double2* tf, float2* tf32, int N)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N / 2) return;
     double s, c;
     sincospi(2.0 * (double)e / (double)N, &s, &c);
     const double wr = c, wi = -s;
-    tf[e] = tw_form_b(e, N) ? make_double2(wi, wr / wi) : make_double2(wr, wi / wr);
+    const double2 v = tw_form_b(e, N) ? make_double2(wi, wr / wi) : make_double2(wr, wi / wr);
+    tf[e] = v;
+    tf32[e] = make_float2((float)v.x, (float)v.y);
 }
 
 int build_twiddles(fa_handle* h)
@@ -57,7 +59,9 @@ int build_twiddles(fa_handle* h)
         if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
         e = cudaMalloc(&h->tf64[L], (N / 2) * sizeof(double2));
         if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
-        fma_twiddle_kernel<<<(N / 2 + 255) / 256, 256>>>(h->tf64[L], N);
+        e = cudaMalloc(&h->tf32[L], (N / 2) * sizeof(float2));
+        if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
+        fma_twiddle_kernel<<<(N / 2 + 255) / 256, 256>>>(h->tf64[L], h->tf32[L], N);
         twiddle_kernel<<<(N + 255) / 256, 256>>>(h->tw64[L], h->tw32[L], N);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(e, "fa_create: twiddle kernel");
@@ -158,6 +162,7 @@ int fa_destroy(fa_handle* h)
         if (h->tw64[L]) cudaFree(h->tw64[L]);
         if (h->tw32[L]) cudaFree(h->tw32[L]);
         if (h->tf64[L]) cudaFree(h->tf64[L]);
+        if (h->tf32[L]) cudaFree(h->tf32[L]);
     }
     if (h->ws) cudaFree(h->ws);
     delete h;
@@ -214,8 +219,10 @@ int fa_align_pairs(fa_handle* h, const void* z1, const void* z2, int64_t P, int3
         return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs: unknown ztype");
     if (method != FA_FFT && method != FA_DIRECT)
         return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs: unknown method");
-    if (prec != FA_PREC_FP64)
+    if (prec != FA_PREC_FP64 && prec != FA_PREC_MIXED)
         return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs: unknown precision");
+    if (prec == FA_PREC_MIXED && method != FA_FFT)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs: FA_PREC_MIXED needs FA_FFT");
     int logn = -1;
     if (method == FA_FFT) {
         for (int L = kMinLogN; L <= kMaxLogN; ++L)
@@ -234,9 +241,56 @@ int fa_align_pairs(fa_handle* h, const void* z1, const void* z2, int64_t P, int3
     DeviceGuard g(h->device);
     if (g.rc != FA_OK) return g.rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (method == FA_FFT && prec == FA_PREC_MIXED)
+        return launch_align_mixed(h, z1, z2, P, logn, ztype, shift, theta, energy, status, st);
     if (method == FA_FFT)
         return launch_align_fft(h, z1, z2, P, logn, ztype, shift, theta, energy, status, st);
     return launch_align_direct(h, z1, z2, P, N, ztype, shift, theta, energy, status, st);
+}
+
+size_t fa_align_all_pairs_workspace_size(int64_t M, int32_t N)
+{
+    if (M < 0 || N <= 0) return 0;
+    return align_all_ws_bytes(M, N);
+}
+
+int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_t ztype,
+                       int32_t prec, int32_t* shift, double* theta, double* energy,
+                       int8_t* status, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: null handle");
+    if (M < 0) return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: negative curve count");
+    if (ztype != FA_Z_F64 && ztype != FA_Z_F32)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: unknown ztype");
+    if (prec != FA_PREC_FP64)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: unknown precision");
+    int logn = -1;
+    for (int L = kMinLogN; L <= kMaxLogN; ++L)
+        if (N == (1 << L)) logn = L;
+    if (logn < 0)
+        return set_error(FA_ERR_UNSUPPORTED,
+                         "fa_align_all_pairs: N must be a power of two in [4, 4096]");
+    if (M == 0) return FA_OK;
+    if (M > (1 << 16))
+        return set_error(FA_ERR_UNSUPPORTED, "fa_align_all_pairs: more than 65536 curves");
+    if (!z || !shift || !theta || !energy || !status)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: null pointer");
+    const size_t need = align_all_ws_bytes(M, N);
+    DeviceGuard g(h->device);
+    if (g.rc != FA_OK) return g.rc;
+    void* ws = workspace;
+    if (ws) {
+        if (workspace_bytes < need)
+            return set_error(FA_ERR_WORKSPACE, "fa_align_all_pairs: workspace too small");
+        if (reinterpret_cast<uintptr_t>(ws) & 255)
+            return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: workspace not 256-aligned");
+    } else {
+        const int rc = ensure_ws(h, need);
+        if (rc != FA_OK) return rc;
+        ws = h->ws;
+    }
+    return launch_align_all(h, z, M, logn, ztype, ws, status, shift, theta, energy,
+                            static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

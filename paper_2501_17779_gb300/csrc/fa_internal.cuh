@@ -18,6 +18,7 @@ struct fa_handle {
     // FMA-form twiddles for e in [0, N/2): (m, rho) with W_N^e = m (1 + i rho) when
     // |cos| >= |sin| (e <= N/8 or e >= 3N/8), else W_N^e = m (rho + i); |rho| <= 1
     double2* tf64[13] = {};
+    float2* tf32[13] = {};  // the same in FP32 (FA_PREC_MIXED search)
     // handle-owned scratch, used when the caller passes no workspace
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -62,21 +63,6 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b)
 // Which form a FMA twiddle W_N^e (0 <= e < N/2) is stored in (see fa_handle::tf64).
 __host__ __device__ __forceinline__ bool tw_form_b(int e, int N) { return 8 * e > N && 8 * e < 3 * N; }
 
-// (a, b) <- (a + w b, a - w b) with w = (m, rho) in FMA form: 6 DFMA, no other FP64
-// instruction (the form selects operands and flips a sign bit with integer ops).
-__device__ __forceinline__ void fbfly(double2& a, double2& b, double2 t, bool fb)
-{
-    const double m = t.x, rho = t.y;
-    const double U = fb ? b.x : b.y;
-    const double V = fb ? b.y : b.x;
-    const double tx = fma(-rho, U, V);
-    const double ty = fma(rho, V, U);
-    const double mx =
-        __longlong_as_double(__double_as_longlong(m) ^ ((unsigned long long)fb << 63));
-    b = make_double2(fma(-mx, tx, a.x), fma(-m, ty, a.y));
-    a = make_double2(fma(mx, tx, a.x), fma(m, ty, a.y));
-}
-
 // argmax key order: larger |c|^2 first, then the smaller shift.  |c|^2 >= 0,
 // so its IEEE bit pattern orders like the value (integer compare).
 __device__ __forceinline__ bool key_better(long long ka, int ia, long long kb, int ib)
@@ -88,9 +74,21 @@ __device__ __forceinline__ bool key_better(long long ka, int ia, long long kb, i
 int launch_align_fft(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
                      int ztype, int32_t* shift, double* theta, double* energy, int8_t* status,
                      cudaStream_t st);
+// internal status: the mixed-precision search leaves the pair to the FP64 kernel
+constexpr int8_t kStatusRetryFP64 = 100;
+int launch_align_fft_retry(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
+                           int ztype, int32_t* shift, double* theta, double* energy,
+                           int8_t* status, cudaStream_t st);
+int launch_align_mixed(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
+                       int ztype, int32_t* shift, double* theta, double* energy, int8_t* status,
+                       cudaStream_t st);
 int launch_align_direct(const fa_handle* h, const void* z1, const void* z2, int64_t P, int N,
                         int ztype, int32_t* shift, double* theta, double* energy, int8_t* status,
                         cudaStream_t st);
+size_t align_all_ws_bytes(int64_t M, int N);
+int launch_align_all(const fa_handle* h, const void* z, int64_t M, int logn, int ztype, void* ws,
+                     int8_t* status, int32_t* shift, double* theta, double* energy,
+                     cudaStream_t st);
 int launch_resample(const fa_handle* h, const double* pts, const int64_t* offsets, int64_t C,
                     int64_t n_pts, int N_out, int flags, void* z_out, int8_t* status, void* ws,
                     cudaStream_t st);

@@ -6,10 +6,13 @@
 //   A. chord lengths d_l = |p_{l+1} - p_l| and their sum per chunk; a warp scan
 //      gives each chunk's starting arc length and the perimeter L.
 //   B. forward sweep over each chunk's interior nodes (all but its last):
-//      knots u_l, the periodic-spline equations
+//      cumulative arc lengths S_l = L u_l, the periodic-spline equations
 //          h_{l-1} M_{l-1} + 2(h_{l-1}+h_l) M_l + h_l M_{l+1}
 //              = 6[(p_{l+1}-p_l)/h_l - (p_l-p_{l-1})/h_{l-1}],   h_l = d_l / L,
-//      and the Thomas elimination of the interior with the chunk's two
+//      multiplied through by L so that they read
+//          d_{l-1} M_{l-1} + 2(d_{l-1}+d_l) M_l + d_l M_{l+1} = 6 L^2 (tau_l - tau_{l-1})
+//      with the unit chord directions tau_l = (p_{l+1}-p_l)/d_l (same M, fewer
+//      FP64 instructions), and the Thomas elimination of the interior with the chunk's two
 //      neighbouring interface nodes (the last node of the previous chunk and
 //      of this chunk) kept as unknowns: M_i = y_i - I_{j-1} g_i - I_j k_i.
 //   C. a backward sweep without stores gives y, g, k at the first interior
@@ -30,10 +33,15 @@ namespace {
 
 constexpr int kWarps = 4;  // curves per CTA
 
+// minimum resident CTAs per SM requested from the compiler (register cap)
+#ifndef FA_RESAMPLE_MIN_BLOCKS
+#define FA_RESAMPLE_MIN_BLOCKS 1
+#endif
+
 struct Ws {
-    double* U;     // knots u_l                         [n_pts]
+    double* U;     // cumulative arc length S_l = L u_l [n_pts]
     double* D;     // chord lengths d_l                 [n_pts]
-    double* IH;    // 1/h_l = L/d_l                     [n_pts]
+    double* IH;    // 1/d_l                             [n_pts]
     double2* F0;   // forward sweep (c'_l, g'_l)        [n_pts]
     double2* F1;   // forward sweep y'_l (x, y)         [n_pts]
     double2* M;    // spline second derivatives M_l     [n_pts]
@@ -71,7 +79,7 @@ __device__ void fill_nan(void* zout, int64_t base, int Nout, int lane)
 }
 
 template <bool F32OUT>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
     resample_kernel(const double2* __restrict__ pts, const int64_t* __restrict__ offsets,
                     int64_t C, int Nout, int flags, void* __restrict__ zout,
                     int8_t* __restrict__ status, Ws ws)
@@ -134,7 +142,7 @@ __global__ void __launch_bounds__(kWarps * 32)
             const double d = pos ? q * rs : 0.0;
             zero |= !pos;
             D[l] = d;
-            IH[l] = rs;  // becomes L/d = 1/h in the forward sweep
+            IH[l] = rs;
             csum += d;
             pl = pn;
         }
@@ -152,7 +160,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
     const double L = __shfl_sync(0xffffffffu, incl, 31);
     const double base = incl - csum;  // arc length before node s_j
-    const double invL = 1.0 / L;
+    const double L6sq = 6.0 * L * L;
     __syncwarp();
 
     // ---- B: forward sweep over the interior ---------------------------------
@@ -162,24 +170,19 @@ __global__ void __launch_bounds__(kWarps * 32)
     double gL = 0, kL = 0;
     if (act) {
         const int lp = (sj == 0) ? n - 1 : sj - 1;
-        double hprev = D[lp] * invL;
+        double hprev = D[lp];
         double2 pcur = __ldg(p + sj);
-        // (IH[lp] belongs to the previous lane, which rescales it concurrently;
-        //  one division per chunk avoids reading it)
-        double2 gprev = scl2(sub2(pcur, __ldg(p + lp)), L / D[lp]);
+        double2 tprev = scl2(sub2(pcur, __ldg(p + lp)), IH[lp]);
         double S = base;
         double cp = 0, gp = 0;
         double2 yp = d2(0, 0);
         for (int i = sj; i < ej; ++i) {
-            const double d = D[i];
-            const double h = d * invL;
-            const double ih = L * IH[i];
-            IH[i] = ih;
-            U[i] = S * invL;
-            S += d;
+            const double h = D[i];
+            U[i] = S;
+            S += h;
             const double2 pn = __ldg(p + i + 1);  // i + 1 <= ej < n
-            const double2 g = scl2(sub2(pn, pcur), ih);
-            const double2 R = scl2(sub2(g, gprev), 6.0);
+            const double2 tau = scl2(sub2(pn, pcur), IH[i]);
+            const double2 R = scl2(sub2(tau, tprev), L6sq);
             const double B = 2.0 * (hprev + h);
             const bool first = (i == sj);
             const double den = first ? B : fma(-hprev, cp, B);
@@ -191,19 +194,16 @@ __global__ void __launch_bounds__(kWarps * 32)
             F0[i] = d2(ncp, ngp);
             F1[i] = nyp;
             cp = ncp; gp = ngp; yp = nyp;
-            hprev = h; gprev = g; pcur = pn;
+            hprev = h; tprev = tau; pcur = pn;
         }
         // last interior node's values: M_L = y'_L - I_{j-1} g'_L - I_j c'_L
         yL = yp; gL = gp; kL = cp;
         // interface node e_j
-        const double d = D[ej];
-        const double h = d * invL;
-        const double ih = L * IH[ej];
-        IH[ej] = ih;
-        U[ej] = S * invL;
+        const double h = D[ej];
+        U[ej] = S;
         const int en = (ej + 1 == n) ? 0 : ej + 1;
-        const double2 g = scl2(sub2(__ldg(p + en), pcur), ih);
-        Re = scl2(sub2(g, gprev), 6.0);
+        const double2 tau = scl2(sub2(__ldg(p + en), pcur), IH[ej]);
+        Re = scl2(sub2(tau, tprev), L6sq);
         Ae = hprev;
         Ce = h;
         Be = 2.0 * (hprev + h);
@@ -276,32 +276,36 @@ __global__ void __launch_bounds__(kWarps * 32)
     // ---- E: evaluation at t_k = k / N_out ------------------------------------
     const bool pow2 = (Nout & (Nout - 1)) == 0;
     const double invN = 1.0 / (double)Nout;
+    const double LN = L * invN;                  // arc length per output step
+    const double c6 = 1.0 / L6sq;                // h^2/6 = d^2 / (6 L^2)
     const int per = (Nout + 31) / 32;
     const int k0 = lane * per;
     const int k1 = min(k0 + per, Nout);
     double2* raw = F32OUT ? (ws.Z + zbase) : (static_cast<double2*>(zout) + zbase);
     double2 ssum = d2(0, 0);
     if (k0 < k1) {
-        const double t0 = pow2 ? k0 * invN : (double)k0 / (double)Nout;
-        const long long tb0 = __double_as_longlong(t0);
-        // last l with u_l <= t0 (u_0 = 0 <= t0); knots are >= 0 so their bits order like values
+        // arc-length target of output k: L t_k with t_k = k / N_out
+        const double s0 = pow2 ? k0 * LN : L * ((double)k0 / (double)Nout);
+        const long long sb0 = __double_as_longlong(s0);
+        // last l with S_l <= L t (S_0 = 0); arc lengths are >= 0, so their bits
+        // order like their values
         int lo = 0, hi = n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (__double_as_longlong(U[mid]) <= tb0) lo = mid; else hi = mid - 1;
+            if (__double_as_longlong(U[mid]) <= sb0) lo = mid; else hi = mid - 1;
         }
         int l = lo;
         for (int k = k0; k < k1; ++k) {
-            const double t = pow2 ? k * invN : (double)k / (double)Nout;
-            const long long tb = __double_as_longlong(t);
-            while (l + 1 < n && __double_as_longlong(U[l + 1]) <= tb) ++l;
+            const double st = pow2 ? k * LN : L * ((double)k / (double)Nout);
+            const long long sb = __double_as_longlong(st);
+            while (l + 1 < n && __double_as_longlong(U[l + 1]) <= sb) ++l;
             const int ln = (l + 1 == n) ? 0 : l + 1;
             const double2 pl = __ldg(p + l), pn = __ldg(p + ln);
             const double2 Ml = M[l], Mn = M[ln];
-            const double h = D[l] * invL;
-            const double b = (t - U[l]) * IH[l];
+            const double d = D[l];
+            const double b = (st - U[l]) * IH[l];  // (t - u_l) / h_l
             const double a = 1.0 - b;
-            const double h6 = h * h * (1.0 / 6.0);
+            const double h6 = d * d * c6;
             const double ca = a * fma(a, a, -1.0) * h6;
             const double cb = b * fma(b, b, -1.0) * h6;
             const double2 S = d2(fma(ca, Ml.x, fma(cb, Mn.x, fma(b, pn.x - pl.x, pl.x))),
