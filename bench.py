@@ -78,6 +78,25 @@ def resample_flops(n_in: np.ndarray, N: int) -> int:
     return int(46 * int(n_in.sum()) + 42 * N * n_in.size)
 
 
+def ragged_flops(sizes: np.ndarray) -> int:
+    """FP64 flops of fa_align_pairs_ragged: per pair with transform length L =
+    R B (B <= 4096): 3R transforms of length B, the spectrum product (6 per
+    bin), the radix-R input stage and output recombination (complex products
+    for R > 1), |c|^2, c(s*) and the energy over the n nodes."""
+    tot = 0
+    for n in np.asarray(sizes, np.int64):
+        n = int(n)
+        L = n if n & (n - 1) == 0 else 1 << (2 * n - 1).bit_length()
+        B = min(L, 4096)
+        R = L // B
+        logb = B.bit_length() - 1
+        tot += 3 * R * fft_flops(logb) + 6 * L
+        if R > 1:
+            tot += 2 * (R - 1) * B * 6 + (R - 1) * 8 * n
+        tot += 3 * n + 8 * n + 12 * n
+    return tot
+
+
 def direct_flops_per_pair(N: int) -> int:
     return 8 * N * N + 3 * N + 12 * N
 
@@ -397,6 +416,51 @@ def run_gpu(args):
                 "status_ok": bool((outs[3] == 0).all().item())}
         del za, outs
 
+    # uneven batch: 100,000 pairs, n log-uniform in [64, 8192] (multiples of
+    # 16), one persistent launch, autotuned CTA size, replayed as a CUDA graph
+    rag = None
+    if not args.no_ragged:
+        from paper_2501_17779_gb300 import synth
+
+        sizes = synth.log_uniform_sizes(SEED + 11, args.ragged_pairs)
+        rz1, rz2, roffs = synth.ragged_pairs_device(SEED + 11, sizes, dev)
+        Pr = roffs.numel() - 1
+        rws = torch.empty(api.ragged_workspace_size(Pr, 8192, local), dtype=torch.uint8, device=dev)
+        rout = (torch.empty(Pr, dtype=torch.int32, device=dev),
+                torch.empty(Pr, dtype=torch.float64, device=dev),
+                torch.empty(Pr, dtype=torch.float64, device=dev),
+                torch.empty(Pr, dtype=torch.int8, device=dev))
+        with torch.cuda.stream(stream):
+            api.align_pairs_ragged(rz1, rz2, roffs, max_n=8192, workspace=rws, out=rout,
+                                   autotune=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(3):
+                api.align_pairs_ragged(rz1, rz2, roffs, max_n=8192, workspace=rws, out=rout)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        rag_ms = e0.elapsed_time(e1) / 3
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            api.align_pairs_ragged(rz1, rz2, roffs, max_n=8192, workspace=rws, out=rout)
+        with torch.cuda.stream(stream):
+            graph.replay()
+            e0.record(stream)
+            for _ in range(3):
+                graph.replay()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        rag_graph_ms = e0.elapsed_time(e1) / 3
+        fl_rag = ragged_flops(sizes)
+        rag = {"workload": f"{Pr} pairs, n log-uniform in [64, 8192] (multiples of 16), 4..32 "
+                           "harmonics, FP64, one persistent launch",
+               "ms": rag_ms, "graph_ms": rag_graph_ms, "pairs_per_s": Pr / (rag_graph_ms * 1e-3),
+               "nodes": int(np.asarray(sizes).sum()),
+               "tflops": fl_rag / (rag_graph_ms * 1e-3) / 1e12,
+               "frac_of_fp64_peak": fl_rag / (rag_graph_ms * 1e-3) / 1e12 / fp64_peak,
+               "status_ok": bool((rout[3] == 0).all().item())}
+        del rz1, rz2, roffs, rws, rout, graph
+
     line = None
     if rank == 0:
         cpu = None
@@ -431,6 +495,7 @@ def run_gpu(args):
                 "shift_agreement_with_fp64": mixed_agree, "disagreements_within_tie": mixed_tie_ok,
                 "dtype": "f32 search + f64 re-score/theta/energy"}},
             "all_pairs": allp,
+            "ragged": rag,
             "cpu_baseline": cpu,
             "e2e": {"value": world * P / (e2e_ms * 1e-3), "unit": "pairs/s",
                     "h2d_bytes_per_step": int(rp.pts.nbytes + rp.offsets.nbytes),
@@ -457,6 +522,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-all-pairs", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true")
+    ap.add_argument("--ragged-pairs", type=int, default=100_000)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()

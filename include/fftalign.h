@@ -52,6 +52,7 @@ typedef struct fa_handle fa_handle;
 #define FA_STATUS_DEGENERATE 1 /* fewer than 4 nodes, a zero-length segment,
                                   zero perimeter                               */
 #define FA_STATUS_NONFINITE 2  /* a NaN or Inf coordinate in the input        */
+#define FA_STATUS_BAD_SIZE 3   /* node count outside the supported range       */
 
 /* resampling flags */
 #define FA_CENTER 1      /* subtract the mean of the N resampled nodes         */
@@ -181,6 +182,51 @@ size_t fa_align_all_pairs_workspace_size(int64_t M, int32_t N);
 int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_t ztype,
                        int32_t prec, int32_t* shift, double* theta, double* energy,
                        int8_t* status, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Alignment of P pairs with DIFFERENT node counts in one persistent launch.
+ *
+ * Pair p is z1[offsets[p] .. offsets[p+1]) and z2[offsets[p] .. offsets[p+1])
+ * (n_p nodes each, same CSR offsets for both curves), otherwise as in
+ * fa_align_pairs.  Any n_p in [4, max_n] is supported (max_n <= 8192): for a
+ * power of two the transforms have length n_p; otherwise the cyclic
+ * correlation is computed exactly as a zero-padded linear correlation with
+ * transforms of length L = the power of two >= 2 n_p (no chirps, no
+ * approximation).  The pairs are sorted on the device by transform length
+ * (longest first) and processed by persistent CTAs that take pairs from a
+ * shared counter.  Every step is a launch or memset on `stream`, so the call
+ * can be captured into a CUDA graph (pass a workspace then, so that nothing
+ * is allocated).
+ *
+ *   z1, z2     complex128 (FA_Z_F64) or complex64 (FA_Z_F32) arrays of
+ *              offsets[P] points (device), each curve centred, unit length
+ *   offsets    int64[P+1] non-decreasing CSR offsets (device)
+ *   max_n      upper bound on every n_p, in [4, 8192]; sizes the workspace;
+ *              pairs with n_p < 4 or n_p > max_n get FA_STATUS_BAD_SIZE
+ *   shift, theta, energy, status   as in fa_align_pairs ([P] each, device)
+ *   workspace  fa_align_pairs_ragged_workspace_size(h, P, max_n) bytes,
+ *              256-byte aligned, or NULL for the handle's buffer
+ */
+size_t fa_align_pairs_ragged_workspace_size(fa_handle* h, int64_t P, int32_t max_n);
+int fa_align_pairs_ragged(fa_handle* h, const void* z1, const void* z2, const int64_t* offsets,
+                          int64_t P, int32_t max_n, int32_t ztype, int32_t* shift, double* theta,
+                          double* energy, int8_t* status, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/*
+ * Autotuner of fa_align_pairs_ragged: runs the caller's batch with each CTA
+ * size of the persistent kernel (256, 512, 1024 threads), three timed runs
+ * each, keeps the fastest in the handle for later calls and returns it in
+ * *chosen_threads.  Same arguments and outputs as fa_align_pairs_ragged (the
+ * outputs hold the chosen configuration's result afterwards; different CTA
+ * sizes sum in a different order and may differ in the last bit).
+ * Synchronises the stream; not for use during stream capture.
+ */
+int fa_align_pairs_ragged_autotune(fa_handle* h, const void* z1, const void* z2,
+                                   const int64_t* offsets, int64_t P, int32_t max_n,
+                                   int32_t ztype, int32_t* shift, double* theta, double* energy,
+                                   int8_t* status, void* workspace, size_t workspace_bytes,
+                                   void* stream, int32_t* chosen_threads);
 
 /*
  * End-to-end convenience call on HOST buffers: arc-length resampling of 2P

@@ -37,7 +37,10 @@ EXPORTS = (
     "fa_resample_workspace_size", "fa_resample_arclength", "fa_align_pairs",
     "fa_align_curves_host", "fa_resample_arclength_noalloc",
     "fa_align_all_pairs_workspace_size", "fa_align_all_pairs",
+    "fa_align_pairs_ragged_workspace_size", "fa_align_pairs_ragged",
+    "fa_align_pairs_ragged_autotune",
 )
+STATUS_BAD_SIZE = 3
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
@@ -88,6 +91,13 @@ def load(build_if_missing: bool = False):
     L.fa_align_all_pairs_workspace_size.restype = sz
     L.fa_align_all_pairs.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, vp, sz, vp]
     L.fa_align_all_pairs.restype = ctypes.c_int
+    L.fa_align_pairs_ragged_workspace_size.argtypes = [vp, i64, i32]
+    L.fa_align_pairs_ragged_workspace_size.restype = sz
+    L.fa_align_pairs_ragged.argtypes = [vp, vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, sz, vp]
+    L.fa_align_pairs_ragged.restype = ctypes.c_int
+    L.fa_align_pairs_ragged_autotune.argtypes = [vp, vp, vp, vp, i64, i32, i32, vp, vp, vp, vp,
+                                                 vp, sz, vp, vp]
+    L.fa_align_pairs_ragged_autotune.restype = ctypes.c_int
     L.fa_resample_arclength_noalloc.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp]
     L.fa_resample_arclength_noalloc.restype = ctypes.c_int
     _lib = L

@@ -7,6 +7,7 @@ include/fftalign.h:
 * ``resample_arclength``  -> fa_resample_arclength
 * ``align_pairs``         -> fa_align_pairs
 * ``align_all_pairs``     -> fa_align_all_pairs
+* ``align_pairs_ragged``  -> fa_align_pairs_ragged (+ _autotune)
 * ``align_curves_host``   -> fa_align_curves_host (host buffers in and out)
 """
 from __future__ import annotations
@@ -163,6 +164,56 @@ def align_all_pairs(z: torch.Tensor, *, prec: str = "fp64", workspace: torch.Ten
                               workspace.numel(), _stream_ptr(dev))
     _lib.check(rc)
     return shift, theta, energy, status
+
+
+def align_pairs_ragged(z1: torch.Tensor, z2: torch.Tensor, offsets: torch.Tensor, *,
+                       max_n: int | None = None, workspace: torch.Tensor | None = None,
+                       autotune: bool = False, out: tuple | None = None):
+    """Alignment of pairs with different node counts (fa_align_pairs_ragged).
+
+    z1, z2: flat complex128/complex64 CUDA tensors of offsets[-1] points; pair p
+    is [offsets[p], offsets[p+1]) in both.  offsets: int64 CUDA tensor [P+1].
+    max_n bounds every pair's node count (default: computed from offsets, which
+    reads them back to the host).  With ``autotune`` the CTA size is chosen by
+    timed runs first (fa_align_pairs_ragged_autotune).  Returns (shift, theta,
+    energy, status) [P] each.
+    """
+    if z1.dtype not in (torch.complex128, torch.complex64):
+        raise ValueError("z1 must be complex128 or complex64")
+    _need_cuda("z1", z1, z1.dtype)
+    _need_cuda("z2", z2, z1.dtype)
+    _need_cuda("offsets", offsets, torch.int64)
+    P = offsets.numel() - 1
+    dev = z1.device
+    if max_n is None:
+        max_n = int((offsets[1:] - offsets[:-1]).max().item()) if P > 0 else 4
+        max_n = min(max(max_n, 4), 8192)
+    if out is None:
+        shift = torch.empty(P, dtype=torch.int32, device=dev)
+        theta = torch.empty(P, dtype=torch.float64, device=dev)
+        energy = torch.empty(P, dtype=torch.float64, device=dev)
+        status = torch.empty(P, dtype=torch.int8, device=dev)
+    else:
+        shift, theta, energy, status = out
+    L = _lib.load()
+    h = handle(dev.index)
+    need = int(L.fa_align_pairs_ragged_workspace_size(h, P, max_n))
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    ztype = _lib.Z_F64 if z1.dtype == torch.complex128 else _lib.Z_F32
+    args = (h, _ptr(z1), _ptr(z2), _ptr(offsets), P, max_n, ztype, _ptr(shift), _ptr(theta),
+            _ptr(energy), _ptr(status), _ptr(workspace), workspace.numel(), _stream_ptr(dev))
+    if autotune:
+        chosen = ctypes.c_int32(0)
+        _lib.check(L.fa_align_pairs_ragged_autotune(*args, ctypes.byref(chosen)))
+    else:
+        _lib.check(L.fa_align_pairs_ragged(*args))
+    return shift, theta, energy, status
+
+
+def ragged_workspace_size(P: int, max_n: int, device: int | None = None) -> int:
+    L = _lib.load()
+    return int(L.fa_align_pairs_ragged_workspace_size(handle(device), P, max_n))
 
 
 def align_curves_host(pts: torch.Tensor, offsets: torch.Tensor, N: int, *, method: str = "fft",

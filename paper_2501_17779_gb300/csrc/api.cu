@@ -51,6 +51,17 @@ __global__ void fma_twiddle_kernel(double2* tf, float2* tf32, int N)
 
 int build_twiddles(fa_handle* h)
 {
+    for (int L = kMaxLogN + 1; L <= kMaxRaggedLogL; ++L) {
+        const int N = 1 << L;
+        float2* tmp32 = nullptr;
+        cudaError_t e = cudaMalloc(&h->tw64[L], N * sizeof(double2));
+        if (e == cudaSuccess) e = cudaMalloc(&tmp32, N * sizeof(float2));
+        if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
+        twiddle_kernel<<<(N + 255) / 256, 256>>>(h->tw64[L], tmp32, N);
+        e = cudaDeviceSynchronize();
+        cudaFree(tmp32);
+        if (e != cudaSuccess) return cuda_error(e, "fa_create: twiddle kernel");
+    }
     for (int L = kMinLogN; L <= kMaxLogN; ++L) {
         const int N = 1 << L;
         cudaError_t e = cudaMalloc(&h->tw64[L], N * sizeof(double2));
@@ -149,6 +160,7 @@ int fa_create(fa_handle** out, int device)
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) { delete h; return cuda_error(e, "fa_create: attributes"); }
     int rc = build_twiddles(h);
+    if (rc == FA_OK) rc = ragged_set_attributes();
     if (rc != FA_OK) { fa_destroy(h); return rc; }
     *out = h;
     return FA_OK;
@@ -158,6 +170,8 @@ int fa_destroy(fa_handle* h)
 {
     if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_destroy: null handle");
     DeviceGuard g(h->device);
+    for (int L = kMaxLogN + 1; L <= kMaxRaggedLogL; ++L)
+        if (h->tw64[L]) cudaFree(h->tw64[L]);
     for (int L = 0; L <= kMaxLogN; ++L) {
         if (h->tw64[L]) cudaFree(h->tw64[L]);
         if (h->tw32[L]) cudaFree(h->tw32[L]);
@@ -246,6 +260,112 @@ int fa_align_pairs(fa_handle* h, const void* z1, const void* z2, int64_t P, int3
     if (method == FA_FFT)
         return launch_align_fft(h, z1, z2, P, logn, ztype, shift, theta, energy, status, st);
     return launch_align_direct(h, z1, z2, P, N, ztype, shift, theta, energy, status, st);
+}
+
+size_t fa_align_pairs_ragged_workspace_size(fa_handle* h, int64_t P, int32_t max_n)
+{
+    if (!h || P < 0 || max_n < 4 || max_n > kMaxRaggedN) return 0;
+    DeviceGuard g(h->device);
+    return ragged_ws_bytes(h, P, max_n);
+}
+
+static int ragged_check(fa_handle* h, const void* z1, const void* z2, const int64_t* offsets,
+                        int64_t P, int32_t max_n, int32_t ztype, int32_t* shift, double* theta,
+                        double* energy, int8_t* status, void* workspace, size_t workspace_bytes,
+                        void** ws_out)
+{
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged: null handle");
+    if (P < 0 || P > ((int64_t)1 << 31) - 1)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged: bad pair count");
+    if (max_n < 4 || max_n > kMaxRaggedN)
+        return set_error(FA_ERR_UNSUPPORTED, "fa_align_pairs_ragged: max_n outside [4, 8192]");
+    if (ztype != FA_Z_F64 && ztype != FA_Z_F32)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged: unknown ztype");
+    if (P == 0) return FA_OK;
+    if (!z1 || !z2 || !offsets || !shift || !theta || !energy || !status)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged: null pointer");
+    const size_t need = ragged_ws_bytes(h, P, max_n);
+    void* ws = workspace;
+    if (ws) {
+        if (workspace_bytes < need)
+            return set_error(FA_ERR_WORKSPACE, "fa_align_pairs_ragged: workspace too small");
+        if (reinterpret_cast<uintptr_t>(ws) & 255)
+            return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged: workspace not 256-aligned");
+    } else {
+        const int rc = ensure_ws(h, need);
+        if (rc != FA_OK) return rc;
+        ws = h->ws;
+    }
+    *ws_out = ws;
+    return FA_OK;
+}
+
+int fa_align_pairs_ragged(fa_handle* h, const void* z1, const void* z2, const int64_t* offsets,
+                          int64_t P, int32_t max_n, int32_t ztype, int32_t* shift, double* theta,
+                          double* energy, int8_t* status, void* workspace, size_t workspace_bytes,
+                          void* stream)
+{
+    if (h) {
+        DeviceGuard g(h->device);
+        if (g.rc != FA_OK) return g.rc;
+        void* ws = nullptr;
+        int rc = ragged_check(h, z1, z2, offsets, P, max_n, ztype, shift, theta, energy, status,
+                              workspace, workspace_bytes, &ws);
+        if (rc != FA_OK || P == 0) return rc;
+        return launch_align_ragged(h, z1, z2, offsets, P, max_n, ztype, h->ragged_threads, shift,
+                                   theta, energy, status, ws, static_cast<cudaStream_t>(stream));
+    }
+    return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged: null handle");
+}
+
+int fa_align_pairs_ragged_autotune(fa_handle* h, const void* z1, const void* z2,
+                                   const int64_t* offsets, int64_t P, int32_t max_n,
+                                   int32_t ztype, int32_t* shift, double* theta, double* energy,
+                                   int8_t* status, void* workspace, size_t workspace_bytes,
+                                   void* stream, int32_t* chosen_threads)
+{
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged_autotune: null handle");
+    DeviceGuard g(h->device);
+    if (g.rc != FA_OK) return g.rc;
+    void* ws = nullptr;
+    int rc = ragged_check(h, z1, z2, offsets, P, max_n, ztype, shift, theta, energy, status,
+                          workspace, workspace_bytes, &ws);
+    if (rc != FA_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int cand[3] = {256, 512, 1024};
+    float best_ms = -1.f;
+    int best = h->ragged_threads;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int c = 0; c < 3 && P > 0; ++c) {
+        rc = launch_align_ragged(h, z1, z2, offsets, P, max_n, ztype, cand[c], shift, theta,
+                                 energy, status, ws, st);  // warm-up
+        if (rc != FA_OK) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && rc == FA_OK; ++r)
+            rc = launch_align_ragged(h, z1, z2, offsets, P, max_n, ztype, cand[c], shift, theta,
+                                     energy, status, ws, st);
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (rc != FA_OK || e != cudaSuccess) { if (rc == FA_OK) rc = cuda_error(e, "autotune"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = cand[c]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FA_OK) return rc;
+    // leave the outputs of the chosen configuration (sums run in a CTA-size
+    // dependent order, so other sizes can differ in the last bit)
+    if (P > 0) {
+        rc = launch_align_ragged(h, z1, z2, offsets, P, max_n, ztype, best, shift, theta, energy,
+                                 status, ws, st);
+        if (rc != FA_OK) return rc;
+    }
+    h->ragged_threads = best;
+    if (chosen_threads) *chosen_threads = best;
+    return FA_OK;
 }
 
 size_t fa_align_all_pairs_workspace_size(int64_t M, int32_t N)

@@ -12,13 +12,15 @@
 struct fa_handle {
     int device = 0;
     int num_sms = 0;
-    // twiddle tables W_N[k] = exp(-2 pi i k / N), k = 0..N-1, for N = 2^logn, logn in [2, 12]
-    double2* tw64[13] = {};
+    // twiddle tables W_N[k] = exp(-2 pi i k / N), k = 0..N-1, for N = 2^logn,
+    // logn in [2, 14] for tw64 (the ragged path's long transforms), [2, 12] otherwise
+    double2* tw64[15] = {};
     float2* tw32[13] = {};
     // FMA-form twiddles for e in [0, N/2): (m, rho) with W_N^e = m (1 + i rho) when
     // |cos| >= |sin| (e <= N/8 or e >= 3N/8), else W_N^e = m (rho + i); |rho| <= 1
     double2* tf64[13] = {};
     float2* tf32[13] = {};  // the same in FP32 (FA_PREC_MIXED search)
+    int ragged_threads = 256;  // CTA size of the ragged persistent kernel (autotuned)
     // handle-owned scratch, used when the caller passes no workspace
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -29,6 +31,8 @@ namespace fa {
 constexpr int kMinLogN = 2;
 constexpr int kMaxLogN = 12;
 constexpr int kMaxDirectN = 4096;
+constexpr int kMaxRaggedN = 8192;      // largest node count of fa_align_pairs_ragged
+constexpr int kMaxRaggedLogL = 14;     // its longest transform, 2^14
 
 // error reporting (thread-local message for fa_last_error)
 int set_error(int code, const std::string& msg);
@@ -89,6 +93,13 @@ size_t align_all_ws_bytes(int64_t M, int N);
 int launch_align_all(const fa_handle* h, const void* z, int64_t M, int logn, int ztype, void* ws,
                      int8_t* status, int32_t* shift, double* theta, double* energy,
                      cudaStream_t st);
+int ragged_grid(const fa_handle* h, int threads);
+int ragged_set_attributes();
+size_t ragged_ws_bytes(const fa_handle* h, int64_t P, int max_n);
+int launch_align_ragged(const fa_handle* h, const void* z1, const void* z2, const int64_t* off,
+                        int64_t P, int max_n, int ztype, int threads, int32_t* shift,
+                        double* theta, double* energy, int8_t* status, void* ws,
+                        cudaStream_t st);
 int launch_resample(const fa_handle* h, const double* pts, const int64_t* offsets, int64_t C,
                     int64_t n_pts, int N_out, int flags, void* z_out, int8_t* status, void* ws,
                     cudaStream_t st);

@@ -210,3 +210,100 @@ def template_pair(h: Harmonics, N: int, start: float = 0.25,
     q = int(round(start * N))
     z2 = np.exp(1j * rotation) * np.roll(z1, -q)
     return z1, z2
+
+
+@dataclass
+class RaggedPairs:
+    z1: np.ndarray       # complex128 [sum n]: curve 1 of every pair, concatenated
+    z2: np.ndarray       # complex128 [sum n]: curve 2 of every pair, same offsets
+    offsets: np.ndarray  # int64 [P + 1]
+    shift_true: np.ndarray
+    theta_true: np.ndarray
+
+
+def ragged_aligned_pairs(seed: int, sizes, min_harm: int = 4, max_harm: int = 32,
+                         noise: float = 1e-3, oversample: int = 8) -> RaggedPairs:
+    """Aligned pairs with a different node count per pair (host, numpy).
+
+    Pair p has sizes[p] nodes; curve 1 is uniform in arc length with
+    U{min_harm..max_harm} harmonics, curve 2 its rotated, relabelled and noisy
+    copy (as in ``aligned_pairs``)."""
+    rng = np.random.default_rng(seed)
+    z1, z2, st, tt = [], [], [], []
+    for n in sizes:
+        n = int(n)
+        h = random_harmonics(rng, int(rng.integers(min_harm, max_harm + 1)))
+        a = uniform_arclength_nodes(h, n, oversample)
+        th_g = rng.uniform(0.0, TWO_PI)
+        s_g = int(rng.integers(0, n))
+        b = np.exp(1j * th_g) * np.roll(a, s_g)
+        if noise > 0.0:
+            b = _normalise(b + noise * (rng.standard_normal(n) + 1j * rng.standard_normal(n)))
+        z1.append(a)
+        z2.append(b)
+        st.append(s_g)
+        tt.append(np.angle(np.exp(-1j * th_g)))
+    offs = np.concatenate([[0], np.cumsum([len(a) for a in z1])]).astype(np.int64)
+    return RaggedPairs(np.concatenate(z1), np.concatenate(z2), offs, np.array(st, np.int32),
+                       np.array(tt))
+
+
+def log_uniform_sizes(seed: int, P: int, n_min: int = 64, n_max: int = 8192,
+                      multiple: int = 16) -> np.ndarray:
+    """P node counts log-uniform in [n_min, n_max], rounded to a multiple."""
+    rng = np.random.default_rng(seed)
+    n = np.exp(rng.uniform(np.log(n_min), np.log(n_max), P))
+    return np.clip(np.round(n / multiple) * multiple, n_min, n_max).astype(np.int64)
+
+
+def ragged_pairs_device(seed: int, sizes, device, min_harm: int = 4, max_harm: int = 32,
+                        noise: float = 1e-3):
+    """Large ragged batches generated on the GPU with torch (same family as
+    ``ragged_aligned_pairs``, but nodes uniform in the polar angle, which keeps
+    generation of ~10^8 nodes fast).  Returns (z1, z2, offsets) as device
+    tensors (complex128, complex128, int64).  Input generation only."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    sizes = torch.as_tensor(np.asarray(sizes, np.int64), device=device)
+    P = sizes.numel()
+    offs = torch.zeros(P + 1, dtype=torch.int64, device=device)
+    offs[1:] = torch.cumsum(sizes, 0)
+    total = int(offs[-1].item())
+    pair = torch.repeat_interleave(torch.arange(P, device=device), sizes)
+    k = torch.arange(total, device=device) - offs[pair]
+    nn = sizes[pair].double()
+    phi = (2 * np.pi) * k.double() / nn
+    H = max_harm
+    kk = torch.arange(1, H + 1, device=device, dtype=torch.float64)
+    nh = torch.randint(min_harm, max_harm + 1, (P,), generator=g, device=device)
+    amp = torch.randn(P, H, generator=g, device=device, dtype=torch.float64) * (0.15 / kk)
+    amp = amp * (kk[None, :] <= nh[:, None])
+    ph = torch.rand(P, H, generator=g, device=device, dtype=torch.float64) * (2 * np.pi)
+    # keep r >= 0.25: scale the perturbation by its worst case sum |a_k|
+    worst = amp.abs().sum(1)
+    amp = amp * torch.clamp(0.75 / worst, max=1.0)[:, None]
+    r = torch.ones(total, device=device, dtype=torch.float64)
+    for h0 in range(0, H, 8):
+        hs = slice(h0, min(H, h0 + 8))
+        r += (amp[pair, hs] * torch.cos(phi[:, None] * kk[None, hs] + ph[pair, hs])).sum(1)
+    z1 = torch.polar(r, phi)
+
+    def normalise(z):
+        mean = torch.zeros(P, dtype=z.dtype, device=device).index_add_(0, pair, z) / sizes
+        z = z - mean[pair]
+        nxt = torch.where(k + 1 == sizes[pair], offs[pair], torch.arange(total, device=device) + 1)
+        per = torch.zeros(P, dtype=torch.float64, device=device).index_add_(0, pair, (z[nxt] - z).abs())
+        return z / per[pair]
+
+    z1 = normalise(z1)
+    sg = (torch.rand(P, generator=g, device=device, dtype=torch.float64) * sizes).long()
+    thg = torch.rand(P, generator=g, device=device, dtype=torch.float64) * (2 * np.pi)
+    src = offs[pair] + torch.remainder(k - sg[pair], sizes[pair])
+    z2 = torch.polar(torch.ones_like(thg), thg)[pair] * z1[src]
+    if noise > 0.0:
+        z2 = z2 + noise * torch.complex(torch.randn(total, generator=g, device=device, dtype=torch.float64),
+                                        torch.randn(total, generator=g, device=device, dtype=torch.float64))
+        z2 = normalise(z2)
+    return z1.contiguous(), z2.contiguous(), offs

@@ -1,0 +1,140 @@
+"""GPU parity of fa_align_pairs_ragged (uneven node counts, one persistent
+launch) against the FP64 oracle (C ABI)."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2501_17779_gb300 import _lib, api, synth
+
+from _parity import check_align, wrap
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _split(rp):
+    P = rp.offsets.size - 1
+    n = np.diff(rp.offsets)
+    return P, n
+
+
+def _check_ragged(rp, out):
+    """Oracle per pair (any length), FP64 bounds."""
+    s, th, e, st = [x.cpu().numpy() for x in out]
+    P, n = _split(rp)
+    for N in np.unique(n):
+        idx = np.nonzero(n == N)[0]
+        z1 = np.stack([rp.z1[rp.offsets[p]:rp.offsets[p + 1]] for p in idx])
+        z2 = np.stack([rp.z2[rp.offsets[p]:rp.offsets[p + 1]] for p in idx])
+        check_align(z1, z2, s[idx], th[idx], e[idx], st[idx])
+
+
+def _dev(rp, dtype=torch.complex128):
+    return (torch.from_numpy(rp.z1).to(DEV, dtype), torch.from_numpy(rp.z2).to(DEV, dtype),
+            torch.from_numpy(rp.offsets).to(DEV))
+
+
+def test_ragged_mixed_sizes_all_decompositions():
+    """Powers of two (L = n, one to two sub-transforms), non-powers with
+    L = 2..4 x 4096 (one, two and four sub-transforms), the smallest sizes."""
+    sizes = [4, 5, 7, 16, 17, 64, 100, 256, 333, 1000, 1024, 2047, 2048, 2049, 3000, 4096,
+             4097, 5000, 6144, 8191, 8192]
+    rp = synth.ragged_aligned_pairs(21, sizes, min_harm=2, max_harm=12)
+    out = api.align_pairs_ragged(*_dev(rp))
+    torch.cuda.synchronize()
+    _check_ragged(rp, out)
+
+
+def test_ragged_noise_free_exact_recovery():
+    sizes = synth.log_uniform_sizes(5, 40, 64, 8192)
+    rp = synth.ragged_aligned_pairs(22, sizes, noise=0.0)
+    s, th, e, st = [x.cpu().numpy() for x in api.align_pairs_ragged(*_dev(rp))]
+    np.testing.assert_array_equal(s, rp.shift_true)
+    assert np.abs(wrap(th - rp.theta_true)).max() < 1e-12
+    assert e.max() < 1e-15 and (st == 0).all()
+
+
+def test_ragged_bad_sizes_and_nonfinite():
+    good = synth.ragged_aligned_pairs(23, [64, 100, 8192, 128])
+    z1 = np.concatenate([good.z1[:64], np.zeros(3), good.z1[64:164], np.zeros(9000),
+                         good.z1[164:]])
+    z2 = np.concatenate([good.z2[:64], np.zeros(3), good.z2[64:164], np.zeros(9000),
+                         good.z2[164:]])
+    sizes = [64, 3, 100, 9000, 0, 8192, 128]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    z1[offs[6] + 5] = np.nan  # pair 6 non-finite
+    rp = synth.RaggedPairs(z1, z2, offs, None, None)
+    s, th, e, st = [x.cpu().numpy() for x in api.align_pairs_ragged(*_dev(rp), max_n=8192)]
+    assert list(st) == [0, 3, 0, 3, 3, 0, 2]
+    assert (s[[1, 3, 4, 6]] == -1).all() and np.isnan(e[[1, 3, 4, 6]]).all()
+    ok = [0, 2, 5]
+    for p in ok:
+        a = z1[offs[p]:offs[p + 1]][None]
+        b = z2[offs[p]:offs[p + 1]][None]
+        check_align(a, b, s[[p]], th[[p]], e[[p]], st[[p]])
+
+
+def test_ragged_max_n_bound_and_complex64():
+    rp = synth.ragged_aligned_pairs(24, [100, 200, 300])
+    s, th, e, st = [x.cpu().numpy() for x in api.align_pairs_ragged(*_dev(rp, torch.complex64),
+                                                                    max_n=250)]
+    assert list(st) == [0, 0, 3]
+    r = synth.RaggedPairs(rp.z1.astype(np.complex64).astype(np.complex128),
+                          rp.z2.astype(np.complex64).astype(np.complex128), rp.offsets, None, None)
+    for p in (0, 1):
+        a = r.z1[r.offsets[p]:r.offsets[p + 1]][None]
+        b = r.z2[r.offsets[p]:r.offsets[p + 1]][None]
+        check_align(a, b, s[[p]], th[[p]], e[[p]], st[[p]])
+
+
+def test_ragged_graph_capture_and_autotune():
+    """The whole call (memset + three launches) captured in a CUDA graph and
+    replayed gives the same result as a direct call; the autotuner picks one of
+    its CTA sizes and leaves a valid result."""
+    sizes = synth.log_uniform_sizes(9, 300, 64, 4096)
+    rp = synth.ragged_aligned_pairs(25, sizes, min_harm=4, max_harm=16)
+    z1, z2, offs = _dev(rp)
+    P = offs.numel() - 1
+    ws = torch.empty(api.ragged_workspace_size(P, 4096), dtype=torch.uint8, device=DEV)
+    ref = api.align_pairs_ragged(z1, z2, offs, max_n=4096, workspace=ws, autotune=True)
+    torch.cuda.synchronize()
+    ref = [x.clone() for x in ref]
+    out = tuple(torch.empty_like(x) for x in ref)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        api.align_pairs_ragged(z1, z2, offs, max_n=4096, workspace=ws, out=out)  # warm-up
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        api.align_pairs_ragged(z1, z2, offs, max_n=4096, workspace=ws, out=out)
+    for x in out:
+        x.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, out):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
+    _check_ragged(rp, ref)
+
+
+def test_ragged_large_batch_sampled():
+    """4000 pairs, n log-uniform in [64, 8192] (multiples of 16), 4..32
+    harmonics, generated on the device; the oracle checks a sample of 24 pairs
+    across the size range, every pair is checked for validity."""
+    sizes = synth.log_uniform_sizes(31, 4000)
+    z1, z2, offs = synth.ragged_pairs_device(31, sizes, DEV)
+    s, th, e, st = api.align_pairs_ragged(z1, z2, offs, max_n=8192)
+    torch.cuda.synchronize()
+    s, th, e, st = [x.cpu().numpy() for x in (s, th, e, st)]
+    n = np.asarray(sizes)
+    assert (st == 0).all() and (s >= 0).all() and (s < n).all() and np.isfinite(e).all()
+    order = np.argsort(n)
+    idx = order[np.linspace(0, len(n) - 1, 24).astype(int)]
+    o = offs.cpu().numpy()
+    a1, a2 = z1.cpu().numpy(), z2.cpu().numpy()
+    for p in idx:
+        check_align(a1[o[p]:o[p + 1]][None], a2[o[p]:o[p + 1]][None], s[[p]], th[[p]], e[[p]],
+                    st[[p]])
