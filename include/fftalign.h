@@ -69,10 +69,14 @@ typedef struct fa_handle fa_handle;
 
 /* arithmetic of the shift search (theta and the energy are always FP64) */
 #define FA_PREC_FP64 0  /* every step in FP64                                  */
-#define FA_PREC_MIXED 1 /* FA_FFT only: the transforms in FP32; every shift whose
-                           FP32 |c(s)| lies within a rigorous error bound of the
-                           maximum is re-scored by its FP64 sum, so the result
-                           obeys the same bounds as FA_PREC_FP64               */
+#define FA_PREC_MIXED 1 /* FA_FFT only: the three transforms in double-float
+                           arithmetic (pairs of floats, ~48-bit significands)
+                           on the FP32 pipe; their error (~1e-13 of max|c|)
+                           keeps the argmax inside the tie tolerance; c(s*),
+                           theta and the energy are computed in FP64, so the
+                           result obeys the same bounds as FA_PREC_FP64.
+                           Coordinates must lie within [2^-74, 2^128) in
+                           magnitude (or be 0): unit-length curves do        */
 
 /* Create a handle bound to CUDA device `device` (its twiddle tables are built
  * here, synchronously).  *h receives the handle.  Not thread-safe with
@@ -171,7 +175,7 @@ int fa_align_pairs(fa_handle* h, const void* z1, const void* z2, int64_t P, int3
  *              centred and of unit length
  *   M          number of curves, in [0, 65536]
  *   N          nodes per curve, a power of two in [4, 4096]
- *   prec       FA_PREC_FP64
+ *   prec       FA_PREC_FP64 or FA_PREC_MIXED (search in double-float)
  *   shift      int32[M*M], theta double[M*M], energy double[M*M] (device)
  *   status     int8[M] per-curve status (FA_STATUS_OK or _NONFINITE); rows and
  *              columns of a non-finite curve get shift -1 and NaN

@@ -26,9 +26,7 @@
 namespace fa {
 namespace {
 
-// RETRY: only pairs whose status is kStatusRetryFP64 (left by the mixed-
-// precision search) are processed; CTAs with none of them return at once.
-template <int LOGN, typename ZT, bool RETRY>
+template <int LOGN, typename ZT>
 __global__ void __launch_bounds__(Geo<LOGN>::T)
     align_fft_kernel(const ZT* __restrict__ z1, const ZT* __restrict__ z2, int64_t P,
                      const double2* __restrict__ W, int32_t* __restrict__ shift,
@@ -48,15 +46,10 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
 
     const int g = threadIdx.x / Q;
     const int t = threadIdx.x % Q;
-    const int64_t pair0 = (int64_t)blockIdx.x * G + g;
-    bool valid = pair0 < P;
-    if constexpr (RETRY) {
-        valid = valid && status[pair0] == kStatusRetryFP64;
-        if (!__syncthreads_or(valid)) return;  // CTA-uniform
-    }
-    const int64_t pair = pair0;
-    const ZT* p1 = z1 + (pair0 < P ? pair : 0) * N;
-    const ZT* p2 = z2 + (pair0 < P ? pair : 0) * N;
+    const int64_t pair = (int64_t)blockIdx.x * G + g;
+    const bool valid = pair < P;
+    const ZT* p1 = z1 + (valid ? pair : 0) * N;
+    const ZT* p2 = z2 + (valid ? pair : 0) * N;
 
     if (t == 0) bad[g] = 0;
     __syncthreads();
@@ -133,7 +126,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     }
 }
 
-template <int LOGN, typename ZT, bool RETRY = false>
+template <int LOGN, typename ZT>
 int launch_one(const fa_handle* h, const void* z1, const void* z2, int64_t P, int32_t* shift,
                double* theta, double* energy, int8_t* status, cudaStream_t st)
 {
@@ -141,7 +134,7 @@ int launch_one(const fa_handle* h, const void* z1, const void* z2, int64_t P, in
     const size_t smem = (size_t)Gm::G * 2 * Gm::N * sizeof(double2) + 2 * Gm::G * sizeof(double2) +
                         (size_t)Gm::G * Gm::W * (sizeof(long long) + sizeof(int)) +
                         Gm::G * sizeof(int);
-    auto kern = align_fft_kernel<LOGN, ZT, RETRY>;
+    auto kern = align_fft_kernel<LOGN, ZT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -154,13 +147,13 @@ int launch_one(const fa_handle* h, const void* z1, const void* z2, int64_t P, in
     return cuda_error(cudaGetLastError(), "align_fft launch");
 }
 
-template <typename ZT, bool RETRY>
+template <typename ZT>
 int dispatch(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
              int32_t* shift, double* theta, double* energy, int8_t* status, cudaStream_t st)
 {
     switch (logn) {
 #define FA_CASE(L) \
-    case L: return launch_one<L, ZT, RETRY>(h, z1, z2, P, shift, theta, energy, status, st);
+    case L: return launch_one<L, ZT>(h, z1, z2, P, shift, theta, energy, status, st);
         FA_CASE(2) FA_CASE(3) FA_CASE(4) FA_CASE(5) FA_CASE(6) FA_CASE(7) FA_CASE(8) FA_CASE(9)
         FA_CASE(10) FA_CASE(11) FA_CASE(12)
 #undef FA_CASE
@@ -176,18 +169,8 @@ int launch_align_fft(const fa_handle* h, const void* z1, const void* z2, int64_t
 {
     if (P == 0) return FA_OK;
     if (ztype == FA_Z_F64)
-        return dispatch<double2, false>(h, z1, z2, P, logn, shift, theta, energy, status, st);
-    return dispatch<float2, false>(h, z1, z2, P, logn, shift, theta, energy, status, st);
-}
-
-int launch_align_fft_retry(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
-                           int ztype, int32_t* shift, double* theta, double* energy,
-                           int8_t* status, cudaStream_t st)
-{
-    if (P == 0) return FA_OK;
-    if (ztype == FA_Z_F64)
-        return dispatch<double2, true>(h, z1, z2, P, logn, shift, theta, energy, status, st);
-    return dispatch<float2, true>(h, z1, z2, P, logn, shift, theta, energy, status, st);
+        return dispatch<double2>(h, z1, z2, P, logn, shift, theta, energy, status, st);
+    return dispatch<float2>(h, z1, z2, P, logn, shift, theta, energy, status, st);
 }
 
 }  // namespace fa

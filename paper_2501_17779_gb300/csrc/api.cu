@@ -37,16 +37,25 @@ __global__ void twiddle_kernel(double2* w64, float2* w32, int N)
 }
 
 // FMA-form twiddles (m, rho) for e in [0, N/2): W = m (1 + i rho) or m (rho + i).
-__global__ void fma_twiddle_kernel(double2* tf, float2* tf32, int N)
+__global__ void fma_twiddle_kernel(double2* tf, int N)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N / 2) return;
     double s, c;
     sincospi(2.0 * (double)e / (double)N, &s, &c);
     const double wr = c, wi = -s;
-    const double2 v = tw_form_b(e, N) ? make_double2(wi, wr / wi) : make_double2(wr, wi / wr);
-    tf[e] = v;
-    tf32[e] = make_float2((float)v.x, (float)v.y);
+    tf[e] = tw_form_b(e, N) ? make_double2(wi, wr / wi) : make_double2(wr, wi / wr);
+}
+
+// W_N[k] as double-float pairs: hi = nearest float, lo = nearest float to the rest
+__global__ void df_twiddle_kernel(const double2* w64, float4* tdf, int N)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const double2 w = w64[k];
+    const float rh = __double2float_rn(w.x), ih = __double2float_rn(w.y);
+    tdf[k] = make_float4(rh, __double2float_rn(w.x - (double)rh), ih,
+                         __double2float_rn(w.y - (double)ih));
 }
 
 int build_twiddles(fa_handle* h)
@@ -70,10 +79,11 @@ int build_twiddles(fa_handle* h)
         if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
         e = cudaMalloc(&h->tf64[L], (N / 2) * sizeof(double2));
         if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
-        e = cudaMalloc(&h->tf32[L], (N / 2) * sizeof(float2));
+        e = cudaMalloc(&h->tdf[L], N * sizeof(float4));
         if (e != cudaSuccess) return cuda_error(e, "fa_create: cudaMalloc twiddles");
-        fma_twiddle_kernel<<<(N / 2 + 255) / 256, 256>>>(h->tf64[L], h->tf32[L], N);
+        fma_twiddle_kernel<<<(N / 2 + 255) / 256, 256>>>(h->tf64[L], N);
         twiddle_kernel<<<(N + 255) / 256, 256>>>(h->tw64[L], h->tw32[L], N);
+        df_twiddle_kernel<<<(N + 255) / 256, 256>>>(h->tw64[L], h->tdf[L], N);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(e, "fa_create: twiddle kernel");
     }
@@ -176,7 +186,7 @@ int fa_destroy(fa_handle* h)
         if (h->tw64[L]) cudaFree(h->tw64[L]);
         if (h->tw32[L]) cudaFree(h->tw32[L]);
         if (h->tf64[L]) cudaFree(h->tf64[L]);
-        if (h->tf32[L]) cudaFree(h->tf32[L]);
+        if (h->tdf[L]) cudaFree(h->tdf[L]);
     }
     if (h->ws) cudaFree(h->ws);
     delete h;
@@ -256,7 +266,7 @@ int fa_align_pairs(fa_handle* h, const void* z1, const void* z2, int64_t P, int3
     if (g.rc != FA_OK) return g.rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (method == FA_FFT && prec == FA_PREC_MIXED)
-        return launch_align_mixed(h, z1, z2, P, logn, ztype, shift, theta, energy, status, st);
+        return launch_align_df(h, z1, z2, P, logn, ztype, shift, theta, energy, status, st);
     if (method == FA_FFT)
         return launch_align_fft(h, z1, z2, P, logn, ztype, shift, theta, energy, status, st);
     return launch_align_direct(h, z1, z2, P, N, ztype, shift, theta, energy, status, st);
@@ -382,7 +392,7 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
     if (M < 0) return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: negative curve count");
     if (ztype != FA_Z_F64 && ztype != FA_Z_F32)
         return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: unknown ztype");
-    if (prec != FA_PREC_FP64)
+    if (prec != FA_PREC_FP64 && prec != FA_PREC_MIXED)
         return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: unknown precision");
     int logn = -1;
     for (int L = kMinLogN; L <= kMaxLogN; ++L)
@@ -409,6 +419,9 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
         if (rc != FA_OK) return rc;
         ws = h->ws;
     }
+    if (prec == FA_PREC_MIXED)
+        return launch_align_all_df(h, z, M, logn, ztype, ws, status, shift, theta, energy,
+                                   static_cast<cudaStream_t>(stream));
     return launch_align_all(h, z, M, logn, ztype, ws, status, shift, theta, energy,
                             static_cast<cudaStream_t>(stream));
 }

@@ -19,7 +19,7 @@ struct fa_handle {
     // FMA-form twiddles for e in [0, N/2): (m, rho) with W_N^e = m (1 + i rho) when
     // |cos| >= |sin| (e <= N/8 or e >= 3N/8), else W_N^e = m (rho + i); |rho| <= 1
     double2* tf64[13] = {};
-    float2* tf32[13] = {};  // the same in FP32 (FA_PREC_MIXED search)
+    float4* tdf[13] = {};   // W_N[k] in double-float (re.h, re.l, im.h, im.l), FA_PREC_MIXED
     int ragged_threads = 256;  // CTA size of the ragged persistent kernel (autotuned)
     // handle-owned scratch, used when the caller passes no workspace
     void* ws = nullptr;
@@ -78,14 +78,12 @@ __device__ __forceinline__ bool key_better(long long ka, int ia, long long kb, i
 int launch_align_fft(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
                      int ztype, int32_t* shift, double* theta, double* energy, int8_t* status,
                      cudaStream_t st);
-// internal status: the mixed-precision search leaves the pair to the FP64 kernel
-constexpr int8_t kStatusRetryFP64 = 100;
-int launch_align_fft_retry(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
-                           int ztype, int32_t* shift, double* theta, double* energy,
-                           int8_t* status, cudaStream_t st);
-int launch_align_mixed(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
-                       int ztype, int32_t* shift, double* theta, double* energy, int8_t* status,
-                       cudaStream_t st);
+int launch_align_df(const fa_handle* h, const void* z1, const void* z2, int64_t P, int logn,
+                    int ztype, int32_t* shift, double* theta, double* energy, int8_t* status,
+                    cudaStream_t st);
+int launch_align_all_df(const fa_handle* h, const void* z, int64_t M, int logn, int ztype,
+                        void* ws, int8_t* status, int32_t* shift, double* theta, double* energy,
+                        cudaStream_t st);
 int launch_align_direct(const fa_handle* h, const void* z1, const void* z2, int64_t P, int N,
                         int ztype, int32_t* shift, double* theta, double* energy, int8_t* status,
                         cudaStream_t st);

@@ -177,10 +177,10 @@ def test_repeatable_bitwise(path):
         np.testing.assert_array_equal(x, y)
 
 
-def test_mixed_candidates_cover_near_ties():
+def test_mixed_near_ties():
     """Pairs built to have two nearly equal shifts (a curve with a two-fold
-    symmetry plus a tiny perturbation): the mixed search must still return the
-    oracle's winner or a shift inside the tie tolerance."""
+    symmetry plus a tiny perturbation): the double-float search must still
+    return the oracle's winner or a shift inside the tie tolerance."""
     N = 512
     rng = np.random.default_rng(11)
     phi = 2 * np.pi * np.arange(N) / N

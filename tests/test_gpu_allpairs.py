@@ -18,16 +18,17 @@ def _curves(seed, M, N, n_harm=8):
     return np.concatenate([ap.z1, ap.z2])[:M]
 
 
-def _gpu_all(z, dtype=torch.complex128):
-    s, th, e, st = api.align_all_pairs(torch.from_numpy(z).to(DEV, dtype))
+def _gpu_all(z, dtype=torch.complex128, prec="fp64"):
+    s, th, e, st = api.align_all_pairs(torch.from_numpy(z).to(DEV, dtype), prec=prec)
     torch.cuda.synchronize()
     return s.cpu().numpy(), th.cpu().numpy(), e.cpu().numpy(), st.cpu().numpy()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("M,N", [(24, 256), (17, 64), (9, 1024), (2, 16)])
-def test_all_pairs_match_oracle(M, N):
+def test_all_pairs_match_oracle(M, N, prec):
     z = _curves(M * 7 + N, M, N)
-    s, th, e, st = _gpu_all(z)
+    s, th, e, st = _gpu_all(z, prec=prec)
     assert (st == 0).all()
     iu, ju = np.triu_indices(M, 1)
     ok = np.zeros(len(iu), np.int8)
@@ -56,12 +57,13 @@ def test_all_pairs_complex64_and_bad_curve():
     assert len(good) == M - 1
 
 
-def test_all_pairs_full_size_sample():
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_all_pairs_full_size_sample(prec):
     """M = 2048 curves at N = 512 (2,096,128 ordered pairs); the oracle checks a
     sample of 64 pairs, every entry is checked for validity and symmetry."""
     M, N = 2048, 512
     z = _curves(777, M, N, n_harm=12)
-    s, th, e, st = _gpu_all(z)
+    s, th, e, st = _gpu_all(z, prec=prec)
     assert (st == 0).all()
     off = ~np.eye(M, dtype=bool)
     assert ((s >= 0) & (s < N)).all() and np.isfinite(th).all() and (e[off] >= 0).all()
