@@ -26,8 +26,17 @@
 namespace fa {
 namespace {
 
+// Resident CTAs per SM requested from the compiler for CTAs of <= 256
+// threads: 3 (a register cap of ~85 per thread; at N = 1024 measured 1.6 %
+// faster than 2 despite a small spill).  Larger CTAs keep the compiler's choice.
+#ifndef FA_ALIGN_MIN_BLOCKS
+#define FA_ALIGN_MIN_BLOCKS 3
+#endif
+template <int T>
+constexpr int align_min_blocks() { return T <= 256 ? FA_ALIGN_MIN_BLOCKS : 1; }
+
 template <int LOGN, typename ZT>
-__global__ void __launch_bounds__(Geo<LOGN>::T)
+__global__ void __launch_bounds__(Geo<LOGN>::T, align_min_blocks<Geo<LOGN>::T>())
     align_fft_kernel(const ZT* __restrict__ z1, const ZT* __restrict__ z2, int64_t P,
                      const double2* __restrict__ W, int32_t* __restrict__ shift,
                      double* __restrict__ theta, double* __restrict__ energy,
