@@ -3,8 +3,9 @@
 //
 // One warp per curve.  Lane j owns a contiguous chunk of nodes
 // [s_j, s_{j+1}) (P chunks, P = 32 for n >= 64).  Steps:
-//   A. chord lengths d_l = |p_{l+1} - p_l| and their sum per chunk; a warp scan
-//      gives each chunk's starting arc length and the perimeter L.
+//   A. chord lengths d_l = |p_{l+1} - p_l| (node-parallel), their sum per
+//      chunk; a warp scan gives each chunk's starting arc length and the
+//      perimeter L.
 //   B. forward sweep over each chunk's interior nodes (all but its last):
 //      cumulative arc lengths S_l = L u_l, the periodic-spline equations
 //          h_{l-1} M_{l-1} + 2(h_{l-1}+h_l) M_l + h_l M_{l+1}
@@ -126,28 +127,25 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
     double2* F1 = ws.F1 + o;
     double2* M = ws.M + o;
 
-    // ---- A: chords, chunk sums, warp scan -------------------------------------
+    // ---- A: chords (node-parallel, coalesced), chunk sums, warp scan --------
     // d = q * rsqrt(q) and 1/d = rsqrt(q) from one reciprocal square root
     // (q = |p_{l+1} - p_l|^2 >= 0, so its bit pattern tests > 0 as an integer)
-    double csum = 0.0;
     bool zero = false;
-    if (act) {
-        double2 pl = __ldg(p + sj);
-        for (int l = sj; l < sj1; ++l) {
-            const int ln = (l + 1 == n) ? 0 : l + 1;
-            const double2 pn = __ldg(p + ln);
-            const double dx = pn.x - pl.x, dy = pn.y - pl.y;
-            const double q = fma(dx, dx, dy * dy);
-            const bool pos = __double_as_longlong(q) > 0;
-            const double rs = rsqrt(q);
-            const double d = pos ? q * rs : 0.0;
-            zero |= !pos;
-            D[l] = d;
-            IH[l] = rs;
-            csum += d;
-            pl = pn;
-        }
+    for (int l = lane; l < n; l += 32) {
+        const double2 pl = __ldg(p + l);
+        const double2 pn = __ldg(p + ((l + 1 == n) ? 0 : l + 1));
+        const double dx = pn.x - pl.x, dy = pn.y - pl.y;
+        const double q = fma(dx, dx, dy * dy);
+        const bool pos = __double_as_longlong(q) > 0;
+        const double rs = rsqrt(q);
+        zero |= !pos;
+        D[l] = pos ? q * rs : 0.0;
+        IH[l] = rs;
     }
+    __syncwarp();
+    double csum = 0.0;
+    if (act)
+        for (int l = sj; l < sj1; ++l) csum += D[l];
     if (__any_sync(0xffffffffu, zero)) {
         fill_nan<F32OUT>(zout, zbase, Nout, lane);
         if (lane == 0) status[curve] = FA_STATUS_DEGENERATE;
