@@ -50,6 +50,49 @@ struct Ws {
     double2* Z;    // raw outputs before normalisation  [C*N_out] (FP32 output only)
 };
 
+// ---- reciprocal square root and reciprocal by one Newton-Raphson step -------
+// The FP32 seed is built from the double's bits with integer instructions, the
+// FP32 hardware approximation (rsqrtf / __frcp_rn) refines it to ~2^-22, and
+// one FP64 Newton-Raphson step (Newton's method on f(y) = 1/y^2 - q, resp.
+// f(r) = 1/r - x) squares the relative error to below 2e-13 (rsqrt) and 1e-13
+// (reciprocal) -- three and two FP64 instructions instead of a full-precision
+// sequence.  The chord lengths, their reciprocals, the pivots and the
+// perimeter need no more: their errors move the resampled nodes by < 2e-13 of
+// the curve length, inside the 1e-12 parity bound.  Valid for positive
+// normal inputs within the FP32 exponent range, which chords, perimeters and
+// pivots of curves of reasonable size are; other inputs take the CUDA call.
+__device__ __forceinline__ bool f32_range(double x)
+{
+    const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+    return e > -120 && e < 120;
+}
+__device__ __forceinline__ float seed_f32(double x)  // x truncated to a float (x > 0)
+{
+    const long long b = __double_as_longlong(x);
+    const unsigned e = (unsigned)(((b >> 52) & 0x7ff) - 1023 + 127);
+    return __uint_as_float((e << 23) | (unsigned)((b >> 29) & 0x7fffff));
+}
+__device__ __forceinline__ double widen_f32(float f)  // exact float -> double by bits (f > 0)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long e = ((u >> 23) & 0xff) - 127 + 1023;
+    return __longlong_as_double((long long)((e << 52) | ((unsigned long long)(u & 0x7fffff) << 29)));
+}
+__device__ __forceinline__ double rsqrt_nr(double q)
+{
+    if (!f32_range(q)) return rsqrt(q);
+    const float y0f = rsqrtf(seed_f32(q));
+    const double y0 = widen_f32(y0f), h0 = widen_f32(0.5f * y0f);
+    const double e = fma(-q * y0, y0, 1.0);  // 1 - q y0^2
+    return fma(h0, e, y0);
+}
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    if (__double_as_longlong(x) <= 0 || !f32_range(x)) return __drcp_rn(x);
+    const double r0 = widen_f32(__frcp_rn(seed_f32(x)));
+    return fma(r0, fma(-x, r0, 1.0), r0);
+}
+
 __device__ __forceinline__ double2 d2(double x, double y) { return make_double2(x, y); }
 __device__ __forceinline__ double2 add2(double2 a, double2 b) { return d2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 sub2(double2 a, double2 b) { return d2(a.x - b.x, a.y - b.y); }
@@ -137,7 +180,7 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
         const double dx = pn.x - pl.x, dy = pn.y - pl.y;
         const double q = fma(dx, dx, dy * dy);
         const bool pos = __double_as_longlong(q) > 0;
-        const double rs = rsqrt(q);
+        const double rs = rsqrt_nr(q);
         zero |= !pos;
         D[l] = pos ? q * rs : 0.0;
         IH[l] = rs;
@@ -185,7 +228,7 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
             const double B = 2.0 * (hprev + h);
             const bool first = (i == sj);
             const double den = first ? B : fma(-hprev, cp, B);
-            const double r = __drcp_rn(den);
+            const double r = rcp_nr(den);
             const double ncp = h * r;
             const double2 nyp = first ? scl2(R, r)
                                       : d2((R.x - hprev * yp.x) * r, (R.y - hprev * yp.y) * r);
@@ -295,7 +338,9 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
         }
         int l = lo;
         for (int k = k0; k < k1; ++k) {
-            const double st = pow2 ? k * LN : L * ((double)k / (double)Nout);
+            // (double)k without an FP64 conversion: k < 2^20 is exact in FP32
+            const double kd = k > 0 ? widen_f32(__int2float_rn(k)) : 0.0;
+            const double st = pow2 ? kd * LN : L * (kd / (double)Nout);
             const long long sb = __double_as_longlong(st);
             while (l + 1 < n && __double_as_longlong(U[l + 1]) <= sb) ++l;
             const int ln = (l + 1 == n) ? 0 : l + 1;
@@ -327,7 +372,7 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
             const double2 a = raw[k], b = raw[(k + 1 == Nout) ? 0 : k + 1];
             const double dx = b.x - a.x, dy = b.y - a.y;
             const double q = fma(dx, dx, dy * dy);
-            per_len += __double_as_longlong(q) > 0 ? q * rsqrt(q) : 0.0;
+            per_len += __double_as_longlong(q) > 0 ? q * rsqrt_nr(q) : 0.0;
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) per_len += __shfl_xor_sync(0xffffffffu, per_len, off);
