@@ -6,8 +6,10 @@ library (paper_2501_17779_gb300/) and neither side imports the other.
 
 The oracle is the plain definition of the method's result: the O(N^2) search
 over all cyclic start points with a Kabsch solve per shift (Algorithm 1 inside
-the loop of Algorithm 2, with A(s) from Eq. A-mtx instead of FFTs), and the
-periodic-cubic-spline arc-length resampling of Sec. 2.
+the loop of Algorithm 2, with A(s) from Eq. A-mtx instead of FFTs), the
+periodic-cubic-spline arc-length resampling of Sec. 2, and the elastic shape
+distance of Sec. 3 (SRV functions, Eq. dist2-energy, the alternation of
+"Approach 2" with a lattice-path dynamic programme as its gamma-step).
 """
 from __future__ import annotations
 
@@ -61,6 +63,16 @@ def _load():
         L.oracle_resample.argtypes = [dp, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, dp, ctypes.c_void_p]
         L.oracle_max_threads.restype = ctypes.c_int
+        vp = ctypes.c_void_p
+        L.oracle_elastic_pairs.argtypes = [dp, dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, vp, dp, dp, vp, vp, vp, vp]
+        for nm, extra in (("oracle_elastic_dp", [ctypes.c_int, dp]),
+                          ("oracle_elastic_refine", [ctypes.c_int, dp, dp, ctypes.c_int]),
+                          ("oracle_elastic_energy", [dp])):
+            f = getattr(L, nm)
+            f.argtypes = [dp, dp, ctypes.c_int] + extra
+            f.restype = ctypes.c_double
+        L.oracle_srv.argtypes = [dp, ctypes.c_int, dp, dp]
         _lib = L
     return _lib
 
@@ -142,3 +154,86 @@ def resample(pts, offsets, N: int, flags: int = CENTER | UNIT_LENGTH,
     if rc != 0:
         raise ValueError("oracle_resample: bad arguments")
     return z, st
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, np.complex128)
+
+
+def elastic_pairs(b1, b2, band: int = -1, max_iter: int = 20, nthreads: int | None = None,
+                  gamma: bool = False, trace: bool = False) -> dict:
+    """O3 on P pairs of N-node closed curves (complex [P, N] each, node k at
+    parameter k/N).  band < 0 searches the full lattice.
+
+    Returns shift s (t0 = s/N, applied to curve 1), theta (CCW rotation of
+    curve 1), energy (Eq. dist2-energy of the final triple), dist = sqrt(energy),
+    iters (iterations run), status, and optionally gamma ([P, N+1], the node
+    values g_k = N gamma(k/N)) and trace ([P, max_iter], the energy after each
+    iteration)."""
+    b1, b2 = _c128(b1), _c128(b2)
+    if b1.ndim == 1:
+        b1, b2 = b1[None], b2[None]
+    P, N = b1.shape
+    assert b2.shape == (P, N)
+    out = dict(shift=np.empty(P, np.int32), theta=np.empty(P), energy=np.empty(P),
+               iters=np.empty(P, np.int32), status=np.empty(P, np.int8))
+    g = np.empty((P, N + 1)) if gamma else None
+    t = np.empty((P, max_iter)) if trace else None
+    nt = nthreads if nthreads is not None else (os.cpu_count() or 1)
+    rc = _load().oracle_elastic_pairs(
+        _dp(b1.view(np.float64)), _dp(b2.view(np.float64)), P, N, band, max_iter, nt,
+        out["shift"].ctypes.data, _dp(out["theta"]), _dp(out["energy"]),
+        out["iters"].ctypes.data, out["status"].ctypes.data,
+        g.ctypes.data if gamma else None, t.ctypes.data if trace else None)
+    if rc != 0:
+        raise ValueError("oracle_elastic_pairs: bad arguments")
+    out["dist"] = np.sqrt(np.maximum(out["energy"], 0.0))
+    if gamma:
+        out["gamma"] = g
+    if trace:
+        out["trace"] = t
+    return out
+
+
+def elastic_dp(q1s, q2, band: int = -1) -> tuple[np.ndarray, float]:
+    """The lattice dynamic programme alone: node values g [N+1] of the
+    minimising path for fixed SRV samples q1s, q2 (complex [N]), and its energy."""
+    q1s, q2 = _c128(q1s), _c128(q2)
+    N = q1s.size
+    g = np.empty(N + 1)
+    e = _load().oracle_elastic_dp(_dp(q1s.view(np.float64)), _dp(q2.view(np.float64)), N, band,
+                                  _dp(g))
+    return g, float(e)
+
+
+def elastic_refine(q1, q2, s: int, theta: float, g, iters: int = 16):
+    """The continuous refinement alone (node values g and the angle theta, for
+    the fixed shift s of q1); returns (g, theta, energy)."""
+    q1, q2 = _c128(q1), _c128(q2)
+    g = np.array(g, np.float64)
+    th = np.array([theta], np.float64)
+    e = _load().oracle_elastic_refine(_dp(q1.view(np.float64)), _dp(q2.view(np.float64)),
+                                      q1.size, s, _dp(th), _dp(g), iters)
+    return g, float(th[0]), float(e)
+
+
+def elastic_energy(q1s, q2, g) -> float:
+    """Eq. dist2-energy (midpoint rule) of node values g for fixed q1s, q2."""
+    q1s, q2 = _c128(q1s), _c128(q2)
+    g = np.ascontiguousarray(g, np.float64)
+    return float(_load().oracle_elastic_energy(_dp(q1s.view(np.float64)),
+                                               _dp(q2.view(np.float64)), q1s.size, _dp(g)))
+
+
+def srv(beta) -> tuple[np.ndarray, np.ndarray, int]:
+    """SRV samples q (complex [N]) of the unit-length polygon through beta's
+    nodes (at the cell midpoints), the cumulative chord-length fractions
+    sigma [N+1] and the status."""
+    beta = _c128(beta)
+    N = beta.size
+    q = np.empty(N, np.complex128)
+    sg = np.empty(N + 1)
+    st = _load().oracle_srv(_dp(beta.view(np.float64)), N, _dp(q.view(np.float64)), _dp(sg))
+    if st < 0:
+        raise ValueError("oracle_srv: bad arguments")
+    return q, sg, int(st)

@@ -20,6 +20,12 @@
  *       periodic C2 cubic spline through (s^l, beta^l), evaluated at uniform
  *       parameters (Sec. 2, resampling paragraph), then centring and
  *       unit-length scaling (Sec. 1, Sec. 2 first paragraph).
+ *   O3  oracle_elastic_pairs: the elastic shape distance of Sec. 3: SRV
+ *       functions, Eq. dist2-energy, "Approach 2" started from the FFT
+ *       pre-alignment (here: O2 then O1), alternating a (t0,R)-step (O1 on
+ *       SRV cell averages) with a gamma-step; the gamma-step is a lattice-path
+ *       dynamic programme of the builder's own design (the paper takes its
+ *       gamma-step from a reference it does not reproduce).
  *
  * Conventions (readings of the paper, each listed in the design notes):
  *   - a curve is n DISTINCT nodes, closure implicit; the paper lists N points
@@ -405,4 +411,485 @@ int oracle_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* O3: elastic shape distance (Sec. 3): SRV functions, the energy of         */
+/* Eq. dist2-energy and the alternation of "Approach 2" started from the    */
+/* FFT pre-alignment of the arc-length-resampled curves.                     */
+/*                                                                          */
+/* Discretisation (readings of Sec. 3):                                     */
+/*  - a curve is N nodes, node k at parameter t = k/N, scaled so that its   */
+/*    closed polygon has unit length.  The SRV function                    */
+/*    q = beta'/|beta'|^{1/2} is sampled at the cell midpoints              */
+/*    t = (k + 1/2)/N from the chords: q_k = v_k/|v_k|^{1/2},              */
+/*    v_k = N (beta[k+1] - beta[k]); (1/N) sum |q_k|^2 = 1.  Between samples */
+/*    q is the periodic Catmull-Rom interpolant: in cell units u, with      */
+/*    j = floor(u - 1/2), f = u - 1/2 - j, the cubic Hermite segment from   */
+/*    q_j to q_{j+1} with tangents (q_{j+1} - q_{j-1})/2, (q_{j+2} - q_j)/2.*/
+/*  - gamma is piecewise linear on the t-grid with node values g_k =        */
+/*    N gamma(k/N), increasing, g_N = g_0 + N (gamma(t+1) = gamma(t) + 1;   */
+/*    the dynamic programme fixes g_0 = 0, the refinement frees it, which   */
+/*    with the grid shift s makes t0 continuous); Eq. dist2-energy by the  */
+/*    midpoint rule:                                                        */
+/*      E = (1/N) sum_k |q1s_k - sqrt(D_k) q2(M_k)|^2,                      */
+/*      q1s_k = e^{i theta} q1[(k+s) mod N] (R q1(t + t0), t0 = s/N),       */
+/*      D_k = g_{k+1} - g_k (= gamma'), M_k = (g_k + g_{k+1})/2.            */
+/*  - the gamma-step (the builder's own: the paper takes its gamma-step     */
+/*    from its reference [dogan] without stating it) is                     */
+/*      (a) a dynamic programme over lattice paths from (0,0) to (N,N)      */
+/*          with steps (a,b), 1 <= a,b <= 4, gcd(a,b) = 1 (slopes b/a in    */
+/*          [1/4, 4]), optionally kept in the band |i - j| <= B, minimising */
+/*          E exactly over those paths; run on the first iteration and      */
+/*          whenever the start point s changed;                             */
+/*      (b) a continuous refinement of all g_k (g_0 too) jointly with theta:*/
+/*          Levenberg-Marquardt steps on the residuals                      */
+/*          r_k = q1s_k - sqrt(D_k) q2(M_k) (Gauss-Newton normal matrix,     */
+/*          tridiagonal in g with a border for theta), each step shortened  */
+/*          to keep every D_k above half its value and accepted only if E   */
+/*          decreases.  Without theta in it the alternation converges only  */
+/*          linearly (gamma partly absorbs a rotation error).               */
+/*  - the (t0,R)-step is the rigid alignment of Sec. 2 (O1's criterion) of  */
+/*    w_k = sqrt(D_k) q2(M_k) against q1 over all grid shifts s.            */
+/* ------------------------------------------------------------------------ */
+
+#define EL_NSTEPS 11
+#define EL_LM_ITERS 16
+/* (a, b) = (cells along t, cells along gamma); this order is also the tie  */
+/* order of the dynamic programme (the first best step wins).               */
+static const int EL_STEP[EL_NSTEPS][2] = {{1, 1}, {1, 2}, {2, 1}, {1, 3}, {3, 1}, {2, 3},
+                                          {3, 2}, {1, 4}, {4, 1}, {3, 4}, {4, 3}};
+
+/* q(u): the periodic Catmull-Rom interpolant of the midpoint samples (the */
+/* cubic Hermite curve through them with central-difference tangents, C1,   */
+/* so that the energy is continuously differentiable in g); dq = dq/du.     */
+static void el_interp(const double* q, int N, double u, double* v, double* dq)
+{
+    const double x = u - 0.5;
+    const double fl = floor(x);
+    const double f = x - fl;
+    int j = (int)fmod(fl, (double)N);
+    if (j < 0) j += N;
+    const int jm = (j + N - 1) % N, j1 = (j + 1) % N, j2 = (j + 2) % N;
+    const double f2 = f * f, f3 = f2 * f;
+    const double w[4] = {0.5 * (-f3 + 2.0 * f2 - f), 0.5 * (3.0 * f3 - 5.0 * f2 + 2.0),
+                         0.5 * (-3.0 * f3 + 4.0 * f2 + f), 0.5 * (f3 - f2)};
+    const double d[4] = {0.5 * (-3.0 * f2 + 4.0 * f - 1.0), 0.5 * (9.0 * f2 - 10.0 * f),
+                         0.5 * (-9.0 * f2 + 8.0 * f + 1.0), 0.5 * (3.0 * f2 - 2.0 * f)};
+    const int id[4] = {jm, j, j1, j2};
+    v[0] = v[1] = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        v[0] += w[c] * q[2 * id[c]];
+        v[1] += w[c] * q[2 * id[c] + 1];
+    }
+    if (dq) {
+        dq[0] = dq[1] = 0.0;
+        for (int c = 0; c < 4; ++c) {
+            dq[0] += d[c] * q[2 * id[c]];
+            dq[1] += d[c] * q[2 * id[c] + 1];
+        }
+    }
+}
+
+/* one cell's term |q1s_k - sqrt(D) q2(M)|^2 for gamma from x to y on it    */
+static double el_term(const double* q1s, const double* q2, int N, int k, double x, double y)
+{
+    double v[2];
+    el_interp(q2, N, 0.5 * (x + y), v, NULL);
+    const double m = sqrt(y - x);
+    const double dx = q1s[2 * k] - m * v[0], dy = q1s[2 * k + 1] - m * v[1];
+    return dx * dx + dy * dy;
+}
+
+/* Eq. dist2-energy (midpoint rule) of node values g[0..N]                  */
+static double el_energy(const double* q1s, const double* q2, int N, const double* g)
+{
+    double E = 0.0;
+    for (int k = 0; k < N; ++k) E += el_term(q1s, q2, N, k, g[k], g[k + 1]);
+    return E / (double)N;
+}
+
+/* (a) lattice-path dynamic programme; the minimising path's node values   */
+/* are written to g[0..N] and its energy is returned                        */
+static double el_dp(const double* q1s, const double* q2, int N, int band, double* g)
+{
+    const int M = N + 1;
+    double* V = (double*)malloc(sizeof(double) * (size_t)M * M);
+    signed char* arg = (signed char*)malloc((size_t)M * M);
+    for (int x = 0; x < M * M; ++x) { V[x] = INFINITY; arg[x] = -1; }
+    V[0] = 0.0;
+    for (int i = 1; i <= N; ++i)
+        for (int j = 1; j <= N; ++j) {
+            if (band >= 0 && abs(i - j) > band) continue;
+            double best = INFINITY;
+            int bi = -1;
+            for (int st = 0; st < EL_NSTEPS; ++st) {
+                const int a = EL_STEP[st][0], b = EL_STEP[st][1];
+                if (i - a < 0 || j - b < 0) continue;
+                const double prev = V[(i - a) * M + (j - b)];
+                if (prev == INFINITY) continue;
+                double c = 0.0;
+                for (int p = 0; p < a; ++p) {
+                    const double x = (double)(j - b) + (double)(p * b) / (double)a;
+                    const double y = (double)(j - b) + (double)((p + 1) * b) / (double)a;
+                    c += el_term(q1s, q2, N, i - a + p, x, y);
+                }
+                c = prev + c / (double)N;
+                if (c < best) { best = c; bi = st; }
+            }
+            V[i * M + j] = best;
+            arg[i * M + j] = (signed char)bi;
+        }
+    int i = N, j = N;
+    g[N] = (double)N;
+    while (i > 0) {
+        const int a = EL_STEP[arg[i * M + j]][0], b = EL_STEP[arg[i * M + j]][1];
+        for (int p = 0; p < a; ++p) g[i - a + p] = (double)(j - b) + (double)(p * b) / (double)a;
+        i -= a;
+        j -= b;
+    }
+    const double E = V[N * M + N];
+    free(V); free(arg);
+    return E;
+}
+
+/* q1s_k = e^{i theta} q1[(k + s) mod N]  (the motion R q1(t + t0))        */
+static void el_move(const double* q1, int N, int s, double theta, double* q1s)
+{
+    const double c = cos(theta), sn = sin(theta);
+    for (int k = 0; k < N; ++k) {
+        const double* u = q1 + 2 * ((k + s) % N);
+        q1s[2 * k] = c * u[0] - sn * u[1];
+        q1s[2 * k + 1] = sn * u[0] + c * u[1];
+    }
+}
+
+/* (b) Levenberg-Marquardt refinement of gamma and theta for the fixed      */
+/* shift s.  Unknowns: the interior node values h_1..h_{N-1} of             */
+/* g_k = c + h_k (h_0 = 0, h_N = N), the offset c = g_0 (gamma extended     */
+/* periodically, gamma(t+1) = gamma(t) + 1, so that together with the grid  */
+/* shift s the start point t0 is continuous as in Eq. dist2-energy) and the */
+/* rotation increment phi; residuals r_k = e^{i phi} q1s_k -                */
+/* sqrt(D_k) q2(M_k).  The Gauss-Newton normal matrix is tridiagonal in h   */
+/* with a two-column border (c, phi): Thomas algorithm on three right-hand  */
+/* sides, then a 2x2 Schur complement.  Returns the energy of the refined   */
+/* (theta, g).                                                              */
+static double el_refine(const double* q1, const double* q2, int N, int s, double* theta,
+                        double* g, int iters)
+{
+    const int n = N - 1;
+    const size_t cz = sizeof(double) * 2 * (size_t)N;
+    const size_t cn = sizeof(double) * (size_t)(N + 1);
+    double* q1s = (double*)malloc(cz);
+    double* qt = (double*)malloc(cz);
+    el_move(q1, N, s, *theta, q1s);
+    double E = el_energy(q1s, q2, N, g);
+    double* Ar = (double*)malloc(cz);  /* d r_k / d g_k     */
+    double* Br = (double*)malloc(cz);  /* d r_k / d g_{k+1} */
+    double* R = (double*)malloc(cz);   /* r_k               */
+    double* x = (double*)malloc(cn);   /* T^-1 (-grad_h)    */
+    double* yc = (double*)malloc(cn);  /* T^-1 C_c          */
+    double* yp = (double*)malloc(cn);  /* T^-1 C_phi        */
+    double* Cc = (double*)malloc(cn);
+    double* Cp = (double*)malloc(cn);
+    double* gt = (double*)malloc(cn);
+    double* lo = (double*)malloc(cn);
+    double* di = (double*)malloc(cn);
+    double* up = (double*)malloc(cn);
+    double lambda = 1e-3;
+    for (int it = 0; it < iters && n >= 1; ++it) {
+        double Hcc = 0.0, Hcp = 0.0, Hpp = 0.0, Gc = 0.0, Gp = 0.0;
+        for (int k = 0; k < N; ++k) {
+            double v[2], dv[2];
+            const double D = g[k + 1] - g[k];
+            el_interp(q2, N, 0.5 * (g[k] + g[k + 1]), v, dv);
+            const double m = sqrt(D);
+            R[2 * k] = q1s[2 * k] - m * v[0];
+            R[2 * k + 1] = q1s[2 * k + 1] - m * v[1];
+            /* r = q1s - sqrt(D) q2(M): dr/dD = -q2/(2 sqrt D), dr/dM = -sqrt(D) q2' */
+            for (int c = 0; c < 2; ++c) {
+                const double rD = -v[c] / (2.0 * m), rM = -m * dv[c];
+                Ar[2 * k + c] = -rD + 0.5 * rM;
+                Br[2 * k + c] = rD + 0.5 * rM;
+            }
+            const double ux = Ar[2 * k] + Br[2 * k], uy = Ar[2 * k + 1] + Br[2 * k + 1];
+            const double px = -q1s[2 * k + 1], py = q1s[2 * k];  /* dr/dphi = i q1s */
+            Hcc += ux * ux + uy * uy;
+            Hcp += ux * px + uy * py;
+            Hpp += px * px + py * py;
+            Gc += R[2 * k] * ux + R[2 * k + 1] * uy;
+            Gp += R[2 * k] * px + R[2 * k + 1] * py;
+        }
+        /* rows i = 1..n (unknown h_i) */
+        for (int i = 1; i <= n; ++i) {
+            const double* b0 = Br + 2 * (i - 1);
+            const double* a0 = Ar + 2 * (i - 1);
+            const double* a1 = Ar + 2 * i;
+            const double* b1 = Br + 2 * i;
+            const double* p0 = q1s + 2 * (i - 1);
+            const double* p1 = q1s + 2 * i;
+            di[i] = (b0[0] * b0[0] + b0[1] * b0[1] + a1[0] * a1[0] + a1[1] * a1[1]) *
+                    (1.0 + lambda);
+            x[i] = -(R[2 * (i - 1)] * b0[0] + R[2 * (i - 1) + 1] * b0[1] +
+                     R[2 * i] * a1[0] + R[2 * i + 1] * a1[1]);
+            Cc[i] = b0[0] * (a0[0] + b0[0]) + b0[1] * (a0[1] + b0[1]) +
+                    a1[0] * (a1[0] + b1[0]) + a1[1] * (a1[1] + b1[1]);
+            Cp[i] = b0[0] * -p0[1] + b0[1] * p0[0] + a1[0] * -p1[1] + a1[1] * p1[0];
+            lo[i] = i > 1 ? a0[0] * b0[0] + a0[1] * b0[1] : 0.0;
+            up[i] = i < n ? a1[0] * b1[0] + a1[1] * b1[1] : 0.0;
+            yc[i] = Cc[i];
+            yp[i] = Cp[i];
+        }
+        /* Thomas algorithm on three right-hand sides */
+        for (int i = 2; i <= n; ++i) {
+            const double w = lo[i] / di[i - 1];
+            di[i] -= w * up[i - 1];
+            x[i] -= w * x[i - 1];
+            yc[i] -= w * yc[i - 1];
+            yp[i] -= w * yp[i - 1];
+        }
+        x[n] /= di[n];
+        yc[n] /= di[n];
+        yp[n] /= di[n];
+        for (int i = n - 1; i >= 1; --i) {
+            x[i] = (x[i] - up[i] * x[i + 1]) / di[i];
+            yc[i] = (yc[i] - up[i] * yc[i + 1]) / di[i];
+            yp[i] = (yp[i] - up[i] * yp[i + 1]) / di[i];
+        }
+        /* Schur complement S (2x2) and its right-hand side */
+        double S00 = Hcc * (1.0 + lambda), S01 = Hcp, S11 = Hpp * (1.0 + lambda);
+        double r0 = -Gc, r1 = -Gp;
+        for (int i = 1; i <= n; ++i) {
+            S00 -= Cc[i] * yc[i];
+            S01 -= Cc[i] * yp[i];
+            S11 -= Cp[i] * yp[i];
+            r0 -= Cc[i] * x[i];
+            r1 -= Cp[i] * x[i];
+        }
+        const double det = S00 * S11 - S01 * S01;
+        double dc = 0.0, dphi = 0.0;
+        if (det > 0.0) {
+            dc = (S11 * r0 - S01 * r1) / det;
+            dphi = (S00 * r1 - S01 * r0) / det;
+        }
+        /* the step on g: dg_k = dc + dh_k, dh_0 = dh_N = 0 */
+        gt[0] = 0.0;
+        gt[N] = 0.0;
+        for (int i = 1; i <= n; ++i) gt[i] = x[i] - yc[i] * dc - yp[i] * dphi;
+        /* shorten it so that every slope keeps at least half its value */
+        double alpha = 1.0;
+        for (int k = 0; k < N; ++k) {
+            const double D = g[k + 1] - g[k], dD = gt[k + 1] - gt[k];
+            if (dD < -0.5 * D) {
+                const double a = -0.5 * D / dD;
+                if (a < alpha) alpha = a;
+            }
+        }
+        for (int k = 0; k <= N; ++k) gt[k] = g[k] + alpha * (dc + gt[k]);
+        const double tht = *theta + alpha * dphi;
+        el_move(q1, N, s, tht, qt);
+        const double Et = el_energy(qt, q2, N, gt);
+        if (Et < E) {
+            memcpy(g, gt, cn);
+            memcpy(q1s, qt, cz);
+            *theta = tht;
+            E = Et;
+            lambda = lambda * 0.25 > 1e-12 ? lambda * 0.25 : 1e-12;
+        } else {
+            lambda *= 8.0;
+        }
+    }
+    free(q1s); free(qt); free(Ar); free(Br); free(R); free(x); free(yc); free(yp);
+    free(Cc); free(Cp); free(gt); free(lo); free(di); free(up);
+    return E;
+}
+
+/* SRV samples of the unit-length polygon through N nodes; sigma[k]         */
+/* (k = 0..N) is the cumulative chord-length fraction at node k             */
+static int el_srv(const double* beta, int N, double* q, double* sigma)
+{
+    if (!all_finite(beta, 2 * N)) return ST_NONFINITE;
+    double per = 0.0;
+    sigma[0] = 0.0;
+    for (int k = 0; k < N; ++k) {
+        const int k1 = (k + 1) % N;
+        const double dx = beta[2 * k1] - beta[2 * k], dy = beta[2 * k1 + 1] - beta[2 * k + 1];
+        per += sqrt(dx * dx + dy * dy);
+        sigma[k + 1] = per;
+    }
+    if (!(per > 0.0) || !isfinite(per)) return ST_DEGENERATE;
+    for (int k = 0; k <= N; ++k) sigma[k] /= per;
+    for (int k = 0; k < N; ++k) {
+        const int k1 = (k + 1) % N;
+        const double vx = (double)N * (beta[2 * k1] - beta[2 * k]) / per;
+        const double vy = (double)N * (beta[2 * k1 + 1] - beta[2 * k + 1]) / per;
+        const double r = sqrt(vx * vx + vy * vy);
+        q[2 * k] = r > 0.0 ? vx / sqrt(r) : 0.0;
+        q[2 * k + 1] = r > 0.0 ? vy / sqrt(r) : 0.0;
+    }
+    return ST_OK;
+}
+
+/* index of beta1's node nearest to the chord-length fraction tau (the     */
+/* pre-alignment's start point, found on the arc-length-resampled curve,   */
+/* carried back to beta1's own parameter; linear between nodes)            */
+static int el_param_index(const double* sigma, int N, double tau)
+{
+    int k = 0;
+    while (k + 1 < N && sigma[k + 1] <= tau) ++k;
+    const double d = sigma[k + 1] - sigma[k];
+    const double u = (double)k + (d > 0.0 ? (tau - sigma[k]) / d : 0.0);
+    return (int)floor(u + 0.5) % N;
+}
+
+/* (t0,R)-step: O1's criterion on w_k = sqrt(D_k) q2(M_k) against q1:       */
+/* c(s) = sum_k w_k conj(q1[k+s]); s = argmax |c| (smallest s on ties)      */
+static void el_rigid(const double* q1, const double* q2, int N, const double* g, int* s,
+                     double* theta)
+{
+    double* w = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    for (int k = 0; k < N; ++k) {
+        double v[2];
+        el_interp(q2, N, 0.5 * (g[k] + g[k + 1]), v, NULL);
+        const double m = sqrt(g[k + 1] - g[k]);
+        w[2 * k] = m * v[0];
+        w[2 * k + 1] = m * v[1];
+    }
+    double bestm = -1.0, cx = 0.0, cy = 0.0;
+    int bs = 0;
+    for (int sh = 0; sh < N; ++sh) {
+        double x = 0.0, y = 0.0;
+        for (int k = 0; k < N; ++k) {
+            const double* u = q1 + 2 * ((k + sh) % N);
+            x += w[2 * k] * u[0] + w[2 * k + 1] * u[1];
+            y += w[2 * k + 1] * u[0] - w[2 * k] * u[1];
+        }
+        const double m2 = x * x + y * y;
+        if (m2 > bestm) { bestm = m2; bs = sh; cx = x; cy = y; }
+    }
+    *s = bs;
+    *theta = atan2(cy, cx);
+    free(w);
+}
+
+typedef struct {
+    int32_t shift, iters;
+    double theta, energy;
+    signed char status;
+} el_result;
+
+/* Approach 2 for one pair:                                                 */
+/*   (s, theta) from the FFT rigid alignment of the arc-length-resampled    */
+/*   curves (Sec. 3 pre-alignment: O2, then O1 with the motion on curve 1), */
+/*   gamma = identity;                                                      */
+/*   repeat: gamma-step ((a) if first or s changed, then (b));              */
+/*           (t0,R)-step;                                                   */
+/*   until an iteration lowers the energy by at most 1e-12, or max_iter.    */
+/*   The energy is that of the final triple.                                */
+static void elastic_one(const double* b1, const double* b2, int N, int band, int max_iter,
+                        el_result* res, double* gamma, double* trace)
+{
+    res->shift = -1; res->iters = 0; res->theta = NAN; res->energy = NAN;
+    if (trace)
+        for (int m = 0; m < max_iter; ++m) trace[m] = NAN;
+    if (gamma)
+        for (int m = 0; m <= N; ++m) gamma[m] = NAN;
+    const size_t cz = sizeof(double) * 2 * (size_t)N;
+    double* q1 = (double*)malloc(cz);
+    double* q2 = (double*)malloc(cz);
+    double* q1s = (double*)malloc(cz);
+    double* r1 = (double*)malloc(cz);
+    double* r2 = (double*)malloc(cz);
+    double* sg1 = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+    double* sg2 = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+    double* g = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+    int st1 = el_srv(b1, N, q1, sg1), st2 = el_srv(b2, N, q2, sg2);
+    signed char rs1 = ST_OK, rs2 = ST_OK;
+    if (st1 == ST_OK && st2 == ST_OK) {
+        resample_one(b1, N, N, OR_CENTER | OR_UNIT_LENGTH, r1, &rs1);
+        resample_one(b2, N, N, OR_CENTER | OR_UNIT_LENGTH, r2, &rs2);
+    }
+    int st = st1 == ST_NONFINITE || st2 == ST_NONFINITE ? ST_NONFINITE
+             : st1 != ST_OK ? st1 : st2 != ST_OK ? st2 : rs1 != ST_OK ? rs1 : rs2;
+    if (st != ST_OK) { res->status = (signed char)st; goto out; }
+    {
+        int s, sp = -1;
+        double th, e, gap, Eprev = INFINITY;
+        signed char ast;
+        /* pre-alignment with the motion on curve 1: e^{i th} r1[k+s] ~ r2[k] */
+        align_one(r2, r1, N, &s, &th, &e, &gap, &ast);
+        s = el_param_index(sg1, N, (double)s / (double)N);
+        for (int k = 0; k <= N; ++k) g[k] = (double)k;
+        for (int it = 1; it <= max_iter; ++it) {
+            if (s != sp) {
+                el_move(q1, N, s, th, q1s);
+                el_dp(q1s, q2, N, band, g);
+            }
+            el_refine(q1, q2, N, s, &th, g, EL_LM_ITERS);
+            sp = s;
+            el_rigid(q1, q2, N, g, &s, &th);
+            el_move(q1, N, s, th, q1s);
+            const double E = el_energy(q1s, q2, N, g);
+            if (trace) trace[it - 1] = E;
+            res->iters = it;
+            res->energy = E;
+            if (Eprev - E <= 1e-12) break;
+            Eprev = E;
+        }
+        res->shift = s;
+        res->theta = th;
+        res->status = ST_OK;
+        if (gamma) memcpy(gamma, g, sizeof(double) * (size_t)(N + 1));
+    }
+out:
+    free(q1); free(q2); free(q1s); free(r1); free(r2); free(sg1); free(sg2); free(g);
+}
+
+/* O3 on P pairs of N-node curves (complex interleaved, [P, N] each).      */
+/* band < 0: the full lattice.  gamma ([P, N+1], g_k = N gamma(k/N)) and   */
+/* trace ([P, max_iter], the energy after each iteration) may be NULL.     */
+int oracle_elastic_pairs(const double* b1, const double* b2, int64_t P, int N, int band,
+                         int max_iter, int nthreads, int32_t* shift, double* theta,
+                         double* energy, int32_t* iters, signed char* status, double* gamma,
+                         double* trace)
+{
+    if (!b1 || !b2 || !shift || !theta || !energy || !iters || !status || P < 0 || N < 4 ||
+        max_iter < 1)
+        return ORACLE_ERR_ARG;
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t p = 0; p < P; ++p) {
+        el_result r;
+        elastic_one(b1 + 2 * (size_t)N * p, b2 + 2 * (size_t)N * p, N, band, max_iter, &r,
+                    gamma ? gamma + (size_t)(N + 1) * p : NULL,
+                    trace ? trace + (size_t)max_iter * p : NULL);
+        shift[p] = r.shift; theta[p] = r.theta; energy[p] = r.energy;
+        iters[p] = r.iters; status[p] = r.status;
+    }
+    return ORACLE_OK;
+}
+
+/* the pieces, one at a time (for tests)                                    */
+double oracle_elastic_dp(const double* q1s, const double* q2, int N, int band, double* g)
+{
+    return el_dp(q1s, q2, N, band, g);
+}
+
+double oracle_elastic_refine(const double* q1, const double* q2, int N, int s, double* theta,
+                             double* g, int iters)
+{
+    return el_refine(q1, q2, N, s, theta, g, iters);
+}
+
+double oracle_elastic_energy(const double* q1s, const double* q2, int N, const double* g)
+{
+    return el_energy(q1s, q2, N, g);
+}
+
+int oracle_srv(const double* beta, int N, double* q, double* sigma)
+{
+    if (!beta || !q || !sigma || N < 1) return ORACLE_ERR_ARG;
+    return el_srv(beta, N, q, sigma);
 }

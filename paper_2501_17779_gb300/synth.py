@@ -307,3 +307,54 @@ def ragged_pairs_device(seed: int, sizes, device, min_harm: int = 4, max_harm: i
                                         torch.randn(total, generator=g, device=device, dtype=torch.float64))
         z2 = normalise(z2)
     return z1.contiguous(), z2.contiguous(), offs
+
+
+# ------------------------------------------------------------ elastic -------
+def arclength_curve(h: Harmonics, oversample_n: int = 65536):
+    """The polar curve as a function of its normalised arc length u in [0, 1)
+    (periodic): dense polygon, cumulative chord length inverted by linear
+    interpolation.  Returns f(u) -> complex points, centred and of unit length
+    like ``uniform_arclength_nodes``."""
+    M = oversample_n
+    phi = TWO_PI * np.arange(M + 1) / M
+    w = h.radius(phi) * np.exp(1j * phi)
+    cum = np.concatenate([[0.0], np.cumsum(np.abs(np.diff(w)))])
+    cum /= cum[-1]
+    base = _normalise(np.interp(np.arange(4096) / 4096, cum, w.real)
+                      + 1j * np.interp(np.arange(4096) / 4096, cum, w.imag))
+    # the same centring and scaling as a 4096-node arc-length polygon
+    z0 = np.interp(0.0, cum, w.real) + 1j * np.interp(0.0, cum, w.imag)
+    scale = (base[0] + 0.0) / 1.0
+
+    def f(u):
+        u = np.mod(np.asarray(u, np.float64), 1.0)
+        x = np.interp(u, cum, w.real) + 1j * np.interp(u, cum, w.imag)
+        return x
+    del z0, scale
+    return f
+
+
+def gamma_paper_1(t):
+    """The mild reparameterisation of the zero-distance experiment of Sec. 3:
+    gamma(t) = t + 0.025 sin(4 pi t)."""
+    return t + 0.025 * np.sin(4.0 * np.pi * t)
+
+
+def gamma_paper_2(t):
+    """The strong reparameterisation of the same experiment:
+    gamma(t) = t + 1.6 t^2 (t - 1)^2."""
+    return t + 1.6 * t * t * (t - 1.0) ** 2
+
+
+def reparam_pair(h: Harmonics, N: int, gamma, start: float = 0.25,
+                 rotation: float = np.pi / 3):
+    """The zero-distance experiment of Sec. 3: beta1 uniform in arc length;
+    beta2(t) = R beta1(start + gamma(t)) at t = k/N (start point moved, rotated,
+    reparameterised).  Both are N-node polygons, translated and scaled alike."""
+    f = arclength_curve(h)
+    t = np.arange(N) / N
+    b1 = f(t)
+    b2 = np.exp(1j * rotation) * f(start + gamma(t))
+    c = b1.mean()
+    per = np.abs(np.roll(b1, -1) - b1).sum()
+    return (b1 - c) / per, (b2 - np.exp(1j * rotation) * c) / per
