@@ -438,8 +438,8 @@ int oracle_max_threads(void)
 /*  - the gamma-step (the builder's own: the paper takes its gamma-step     */
 /*    from its reference [dogan] without stating it) is                     */
 /*      (a) a dynamic programme over lattice paths from (0,0) to (N,N)      */
-/*          with steps (a,b), 1 <= a,b <= 4, gcd(a,b) = 1 (slopes b/a in    */
-/*          [1/4, 4]), optionally kept in the band |i - j| <= B, minimising */
+/*          with steps (a,b), 1 <= a,b <= 3, gcd(a,b) = 1 (slopes b/a in    */
+/*          [1/3, 3]), optionally kept in the band |i - j| <= B, minimising */
 /*          E exactly over those paths; run on the first iteration and      */
 /*          whenever the start point s changed;                             */
 /*      (b) a continuous refinement of all g_k (g_0 too) jointly with theta:*/
@@ -453,12 +453,12 @@ int oracle_max_threads(void)
 /*    w_k = sqrt(D_k) q2(M_k) against q1 over all grid shifts s.            */
 /* ------------------------------------------------------------------------ */
 
-#define EL_NSTEPS 11
+#define EL_NSTEPS 7
 #define EL_LM_ITERS 16
 /* (a, b) = (cells along t, cells along gamma); this order is also the tie  */
 /* order of the dynamic programme (the first best step wins).               */
 static const int EL_STEP[EL_NSTEPS][2] = {{1, 1}, {1, 2}, {2, 1}, {1, 3}, {3, 1}, {2, 3},
-                                          {3, 2}, {1, 4}, {4, 1}, {3, 4}, {4, 3}};
+                                          {3, 2}};
 
 /* q(u): the periodic Catmull-Rom interpolant of the midpoint samples (the */
 /* cubic Hermite curve through them with central-difference tangents, C1,   */

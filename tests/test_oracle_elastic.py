@@ -16,7 +16,7 @@ import oracle
 from paper_2501_17779_gb300 import synth
 
 GOLD = Path(__file__).parent / "golden"
-STEPS = [(a, b) for a in range(1, 5) for b in range(1, 5) if gcd(a, b) == 1]
+STEPS = [(a, b) for a in range(1, 4) for b in range(1, 4) if gcd(a, b) == 1]
 
 
 def _curve(seed, N, n_harm=6):
