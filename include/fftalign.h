@@ -188,6 +188,57 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
                        int8_t* status, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Elastic shape distance (Sec. 3): for each pair p, curve idx1[p] of set 1
+ * against curve idx2[p] of set 2, the minimum over (t0, R, gamma) of
+ * Eq. dist2-energy, E = int |R q1(t + t0) - sqrt(gamma') q2(gamma(t))|^2 dt,
+ * with q = beta'/|beta'|^{1/2} the SRV functions of the unit-length curves,
+ * by "Approach 2" started from the FFT pre-alignment (Sec. 3): the curves are
+ * resampled in arc length and rigidly aligned (Algorithm 2, motion on curve
+ * 1); then gamma-steps and (t0,R)-steps (Algorithm 2 applied to SRV
+ * functions, without resampling) alternate until an iteration lowers E by at
+ * most 1e-12 or max_iter iterations have run.  The gamma-step is this
+ * library's own (the paper takes it from a reference it does not state): a
+ * dynamic programme over lattice paths with steps (a,b), a,b <= 3, coprime,
+ * in the band |i - j| <= band, run when the start point changed, followed by
+ * 16 Levenberg-Marquardt steps on gamma's node values, its offset and theta.
+ *
+ * Discretisation: a curve is N nodes, node k at parameter k/N (its own
+ * parameterisation, not resampled), closed, scaled to unit polygon length;
+ * q is sampled at the cell midpoints from the chords and read between samples
+ * by the periodic Catmull-Rom cubic; gamma is piecewise linear with node
+ * values g_k = N gamma(k/N), g_N = g_0 + N; E is taken by the midpoint rule.
+ *
+ *   curves1    [M1][N] complex128 (device): set 1 (moved by (t0, R))
+ *   curves2    [M2][N] complex128 (device): set 2 (reparameterised by gamma)
+ *   N          nodes per curve, a power of two in [8, 1024]
+ *   idx1, idx2 int64[P] (device) curve indices into the sets, or NULL for
+ *              pair p = (p, p) (then M1, M2 >= P); an index out of range gives
+ *              status FA_STATUS_BAD_SIZE for that pair
+ *   band       half-width B of the lattice band, -1 (or >= N) for the full
+ *              lattice; the refinement is not confined to it
+ *   max_iter   iterations at most, in [1, 1000]
+ *   shift      int32[P]   s, t0 = s/N (-1 when status != 0)
+ *   theta      double[P]  CCW angle of R applied to curve 1 (NaN when status != 0)
+ *   energy     double[P]  E of the final triple (the distance is sqrt(E))
+ *   gamma      double[P][N+1] node values g_k, or NULL
+ *   iters      int32[P]   iterations run, or NULL
+ *   status     int8[P]    FA_STATUS_OK, _DEGENERATE (a curve of zero length or
+ *              fewer than 4 distinct nodes), _NONFINITE, _BAD_SIZE
+ *   workspace  device scratch of fa_elastic_workspace_size(h, M1, M2, P, N, band)
+ *              bytes, 256-byte aligned, or NULL for the handle's own
+ * Returns FA_OK, FA_ERR_INVALID_ARG, FA_ERR_UNSUPPORTED, FA_ERR_WORKSPACE or
+ * FA_ERR_CUDA.  Asynchronous on stream; graph-capturable when a workspace is
+ * passed.
+ */
+size_t fa_elastic_workspace_size(fa_handle* h, int64_t M1, int64_t M2, int64_t P, int32_t N,
+                                 int32_t band);
+int fa_elastic_distance(fa_handle* h, const double* curves1, int64_t M1, const double* curves2,
+                        int64_t M2, int32_t N, const int64_t* idx1, const int64_t* idx2,
+                        int64_t P, int32_t band, int32_t max_iter, int32_t* shift,
+                        double* theta, double* energy, double* gamma, int32_t* iters,
+                        int8_t* status, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Alignment of P pairs with DIFFERENT node counts in one persistent launch.
  *
  * Pair p is z1[offsets[p] .. offsets[p+1]) and z2[offsets[p] .. offsets[p+1])

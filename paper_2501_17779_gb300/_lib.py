@@ -38,7 +38,7 @@ EXPORTS = (
     "fa_align_curves_host", "fa_resample_arclength_noalloc",
     "fa_align_all_pairs_workspace_size", "fa_align_all_pairs",
     "fa_align_pairs_ragged_workspace_size", "fa_align_pairs_ragged",
-    "fa_align_pairs_ragged_autotune",
+    "fa_align_pairs_ragged_autotune", "fa_elastic_workspace_size", "fa_elastic_distance",
 )
 STATUS_BAD_SIZE = 3
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -100,6 +100,11 @@ def load(build_if_missing: bool = False):
     L.fa_align_pairs_ragged_autotune.restype = ctypes.c_int
     L.fa_resample_arclength_noalloc.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp]
     L.fa_resample_arclength_noalloc.restype = ctypes.c_int
+    L.fa_elastic_workspace_size.argtypes = [vp, i64, i64, i64, i32, i32]
+    L.fa_elastic_workspace_size.restype = sz
+    L.fa_elastic_distance.argtypes = [vp, vp, i64, vp, i64, i32, vp, vp, i64, i32, i32, vp, vp, vp,
+                                      vp, vp, vp, vp, sz, vp]
+    L.fa_elastic_distance.restype = ctypes.c_int
     _lib = L
     return L
 

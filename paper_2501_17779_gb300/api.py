@@ -216,6 +216,64 @@ def ragged_workspace_size(P: int, max_n: int, device: int | None = None) -> int:
     return int(L.fa_align_pairs_ragged_workspace_size(handle(device), P, max_n))
 
 
+def elastic_workspace_size(M1: int, M2: int, P: int, N: int, band: int = -1,
+                           device: int | None = None) -> int:
+    L = _lib.load()
+    return int(L.fa_elastic_workspace_size(handle(device), M1, M2, P, N, band))
+
+
+def elastic_distance(curves1: torch.Tensor, curves2: torch.Tensor, *,
+                     idx1: torch.Tensor | None = None, idx2: torch.Tensor | None = None,
+                     band: int = -1, max_iter: int = 20, gamma: bool = False,
+                     workspace: torch.Tensor | None = None, out: tuple | None = None):
+    """Elastic shape distance (fa_elastic_distance).
+
+    curves1 [M1, N], curves2 [M2, N]: complex128 CUDA tensors, node k of a curve
+    at parameter k/N.  Pair p is (idx1[p], idx2[p]) (int64 CUDA tensors) or,
+    without them, (p, p).  Returns (shift int32, theta, energy, iters int32,
+    status int8) [P] each, plus gamma [P, N+1] when ``gamma``; the distance is
+    sqrt(energy).
+    """
+    _need_cuda("curves1", curves1, torch.complex128)
+    _need_cuda("curves2", curves2, torch.complex128)
+    if curves1.dim() != 2 or curves2.dim() != 2 or curves1.shape[1] != curves2.shape[1]:
+        raise ValueError("curves1, curves2 must be [M1, N], [M2, N]")
+    M1, N = curves1.shape
+    M2 = curves2.shape[0]
+    if (idx1 is None) != (idx2 is None):
+        raise ValueError("give both index arrays or neither")
+    if idx1 is not None:
+        _need_cuda("idx1", idx1, torch.int64)
+        _need_cuda("idx2", idx2, torch.int64)
+        P = idx1.numel()
+        if idx2.numel() != P:
+            raise ValueError("idx1 and idx2 differ in length")
+    else:
+        P = min(M1, M2)
+    dev = curves1.device
+    if out is None:
+        shift = torch.empty(P, dtype=torch.int32, device=dev)
+        theta = torch.empty(P, dtype=torch.float64, device=dev)
+        energy = torch.empty(P, dtype=torch.float64, device=dev)
+        iters = torch.empty(P, dtype=torch.int32, device=dev)
+        status = torch.empty(P, dtype=torch.int8, device=dev)
+    else:
+        shift, theta, energy, iters, status = out
+    g = torch.empty((P, N + 1), dtype=torch.float64, device=dev) if gamma else None
+    L = _lib.load()
+    h = handle(dev.index)
+    need = int(L.fa_elastic_workspace_size(h, M1, M2, P, N, band))
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    rc = L.fa_elastic_distance(h, _ptr(curves1), M1, _ptr(curves2), M2, N, _ptr(idx1),
+                               _ptr(idx2), P, band, max_iter, _ptr(shift), _ptr(theta),
+                               _ptr(energy), _ptr(g), _ptr(iters), _ptr(status), _ptr(workspace),
+                               workspace.numel(), _stream_ptr(dev))
+    _lib.check(rc)
+    res = (shift, theta, energy, iters, status)
+    return res + (g,) if gamma else res
+
+
 def align_curves_host(pts: torch.Tensor, offsets: torch.Tensor, N: int, *, method: str = "fft",
                       prec: str = "fp64", fp32_storage: bool = False, out: tuple | None = None,
                       device: int | None = None):

@@ -426,6 +426,55 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
                             static_cast<cudaStream_t>(stream));
 }
 
+size_t fa_elastic_workspace_size(fa_handle* h, int64_t M1, int64_t M2, int64_t P, int32_t N,
+                                  int32_t band)
+{
+    if (!h || M1 < 0 || M2 < 0 || P < 0 || N < 8 || N > kMaxElasticN || (N & (N - 1))) return 0;
+    return elastic_ws_bytes(h, M1, M2, P, N, band);
+}
+
+int fa_elastic_distance(fa_handle* h, const double* curves1, int64_t M1, const double* curves2,
+                        int64_t M2, int32_t N, const int64_t* idx1, const int64_t* idx2,
+                        int64_t P, int32_t band, int32_t max_iter, int32_t* shift,
+                        double* theta, double* energy, double* gamma, int32_t* iters,
+                        int8_t* status, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: null handle");
+    if (M1 < 0 || M2 < 0 || P < 0)
+        return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: negative size");
+    if (N < 8 || N > kMaxElasticN || (N & (N - 1)))
+        return set_error(FA_ERR_UNSUPPORTED,
+                         "fa_elastic_distance: N must be a power of two in [8, 1024]");
+    if (max_iter < 1 || max_iter > 1000)
+        return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: max_iter outside [1, 1000]");
+    if (band < -1) return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: band < -1");
+    if ((!idx1 && M1 < P) || (!idx2 && M2 < P))
+        return set_error(FA_ERR_INVALID_ARG,
+                         "fa_elastic_distance: without index arrays each set needs P curves");
+    if (M1 > ((int64_t)1 << 32) || M2 > ((int64_t)1 << 32) || P > ((int64_t)1 << 40))
+        return set_error(FA_ERR_UNSUPPORTED, "fa_elastic_distance: size too large");
+    if (P == 0) return FA_OK;
+    if (!curves1 || !curves2 || !shift || !theta || !energy || !status || M1 == 0 || M2 == 0)
+        return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: null pointer or empty set");
+    DeviceGuard g(h->device);
+    if (g.rc != FA_OK) return g.rc;
+    const size_t need = elastic_ws_bytes(h, M1, M2, P, N, band);
+    void* ws = workspace;
+    if (ws) {
+        if (workspace_bytes < need)
+            return set_error(FA_ERR_WORKSPACE, "fa_elastic_distance: workspace too small");
+        if (reinterpret_cast<uintptr_t>(ws) & 255)
+            return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: workspace not 256-aligned");
+    } else {
+        const int rc = ensure_ws(h, need);
+        if (rc != FA_OK) return rc;
+        ws = h->ws;
+    }
+    return launch_elastic(h, curves1, M1, curves2, M2, N, idx1, idx2, P, band, max_iter, shift,
+                          theta, energy, gamma, iters, status, ws,
+                          static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"
 
 extern "C" int fa_align_curves_host(fa_handle* h, const double* pts, const int64_t* offsets,

@@ -31,6 +31,7 @@ namespace fa {
 constexpr int kMinLogN = 2;
 constexpr int kMaxLogN = 12;
 constexpr int kMaxDirectN = 4096;
+constexpr int kMaxElasticN = 1024;
 constexpr int kMaxRaggedN = 8192;      // largest node count of fa_align_pairs_ragged
 constexpr int kMaxRaggedLogL = 14;     // its longest transform, 2^14
 
@@ -103,5 +104,10 @@ int launch_resample(const fa_handle* h, const double* pts, const int64_t* offset
                     cudaStream_t st);
 size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags);
 int build_twiddles(fa_handle* h);
+size_t elastic_ws_bytes(const fa_handle* h, int64_t M1, int64_t M2, int64_t P, int N, int band);
+int launch_elastic(const fa_handle* h, const double* set1, int64_t M1, const double* set2,
+                   int64_t M2, int N, const int64_t* idx1, const int64_t* idx2, int64_t P,
+                   int band, int max_iter, int32_t* shift, double* theta, double* energy,
+                   double* gamma, int32_t* iters, int8_t* status, void* ws, cudaStream_t st);
 
 }  // namespace fa
