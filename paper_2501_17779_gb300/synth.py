@@ -358,3 +358,74 @@ def reparam_pair(h: Harmonics, N: int, gamma, start: float = 0.25,
     c = b1.mean()
     per = np.abs(np.roll(b1, -1) - b1).sum()
     return (b1 - c) / per, (b2 - np.exp(1j * rotation) * c) / per
+
+
+@dataclass
+class ShapeGallery:
+    curves: np.ndarray   # complex128 [M, N], node k at parameter k/N
+    labels: np.ndarray   # int32 [M] class template of each curve
+
+
+def shape_gallery(seed: int, M: int, N: int = 256, n_classes: int = 50, n_harm: int = 8,
+                  sigma: float = 0.03, reparam: float = 0.3, device: str = "cpu",
+                  dense: int = 4096) -> ShapeGallery:
+    """Curves for elastic k-NN retrieval: ``n_classes`` Fourier-series templates
+    (as ``random_harmonics``); each instance belongs to a uniformly drawn class,
+    perturbs its template's harmonics (a_k += sigma N(0,1)/k,
+    phi_k += sigma N(0,1)), starts at a random point, is rotated by a random
+    angle and is sampled at t = k/N through a random smooth monotone
+    reparameterisation gamma(t) = t + sum_{m=1..3} b_m sin(2 pi m t)/(2 pi m),
+    sum |b_m| <= ``reparam`` < 1 (so gamma' > 0).  The arc-length inversion
+    runs batched in torch on ``device`` (a dense polygon of ``dense`` angles per
+    curve, linear interpolation of its cumulative chord length).  Returns
+    numpy arrays."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    trng = np.random.default_rng(10_000 + n_classes)  # templates depend on n_classes only
+    temps = [random_harmonics(trng, n_harm) for _ in range(n_classes)]
+    TA = np.stack([h.a for h in temps])
+    TP = np.stack([h.ph for h in temps])
+    k = np.arange(1, n_harm + 1)
+    cls = rng.integers(0, n_classes, M)
+    a = TA[cls] + sigma * rng.normal(size=(M, n_harm)) / k
+    ph = TP[cls] + sigma * rng.normal(size=(M, n_harm))
+    b = rng.uniform(-1.0, 1.0, (M, 3))
+    b *= (reparam * rng.uniform(0.0, 1.0, M) / np.abs(b).sum(axis=1))[:, None]
+    start = rng.uniform(0.0, 1.0, M)
+    rot = rng.uniform(0.0, TWO_PI, M)
+    dev = torch.device(device)
+    f64 = torch.float64
+    phi = torch.arange(dense + 1, dtype=f64, device=dev) * (TWO_PI / dense)
+    kk = torch.as_tensor(k, dtype=f64, device=dev)
+    C = torch.cos(kk[:, None] * phi[None, :])
+    S = torch.sin(kk[:, None] * phi[None, :])
+    A = torch.as_tensor(a, dtype=f64, device=dev)
+    Ph = torch.as_tensor(ph, dtype=f64, device=dev)
+    pert = (A * torch.cos(Ph)) @ C - (A * torch.sin(Ph)) @ S           # [M, dense+1]
+    # keep the curve star-shaped: r >= 0.25
+    pmin = pert.min(dim=1).values
+    scale = torch.where(1.0 + pmin < 0.25, 0.75 / (-pmin), torch.ones_like(pmin))
+    r = 1.0 + scale[:, None] * pert
+    w = torch.polar(r, phi.expand_as(r))
+    cum = torch.cat([torch.zeros(M, 1, dtype=f64, device=dev),
+                     torch.cumsum(torch.abs(w[:, 1:] - w[:, :-1]), dim=1)], dim=1)
+    cum = cum / cum[:, -1:]
+    t = torch.arange(N, dtype=f64, device=dev) / N
+    m = torch.arange(1, 4, dtype=f64, device=dev)
+    B = torch.as_tensor(b, dtype=f64, device=dev)
+    gam = t[None, :] + (B[:, None, :] * torch.sin(TWO_PI * t[:, None] * m[None, :])[None]
+                        / (TWO_PI * m)).sum(dim=2)
+    u = torch.remainder(torch.as_tensor(start, dtype=f64, device=dev)[:, None] + gam, 1.0)
+    j = torch.searchsorted(cum, u.contiguous(), right=True).clamp(1, dense) - 1
+    c0 = torch.gather(cum, 1, j)
+    c1 = torch.gather(cum, 1, j + 1)
+    fr = ((u - c0) / (c1 - c0)).clamp(0.0, 1.0)
+    wr, wi = w.real.contiguous(), w.imag.contiguous()
+    x = torch.gather(wr, 1, j) * (1 - fr) + torch.gather(wr, 1, j + 1) * fr
+    y = torch.gather(wi, 1, j) * (1 - fr) + torch.gather(wi, 1, j + 1) * fr
+    z = torch.complex(x, y) * torch.polar(torch.ones(M, dtype=f64, device=dev),
+                                          torch.as_tensor(rot, dtype=f64, device=dev))[:, None]
+    z = z - z.mean(dim=1, keepdim=True)
+    z = z / torch.abs(torch.roll(z, -1, dims=1) - z).sum(dim=1, keepdim=True)
+    return ShapeGallery(z.cpu().numpy(), cls.astype(np.int32))
