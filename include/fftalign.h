@@ -78,6 +78,10 @@ typedef struct fa_handle fa_handle;
                            Coordinates must lie within [2^-74, 2^128) in
                            magnitude (or be 0): unit-length curves do        */
 
+/* key types of fa_select_k */
+#define FA_KEY_F32 0
+#define FA_KEY_F64 1
+
 /* Create a handle bound to CUDA device `device` (its twiddle tables are built
  * here, synchronously).  *h receives the handle.  Not thread-safe with
  * respect to the same handle being destroyed concurrently. */
@@ -339,6 +343,82 @@ int fa_align_curves_host(fa_handle* h, const double* pts, const int64_t* offsets
 int fa_resample_arclength_noalloc(const double* pts, const int64_t* offsets, int64_t C,
                                   int64_t n_pts, int32_t N_out, int32_t flags, void* z_out,
                                   int8_t* status, void* stream);
+
+/* ------------------------------------------------------------------------
+ * k-NN retrieval under the elastic distance with learned candidate pruning.
+ * Not part of the paper (Sec. 3 defines the distance); the pruning network is
+ * this library's addition, with fa_elastic_distance as its fallback and as
+ * the judge of its recall.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Rotation-, translation- and cyclic-shift-invariant descriptors of curves
+ * resampled uniformly in arc length (e.g. by fa_resample_arclength): with
+ * Z = DFT(z)/N, out[m][f-1] = log(|Z[f]| + 1e-30) and out[m][F+f-1] =
+ * log(|Z[-f]| + 1e-30) for f = 1..F.
+ *   z    [M][N] complex128 (device), N a power of two in [8, 1024]
+ *   out  float [M][2F] (device), 1 <= F < N/2
+ */
+int fa_fourier_descriptors(fa_handle* h, const double* z, int64_t M, int32_t N, int32_t F,
+                           float* out, void* stream);
+
+/* Column means and reciprocal population standard deviations of X [M][D]
+ * (device, M > 0; a constant column gets 1/std = 1), and the in-place
+ * standardisation X = (X - mean) * inv_std. */
+int fa_column_stats(fa_handle* h, const float* X, int64_t M, int32_t D, float* mean,
+                    float* inv_std, void* stream);
+int fa_standardize(fa_handle* h, float* X, int64_t M, int32_t D, const float* mean,
+                   const float* inv_std, void* stream);
+
+/* out[q][g] = sum_d (A[q][d] - B[g][d])^2, float32 (device arrays), Q <= 2^21. */
+int fa_embed_sqdist(fa_handle* h, const float* A, int64_t Q, const float* B, int64_t G,
+                    int32_t D, float* out, void* stream);
+
+/*
+ * Per row of keys [rows][C] (float32 or float64 by key_type, device): the
+ * positions of the k smallest keys, ascending by (key, position) (NaN last),
+ * into out_pos [rows][k]; their keys into out_keys [rows][k] (same type) when
+ * not NULL.  1 <= k <= min(256, C).
+ */
+int fa_select_k(fa_handle* h, const void* keys, int32_t key_type, int64_t rows, int64_t C,
+                int32_t k, int64_t* out_pos, void* out_keys, void* stream);
+
+/*
+ * The pruning network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, dimensions
+ * 64 -> 256 -> 256 -> 64, weights used in bfloat16 (float32 master values),
+ * biases, activations and accumulation in float32.  Parameters are one flat
+ * float32 vector of fa_mlp_num_params() values: W1 [256][64], b1 [256],
+ * W2 [256][256], b2 [256], W3 [64][256], b3 [64], each row-major.
+ *
+ * fa_mlp_create      He-normal weights from seed (SplitMix64, Box-Muller), the
+ *                    output layer's scaled by 0.01, zero biases; the handle owns device memory and must be
+ *                    released with fa_mlp_destroy.
+ * fa_mlp_set_params  copies a host parameter vector in (and zeroes the Adam
+ *                    state); fa_mlp_get_params copies it out (synchronous).
+ * fa_mlp_forward     Y [B][64] = network(X [B][64]) (device arrays), B <= 2^21.
+ * fa_mlp_pair_grad   for pairs p: rows pi[p], pj[p] of X [rows][64] (device),
+ *                    target distances d [P] (float32, device): the loss
+ *                    L = (1/P) sum_p (r_p - d_p)^2 / (d_p + 0.05)^2,
+ *                    r_p = sqrt(|y_pi - y_pj|^2 + 1e-12), into *loss (device
+ *                    float), and dL/dparams into the handle (and into grad
+ *                    [fa_mlp_num_params()] on the device when not NULL);
+ *                    P <= 2^20.
+ *                    Synchronises the stream; an index outside [0, rows)
+ *                    returns FA_ERR_INVALID_ARG.
+ * fa_mlp_adam_step   one Adam step (0.9, 0.999, 1e-8) with learning rate lr
+ *                    from the last gradient; refreshes the bfloat16 copy.
+ */
+typedef struct fa_mlp fa_mlp;
+int64_t fa_mlp_num_params(void);
+int fa_mlp_create(fa_handle* h, uint64_t seed, fa_mlp** out);
+int fa_mlp_destroy(fa_mlp* m);
+int fa_mlp_set_params(fa_mlp* m, const float* params);
+int fa_mlp_get_params(fa_mlp* m, float* params);
+int fa_mlp_forward(fa_mlp* m, const float* X, int64_t B, float* Y, void* stream);
+int fa_mlp_pair_grad(fa_mlp* m, const float* X, int64_t rows, const int64_t* pi,
+                     const int64_t* pj, const float* d, int64_t P, float* loss, float* grad,
+                     void* stream);
+int fa_mlp_adam_step(fa_mlp* m, float lr, void* stream);
 
 #ifdef __cplusplus
 }

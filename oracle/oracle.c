@@ -440,21 +440,28 @@ int oracle_max_threads(void)
 /*      (a) a dynamic programme over lattice paths from (0,0) to (N,N)      */
 /*          with steps (a,b), 1 <= a,b <= 3, gcd(a,b) = 1 (slopes b/a in    */
 /*          [1/3, 3]), optionally kept in the band |i - j| <= B, minimising */
-/*          E exactly over those paths; run on the first iteration and      */
-/*          whenever the start point s changed;                             */
+/*          E exactly over those paths; run on the first iteration only     */
+/*          (later the refined gamma carries over: a new shift s from the   */
+/*          (t0,R)-step keeps gamma and lowers E, and the refinement's free  */
+/*          offset g_0 follows it);                                         */
 /*      (b) a continuous refinement of all g_k (g_0 too) jointly with theta:*/
 /*          Levenberg-Marquardt steps on the residuals                      */
 /*          r_k = q1s_k - sqrt(D_k) q2(M_k) (Gauss-Newton normal matrix,     */
 /*          tridiagonal in g with a border for theta), each step shortened  */
 /*          to keep every D_k above half its value and accepted only if E   */
-/*          decreases.  Without theta in it the alternation converges only  */
+/*          decreases; at most 64 steps, ending after an accepted step that  */
+/*          lowers E by <= 1e-12 E or once the damping exceeds 1e6.          */
+/*          Without theta in it the alternation converges only              */
 /*          linearly (gamma partly absorbs a rotation error).               */
 /*  - the (t0,R)-step is the rigid alignment of Sec. 2 (O1's criterion) of  */
 /*    w_k = sqrt(D_k) q2(M_k) against q1 over all grid shifts s.            */
 /* ------------------------------------------------------------------------ */
 
 #define EL_NSTEPS 7
-#define EL_LM_ITERS 16
+#define EL_LM_ITERS 64    /* Levenberg-Marquardt steps per gamma-step, at most */
+#define EL_LM_TOL 1e-12   /* ... ending after an accepted step that lowers E by <= this */
+                          /*     fraction of it                                      */
+#define EL_LM_STALL 1e6   /* ... or once the damping exceeds this */
 /* (a, b) = (cells along t, cells along gamma); this order is also the tie  */
 /* order of the dynamic programme (the first best step wins).               */
 static const int EL_STEP[EL_NSTEPS][2] = {{1, 1}, {1, 2}, {2, 1}, {1, 3}, {3, 1}, {2, 3},
@@ -690,13 +697,17 @@ static double el_refine(const double* q1, const double* q2, int N, int s, double
         el_move(q1, N, s, tht, qt);
         const double Et = el_energy(qt, q2, N, gt);
         if (Et < E) {
+            const double drop = E - Et;
+            const double Eold = E;
             memcpy(g, gt, cn);
             memcpy(q1s, qt, cz);
             *theta = tht;
             E = Et;
             lambda = lambda * 0.25 > 1e-12 ? lambda * 0.25 : 1e-12;
+            if (drop <= EL_LM_TOL * Eold) break;  /* converged */
         } else {
             lambda *= 8.0;
+            if (lambda > EL_LM_STALL) break;  /* no descent left at rounding level */
         }
     }
     free(q1s); free(qt); free(Ar); free(Br); free(R); free(x); free(yc); free(yp);
@@ -782,7 +793,7 @@ typedef struct {
 /*   (s, theta) from the FFT rigid alignment of the arc-length-resampled    */
 /*   curves (Sec. 3 pre-alignment: O2, then O1 with the motion on curve 1), */
 /*   gamma = identity;                                                      */
-/*   repeat: gamma-step ((a) if first or s changed, then (b));              */
+/*   repeat: gamma-step ((a) on the first iteration, then (b));             */
 /*           (t0,R)-step;                                                   */
 /*   until an iteration lowers the energy by at most 1e-12, or max_iter.    */
 /*   The energy is that of the final triple.                                */
@@ -813,7 +824,7 @@ static void elastic_one(const double* b1, const double* b2, int N, int band, int
              : st1 != ST_OK ? st1 : st2 != ST_OK ? st2 : rs1 != ST_OK ? rs1 : rs2;
     if (st != ST_OK) { res->status = (signed char)st; goto out; }
     {
-        int s, sp = -1;
+        int s;
         double th, e, gap, Eprev = INFINITY;
         signed char ast;
         /* pre-alignment with the motion on curve 1: e^{i th} r1[k+s] ~ r2[k] */
@@ -821,12 +832,11 @@ static void elastic_one(const double* b1, const double* b2, int N, int band, int
         s = el_param_index(sg1, N, (double)s / (double)N);
         for (int k = 0; k <= N; ++k) g[k] = (double)k;
         for (int it = 1; it <= max_iter; ++it) {
-            if (s != sp) {
+            if (it == 1) {
                 el_move(q1, N, s, th, q1s);
                 el_dp(q1s, q2, N, band, g);
             }
             el_refine(q1, q2, N, s, &th, g, EL_LM_ITERS);
-            sp = s;
             el_rigid(q1, q2, N, g, &s, &th);
             el_move(q1, N, s, th, q1s);
             const double E = el_energy(q1s, q2, N, g);

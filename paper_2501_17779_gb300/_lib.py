@@ -39,7 +39,12 @@ EXPORTS = (
     "fa_align_all_pairs_workspace_size", "fa_align_all_pairs",
     "fa_align_pairs_ragged_workspace_size", "fa_align_pairs_ragged",
     "fa_align_pairs_ragged_autotune", "fa_elastic_workspace_size", "fa_elastic_distance",
+    "fa_fourier_descriptors", "fa_column_stats", "fa_standardize", "fa_embed_sqdist",
+    "fa_select_k", "fa_mlp_num_params", "fa_mlp_create", "fa_mlp_destroy", "fa_mlp_set_params",
+    "fa_mlp_get_params", "fa_mlp_forward", "fa_mlp_pair_grad", "fa_mlp_adam_step",
 )
+KEY_F32 = 0
+KEY_F64 = 1
 STATUS_BAD_SIZE = 3
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -105,6 +110,24 @@ def load(build_if_missing: bool = False):
     L.fa_elastic_distance.argtypes = [vp, vp, i64, vp, i64, i32, vp, vp, i64, i32, i32, vp, vp, vp,
                                       vp, vp, vp, vp, sz, vp]
     L.fa_elastic_distance.restype = ctypes.c_int
+    for name, args in (
+            ("fa_fourier_descriptors", [vp, vp, i64, i32, i32, vp, vp]),
+            ("fa_column_stats", [vp, vp, i64, i32, vp, vp, vp]),
+            ("fa_standardize", [vp, vp, i64, i32, vp, vp, vp]),
+            ("fa_embed_sqdist", [vp, vp, i64, vp, i64, i32, vp, vp]),
+            ("fa_select_k", [vp, vp, i32, i64, i64, i32, vp, vp, vp]),
+            ("fa_mlp_create", [vp, ctypes.c_uint64, ctypes.POINTER(vp)]),
+            ("fa_mlp_destroy", [vp]),
+            ("fa_mlp_set_params", [vp, vp]),
+            ("fa_mlp_get_params", [vp, vp]),
+            ("fa_mlp_forward", [vp, vp, i64, vp, vp]),
+            ("fa_mlp_pair_grad", [vp, vp, i64, vp, vp, vp, i64, vp, vp, vp]),
+            ("fa_mlp_adam_step", [vp, ctypes.c_float, vp])):
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.fa_mlp_num_params.argtypes = []
+    L.fa_mlp_num_params.restype = i64
     _lib = L
     return L
 

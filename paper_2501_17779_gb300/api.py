@@ -309,3 +309,116 @@ def align_curves_host(pts: torch.Tensor, offsets: torch.Tensor, N: int, *, metho
                                 _ptr(status), _stream_ptr(dev))
     _lib.check(rc)
     return shift, theta, energy, status
+
+
+# ------------------------------------------------ k-NN retrieval helpers ----
+def fourier_descriptors(z: torch.Tensor, F: int = 32) -> torch.Tensor:
+    """log |Z[+-f]|, f = 1..F, of uniformly resampled curves z [M, N]
+    (complex128 CUDA) -> float32 [M, 2F] (fa_fourier_descriptors)."""
+    _need_cuda("z", z, torch.complex128)
+    M, N = z.shape
+    out = torch.empty((M, 2 * F), dtype=torch.float32, device=z.device)
+    _lib.check(_lib.load().fa_fourier_descriptors(handle(z.device.index), _ptr(z), M, N, F,
+                                                  _ptr(out), _stream_ptr(z.device)))
+    return out
+
+
+def column_stats(X: torch.Tensor):
+    _need_cuda("X", X, torch.float32)
+    M, D = X.shape
+    mean = torch.empty(D, dtype=torch.float32, device=X.device)
+    inv = torch.empty(D, dtype=torch.float32, device=X.device)
+    _lib.check(_lib.load().fa_column_stats(handle(X.device.index), _ptr(X), M, D, _ptr(mean),
+                                           _ptr(inv), _stream_ptr(X.device)))
+    return mean, inv
+
+
+def standardize_(X: torch.Tensor, mean: torch.Tensor, inv_std: torch.Tensor) -> torch.Tensor:
+    _need_cuda("X", X, torch.float32)
+    M, D = X.shape
+    _lib.check(_lib.load().fa_standardize(handle(X.device.index), _ptr(X), M, D, _ptr(mean),
+                                          _ptr(inv_std), _stream_ptr(X.device)))
+    return X
+
+
+def embed_sqdist(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    _need_cuda("A", A, torch.float32)
+    _need_cuda("B", B, torch.float32)
+    Q, D = A.shape
+    G = B.shape[0]
+    out = torch.empty((Q, G), dtype=torch.float32, device=A.device)
+    _lib.check(_lib.load().fa_embed_sqdist(handle(A.device.index), _ptr(A), Q, _ptr(B), G, D,
+                                           _ptr(out), _stream_ptr(A.device)))
+    return out
+
+
+def select_k(keys: torch.Tensor, k: int, with_keys: bool = False):
+    """Positions of the k smallest keys per row, ascending by (key, position)."""
+    if keys.dtype not in (torch.float32, torch.float64):
+        raise ValueError("keys must be float32 or float64")
+    _need_cuda("keys", keys, keys.dtype)
+    rows, C = keys.shape
+    pos = torch.empty((rows, k), dtype=torch.int64, device=keys.device)
+    kv = torch.empty((rows, k), dtype=keys.dtype, device=keys.device) if with_keys else None
+    kt = _lib.KEY_F32 if keys.dtype == torch.float32 else _lib.KEY_F64
+    _lib.check(_lib.load().fa_select_k(handle(keys.device.index), _ptr(keys), kt, rows, C, k,
+                                       _ptr(pos), _ptr(kv), _stream_ptr(keys.device)))
+    return (pos, kv) if with_keys else pos
+
+
+class Mlp:
+    """The pruning network (fa_mlp_*): 64 -> 256 -> 256 -> 64, bfloat16 weights."""
+
+    def __init__(self, seed: int = 0, device: int | None = None):
+        self._L = _lib.load()
+        self._h = handle(device)
+        self.device = torch.device("cuda", device if device is not None else torch.cuda.current_device())
+        p = ctypes.c_void_p()
+        _lib.check(self._L.fa_mlp_create(self._h, seed, ctypes.byref(p)))
+        self._m = p.value
+        self.n_params = int(self._L.fa_mlp_num_params())
+
+    def close(self):
+        if self._m:
+            self._L.fa_mlp_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.n_params, np.float32)
+        _lib.check(self._L.fa_mlp_get_params(self._m, out.ctypes.data))
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == self.n_params
+        _lib.check(self._L.fa_mlp_set_params(self._m, p.ctypes.data))
+
+    def forward(self, X: torch.Tensor) -> torch.Tensor:
+        _need_cuda("X", X, torch.float32)
+        B = X.shape[0]
+        Y = torch.empty((B, 64), dtype=torch.float32, device=X.device)
+        _lib.check(self._L.fa_mlp_forward(self._m, _ptr(X), B, _ptr(Y), _stream_ptr(X.device)))
+        return Y
+
+    def pair_grad(self, X, pi, pj, d, grad: bool = False):
+        _need_cuda("X", X, torch.float32)
+        _need_cuda("pi", pi, torch.int64)
+        _need_cuda("pj", pj, torch.int64)
+        _need_cuda("d", d, torch.float32)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device) if grad else None
+        _lib.check(self._L.fa_mlp_pair_grad(self._m, _ptr(X), X.shape[0], _ptr(pi), _ptr(pj),
+                                            _ptr(d), pi.numel(), _ptr(loss), _ptr(g),
+                                            _stream_ptr(X.device)))
+        return (loss, g) if grad else loss
+
+    def adam_step(self, lr: float):
+        _lib.check(self._L.fa_mlp_adam_step(self._m, float(lr), _stream_ptr(self.device)))

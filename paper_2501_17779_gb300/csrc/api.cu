@@ -90,24 +90,6 @@ int build_twiddles(fa_handle* h)
     return cuda_error(cudaDeviceSynchronize(), "fa_create: twiddle build");
 }
 
-// Makes the handle's device current for the lifetime of the object and
-// restores the caller's device afterwards.
-struct DeviceGuard {
-    int prev = -1;
-    int rc = FA_OK;
-    explicit DeviceGuard(int dev)
-    {
-        cudaError_t e = cudaGetDevice(&prev);
-        if (e == cudaSuccess && prev != dev) e = cudaSetDevice(dev);
-        if (e != cudaSuccess) rc = cuda_error(e, "cudaSetDevice");
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 static int ensure_ws(fa_handle* h, size_t bytes)
 {
     if (h->ws_bytes >= bytes) return FA_OK;

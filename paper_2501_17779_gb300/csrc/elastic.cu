@@ -21,7 +21,7 @@
 //                 lowers E by at most 1e-12 (or max_iter):
 //                   gamma-step (this library's own design; the paper takes
 //                   its gamma-step from a reference it does not reproduce):
-//                     (a) when s is new: dynamic programme over lattice paths
+//                     (a) first iteration only: dynamic programme over lattice paths
 //                         (0,0) -> (N,N) with steps (a,b), a,b <= 3, coprime,
 //                         in the band |i - j| <= B, minimising E exactly;
 //                     (b) 16 Levenberg-Marquardt steps on (g_0..g_{N-1},
@@ -53,7 +53,9 @@ namespace {
 constexpr int kElT = 128;         // threads per pair CTA
 constexpr int kNSteps = 7;
 constexpr int kNFrac = 8;
-constexpr int kLmIters = 16;
+constexpr int kLmIters = 64;       // Levenberg-Marquardt steps per gamma-step, at most,
+constexpr double kLmTol = 1e-12;   // ending after an accepted step lowering E by <= kLmTol E
+constexpr double kLmStall = 1e6;   // or once the damping exceeds this
 constexpr double kStopDrop = 1e-12;
 
 // lattice steps (a, b): a cells of q1 along t, b cells of q2 along gamma; this
@@ -86,6 +88,23 @@ __host__ __device__ constexpr int frac_tw(int f)
     return f == 0 ? 0 : f == 1 ? 2 : f == 2 ? 3 : f == 3 ? 4 : f == 4 ? 6 : f == 5 ? 8 : f == 6 ? 9 : 10;
 }
 static_assert(frac_tw(frac_index(piece_tw(6, 0))) == piece_tw(6, 0), "fraction table");
+// sqrt(b/a) of each step, correctly rounded
+__device__ __forceinline__ constexpr double step_m(int st)
+{
+    return st == 0 ? 1.0 : st == 1 ? 1.4142135623730951 : st == 2 ? 0.7071067811865476
+         : st == 3 ? 1.7320508075688772 : st == 4 ? 0.5773502691896257
+         : st == 5 ? 1.224744871391589 : 0.816496580927726;
+}
+
+// 1/sqrt(x) for x in (0, 2^100): float32 seed, two Newton steps in FP64
+// (y <- y (3 - x y^2) / 2), relative error at rounding level
+__device__ __forceinline__ double rsqrt_fast(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    return y;
+}
 
 struct ElasticArgs {
     const double2* q;       // SRV samples [Mtot][N]
@@ -191,7 +210,8 @@ __device__ double energy_n(const double2* q1, const double2* q2, int N, int s, d
     for (int k = threadIdx.x; k < N; k += T) {
         double2 v;
         cr_eval(q2, N, 0.5 * (g[k] + g[k + 1]), v, nullptr);
-        const double m = sqrt(g[k + 1] - g[k]);
+        const double D = g[k + 1] - g[k];
+        const double m = D * rsqrt_fast(D);
         const double2 u = rot(cs, q1[(k + s) & (N - 1)]);
         const double dx = fma(-m, v.x, u.x), dy = fma(-m, v.y, u.y);
         acc[0] = fma(dx, dx, fma(dy, dy, acc[0]));
@@ -211,7 +231,7 @@ __device__ __forceinline__ void dp_steps(int i, int j, const double* __restrict_
         constexpr int a = step_a(ST), b = step_b(ST);
         if (i >= a && j >= b) {
             const double prev = V[((i - a) & 3) * ring_stride + (j - b)];
-            const double m = sqrt((double)b / (double)a);
+            constexpr double m = step_m(ST);
             double acc = 0.0;
 #pragma unroll
             for (int p = 0; p < a; ++p) {
@@ -291,34 +311,34 @@ __device__ void build_q2f(const double2* q2, int N, double2* q2f)
 // ---------------------------------------------------------- refinement ----
 // Parallel cyclic reduction of the symmetric tridiagonal system with rows
 // r = 1..n (lower lo[r], diagonal di[r], upper up[r]) on three right-hand
-// sides x, y1, y2 (all overwritten by the solutions).  Out-of-range rows act
-// as identity rows.
+// sides x, y1, y2 (all overwritten by the solutions), in float32: it gives
+// the Levenberg-Marquardt step direction, which the FP64 energy test then
+// accepts or rejects.  Out-of-range rows act as identity rows.
 template <int T, int NMAX>
-__device__ void pcr3(int n, double* lo, double* di, double* up, double* x, double* y1, double* y2)
+__device__ void pcr3(int n, float* lo, float* di, float* up, float* x, float* y1, float* y2)
 {
     constexpr int RMAX = (NMAX - 1 + T - 1) / T;  // rows per thread (n <= NMAX - 1)
     for (int h = 1; h < n; h <<= 1) {
-        double nl[RMAX], nd[RMAX], nu[RMAX], nx[RMAX], n1[RMAX], n2[RMAX];
+        float nl[RMAX], nd[RMAX], nu[RMAX], nx[RMAX], n1[RMAX], n2[RMAX];
 #pragma unroll
         for (int q = 0; q < RMAX; ++q) {
             const int r = 1 + threadIdx.x + q * T;
             if (r <= n) {
-                double al = 0.0, ga = 0.0;
-                double dd = di[r], xx = x[r], a1 = y1[r], a2 = y2[r], l2 = 0.0, u2 = 0.0;
+                float dd = di[r], xx = x[r], a1 = y1[r], a2 = y2[r], l2 = 0.0f, u2 = 0.0f;
                 if (r - h >= 1) {
-                    al = -lo[r] / di[r - h];
-                    dd = fma(al, up[r - h], dd);
-                    xx = fma(al, x[r - h], xx);
-                    a1 = fma(al, y1[r - h], a1);
-                    a2 = fma(al, y2[r - h], a2);
+                    const float al = -lo[r] / di[r - h];
+                    dd = fmaf(al, up[r - h], dd);
+                    xx = fmaf(al, x[r - h], xx);
+                    a1 = fmaf(al, y1[r - h], a1);
+                    a2 = fmaf(al, y2[r - h], a2);
                     l2 = al * lo[r - h];
                 }
                 if (r + h <= n) {
-                    ga = -up[r] / di[r + h];
-                    dd = fma(ga, lo[r + h], dd);
-                    xx = fma(ga, x[r + h], xx);
-                    a1 = fma(ga, y1[r + h], a1);
-                    a2 = fma(ga, y2[r + h], a2);
+                    const float ga = -up[r] / di[r + h];
+                    dd = fmaf(ga, lo[r + h], dd);
+                    xx = fmaf(ga, x[r + h], xx);
+                    a1 = fmaf(ga, y1[r + h], a1);
+                    a2 = fmaf(ga, y2[r + h], a2);
                     u2 = ga * up[r + h];
                 }
                 nl[q] = l2; nd[q] = dd; nu[q] = u2; nx[q] = xx; n1[q] = a1; n2[q] = a2;
@@ -335,7 +355,7 @@ __device__ void pcr3(int n, double* lo, double* di, double* up, double* x, doubl
         __syncthreads();
     }
     for (int r = 1 + threadIdx.x; r <= n; r += T) {
-        const double inv = 1.0 / di[r];
+        const float inv = 1.0f / di[r];
         x[r] *= inv;
         y1[r] *= inv;
         y2[r] *= inv;
@@ -345,7 +365,8 @@ __device__ void pcr3(int n, double* lo, double* di, double* up, double* x, doubl
 
 struct LmArrays {
     double2 *R, *A, *Bv;
-    double *di, *xv, *Cc, *Cp, *lo, *up, *yc, *yp;
+    double *Cc, *Cp;
+    float *di, *xv, *lo, *up, *yc, *yp;
 };
 
 // Levenberg-Marquardt refinement of (g, theta) for the shift s; returns N E
@@ -365,8 +386,10 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
         for (int k = tid; k < N; k += T) {
             double2 v, dv;
             cr_eval(q2, N, 0.5 * (g[k] + g[k + 1]), v, &dv);
-            const double m = sqrt(g[k + 1] - g[k]);
-            const double hm = 0.5 / m;
+            const double D = g[k + 1] - g[k];
+            const double rs = rsqrt_fast(D);
+            const double m = D * rs;
+            const double hm = 0.5 * rs;
             const double2 u = rot(cs, q1[(k + s) & (N - 1)]);
             const double2 r = make_double2(fma(-m, v.x, u.x), fma(-m, v.y, u.y));
             // dr/dD = -q2 / (2 sqrt D), dr/dM = -sqrt(D) q2'
@@ -391,27 +414,28 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
             const double2 r0 = L.R[i - 1], r1 = L.R[i];
             const double2 p0 = rot(cs, q1[(i - 1 + s) & (N - 1)]);
             const double2 p1 = rot(cs, q1[(i + s) & (N - 1)]);
-            L.di[i] = (b0.x * b0.x + b0.y * b0.y + a1.x * a1.x + a1.y * a1.y) * (1.0 + lambda);
-            L.xv[i] = -(r0.x * b0.x + r0.y * b0.y + r1.x * a1.x + r1.y * a1.y);
+            L.di[i] = (float)((b0.x * b0.x + b0.y * b0.y + a1.x * a1.x + a1.y * a1.y) * (1.0 + lambda));
+            L.xv[i] = (float)(-(r0.x * b0.x + r0.y * b0.y + r1.x * a1.x + r1.y * a1.y));
             const double cc = b0.x * (a0.x + b0.x) + b0.y * (a0.y + b0.y) + a1.x * (a1.x + b1.x) +
                               a1.y * (a1.y + b1.y);
             const double cp = b0.x * -p0.y + b0.y * p0.x + a1.x * -p1.y + a1.y * p1.x;
             L.Cc[i] = cc;
             L.Cp[i] = cp;
-            L.yc[i] = cc;
-            L.yp[i] = cp;
-            L.lo[i] = i > 1 ? a0.x * b0.x + a0.y * b0.y : 0.0;
-            L.up[i] = i < n ? a1.x * b1.x + a1.y * b1.y : 0.0;
+            L.yc[i] = (float)cc;
+            L.yp[i] = (float)cp;
+            L.lo[i] = i > 1 ? (float)(a0.x * b0.x + a0.y * b0.y) : 0.0f;
+            L.up[i] = i < n ? (float)(a1.x * b1.x + a1.y * b1.y) : 0.0f;
         }
         __syncthreads();
         pcr3<T, NMAX>(n, L.lo, L.di, L.up, L.xv, L.yc, L.yp);
         double sc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // Cc.yc, Cc.yp, Cp.yp, Cc.x, Cp.x
         for (int i = 1 + tid; i <= n; i += T) {
-            sc[0] = fma(L.Cc[i], L.yc[i], sc[0]);
-            sc[1] = fma(L.Cc[i], L.yp[i], sc[1]);
-            sc[2] = fma(L.Cp[i], L.yp[i], sc[2]);
-            sc[3] = fma(L.Cc[i], L.xv[i], sc[3]);
-            sc[4] = fma(L.Cp[i], L.xv[i], sc[4]);
+            const double yc = L.yc[i], yp = L.yp[i], xv = L.xv[i];
+            sc[0] = fma(L.Cc[i], yc, sc[0]);
+            sc[1] = fma(L.Cc[i], yp, sc[1]);
+            sc[2] = fma(L.Cp[i], yp, sc[2]);
+            sc[3] = fma(L.Cc[i], xv, sc[3]);
+            sc[4] = fma(L.Cp[i], xv, sc[4]);
         }
         cta_sums<T, 5>(sc, red);
         const double S00 = h[0] * (1.0 + lambda) - sc[0], S01 = h[1] - sc[1];
@@ -425,7 +449,8 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
         }
         // step on the interior nodes, then the slope-keeping shortening
         for (int k = tid; k <= N; k += T)
-            gt[k] = (k == 0 || k == N) ? 0.0 : L.xv[k] - L.yc[k] * dc - L.yp[k] * dphi;
+            gt[k] = (k == 0 || k == N) ? 0.0
+                                       : (double)L.xv[k] - (double)L.yc[k] * dc - (double)L.yp[k] * dphi;
         __syncthreads();
         double al = 1.0;
         for (int k = tid; k < N; k += T) {
@@ -439,16 +464,20 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
         sincos(tht, &ct.y, &ct.x);
         __syncthreads();
         const double Et = energy_n<T>(q1, q2, N, s, ct, gt, red);
+        bool stop;
         if (Et < En) {
             for (int k = tid; k <= N; k += T) g[k] = gt[k];
             theta = tht;
             cs = ct;
+            stop = En - Et <= kLmTol * En;
             En = Et;
             lambda = fmax(lambda * 0.25, 1e-12);
         } else {
             lambda *= 8.0;
+            stop = lambda > kLmStall;
         }
         __syncthreads();
+        if (stop) break;
     }
     return En;
 }
@@ -518,8 +547,12 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
     bp = a.bp_smem ? reinterpret_cast<uint8_t*>(tail) : a.bp_ws + (int64_t)blockIdx.x * a.bp_bytes;
     LmArrays L;
     L.R = X; L.A = Y; L.Bv = q1s;
-    L.di = ar; L.xv = ar + (N + 1); L.Cc = ar + 2 * (N + 1); L.Cp = ar + 3 * (N + 1);
-    L.lo = ar + 4 * (N + 1); L.up = ar + 5 * (N + 1); L.yc = ar + 6 * (N + 1); L.yp = ar + 7 * (N + 1);
+    L.Cc = ar; L.Cp = ar + (N + 1);
+    {
+        float* f = reinterpret_cast<float*>(ar + 2 * (N + 1));
+        L.di = f; L.xv = f + (N + 1); L.lo = f + 2 * (N + 1); L.up = f + 3 * (N + 1);
+        L.yc = f + 4 * (N + 1); L.yp = f + 5 * (N + 1);
+    }
     const double nanv = __longlong_as_double(0x7ff8000000000000LL);
 
     for (int64_t pair = blockIdx.x; pair < a.P; pair += gridDim.x) {
@@ -581,10 +614,10 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
         for (int k = tid; k <= N; k += T) g[k] = (double)k;
         __syncthreads();
 
-        int sp = -1, it = 0;
+        int it = 0;
         double Eprev = HUGE_VAL, En = 0.0;
         for (it = 1; it <= a.max_iter; ++it) {
-            if (s != sp) {
+            if (it == 1) {
                 double2 cs;
                 sincos(theta, &cs.y, &cs.x);
                 for (int k = tid; k < N; k += T) q1s[k] = rot(cs, q1[(k + s) & (N - 1)]);
@@ -592,12 +625,12 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
                 elastic_dp<T>(N, B, q1s, q2f, ar, bp, g);
             }
             elastic_refine<T, NMAX>(q1, q2, N, s, theta, g, gt, L, red);
-            sp = s;
             // (t0, R)-step on w_k = sqrt(D_k) q2(M_k)
             for (int k = tid; k < N; k += T) {
                 double2 v;
                 cr_eval(q2, N, 0.5 * (g[k] + g[k + 1]), v, nullptr);
-                const double m = sqrt(g[k + 1] - g[k]);
+                const double D = g[k + 1] - g[k];
+                const double m = D * rsqrt_fast(D);
                 X[k] = make_double2(m * v.x, m * v.y);
                 Y[k] = X[k];
             }

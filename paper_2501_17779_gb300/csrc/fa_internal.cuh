@@ -39,6 +39,25 @@ constexpr int kMaxRaggedLogL = 14;     // its longest transform, 2^14
 int set_error(int code, const std::string& msg);
 int cuda_error(cudaError_t e, const char* where);
 
+// Makes the handle's device current for the lifetime of the object and
+// restores the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    int rc = FA_OK;
+    explicit DeviceGuard(int dev)
+    {
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e == cudaSuccess && prev != dev) e = cudaSetDevice(dev);
+        if (e != cudaSuccess) rc = cuda_error(e, "cudaSetDevice");
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+
 // ---------------------------------------------------------------- device ----
 __device__ __forceinline__ bool finite2(double2 v)
 {

@@ -15,7 +15,7 @@ def _declared():
     names = set()
     for h in (ROOT / "include").glob("*.h"):
         txt = h.read_text()
-        names |= set(re.findall(r"^\s*(?:int|size_t|const char\*)\s+(fa_\w+)\s*\(", txt, re.M))
+        names |= set(re.findall(r"^\s*(?:int|int64_t|size_t|const char\*)\s+(fa_\w+)\s*\(", txt, re.M))
     return names
 
 
