@@ -478,6 +478,84 @@ def run_gpu(args):
                "status_ok": bool((rout[3] == 0).all().item())}
         del rz1, rz2, roffs, rws, rout, graph
 
+    # elastic shape distance (Sec. 3, Approach 2 with the FFT (t0,R)-step):
+    # 4096 pairs of N = 256 gallery curves (50 Fourier-series classes,
+    # harmonic perturbation 0.03, random smooth reparameterisation), band 32
+    ela = None
+    if not args.no_elastic:
+        from paper_2501_17779_gb300 import synth
+
+        Ne, Pe, Be = 256, 4096, 32
+        ce = torch.from_numpy(synth.shape_gallery(SEED + 13, 2 * Pe, Ne, device=str(dev)).curves).to(dev)
+        c1, c2 = ce[:Pe].contiguous(), ce[Pe:].contiguous()
+        ews = torch.empty(api.elastic_workspace_size(Pe, Pe, Pe, Ne, Be, local), dtype=torch.uint8,
+                          device=dev)
+        with torch.cuda.stream(stream):
+            eo = api.elastic_distance(c1, c2, band=Be, workspace=ews)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(3):
+                api.elastic_distance(c1, c2, band=Be, workspace=ews, out=eo)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ela_ms = e0.elapsed_time(e1) / 3
+        ela = {"workload": f"{Pe} pairs, N={Ne}, lattice band {Be}, gallery curves (50 classes, "
+                           "harmonic perturbation 0.03, random smooth reparameterisation), FP64",
+               "ms": ela_ms, "pairs_per_s": Pe / (ela_ms * 1e-3),
+               "iterations_mean": float(eo[3].double().mean().item()),
+               "iterations_max": int(eo[3].max().item()),
+               "distance_mean": float(torch.sqrt(eo[2]).mean().item()),
+               "status_ok": bool((eo[4] == 0).all().item())}
+        del ce, c1, c2, ews, eo
+
+    # k-NN retrieval, 20,000-curve gallery, 1,000 queries, N = 256: the pruning
+    # network trained on elastic distances, 200 candidates per query
+    knnr = None
+    if not args.no_knn:
+        from paper_2501_17779_gb300 import knn as knnmod
+        from paper_2501_17779_gb300 import synth
+
+        Gk, Qk, Nk, Bk, NC = 20000, 1000, 256, 32, 200
+        gal = torch.from_numpy(synth.shape_gallery(SEED + 17, Gk, Nk, device=str(dev)).curves).to(dev)
+        qry = torch.from_numpy(synth.shape_gallery(SEED + 19, Qk, Nk, device=str(dev)).curves).to(dev)
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            dg = knnmod.descriptors(gal)
+            net, loss, n_train = knnmod.train_pruner(gal, dg, band=Bk, steps=1500, seed=SEED,
+                                                     n_near=12, n_rand=4)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            train_ms = e0.elapsed_time(e1)
+            e0.record(stream)
+            dq = knnmod.descriptors(qry, dg)
+            found, _ = knnmod.search(qry, gal, k=10, band=Bk, n_cand=NC, qdesc=dq.x, gdesc=dg.x,
+                                     net=net)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            search_ms = e0.elapsed_time(e1)
+            Qs = args.knn_exact_queries
+            e0.record(stream)
+            exact, _ = knnmod.search(qry[:Qs], gal, k=10, band=Bk)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            exact_ms = e0.elapsed_time(e1)
+            raw, _ = knnmod.search(qry[:Qs], gal, k=10, band=Bk, n_cand=NC, qdesc=dq.x[:Qs],
+                                   gdesc=dg.x)
+            torch.cuda.synchronize(dev)
+        knnr = {"workload": f"gallery {Gk}, queries {Qk}, N={Nk}, 50 classes, lattice band {Bk}, "
+                            f"{NC} candidates per query",
+                "queries_per_s": Qk / (search_ms * 1e-3), "search_ms": search_ms,
+                "elastic_per_query": NC, "exact_elastic_per_query": Gk,
+                "exact_queries_per_s": Qs / (exact_ms * 1e-3),
+                "speedup_vs_exact": (exact_ms / Qs) / (search_ms / Qk),
+                "recall_at_10": knnmod.recall_at_k(found[:Qs], exact),
+                "recall_at_10_raw_descriptors": knnmod.recall_at_k(raw, exact),
+                "recall_sample": f"the first {Qs} queries, exact search over all {Gk} curves",
+                "train_ms": train_ms, "train_elastic_pairs": n_train, "train_loss": loss,
+                "network": "64-256-256-64, bf16 weights, fp32 accumulate, Adam, 1500 steps x 4096 pairs"}
+        del gal, qry, dg, dq, found, exact, raw, net
+
     line = None
     if rank == 0:
         cpu = None
@@ -513,6 +591,8 @@ def run_gpu(args):
                 "dtype": "double-float (f32x2) search + f64 c(s*)/theta/energy"}},
             "all_pairs": allp,
             "ragged": rag,
+            "elastic": ela,
+            "knn": knnr,
             "cpu_baseline": cpu,
             "e2e": {"value": world * P / (e2e_ms * 1e-3), "unit": "pairs/s",
                     "h2d_bytes_per_step": int(rp.pts.nbytes + rp.offsets.nbytes),
@@ -541,6 +621,9 @@ def main():
     ap.add_argument("--no-all-pairs", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--ragged-pairs", type=int, default=100_000)
+    ap.add_argument("--no-elastic", action="store_true")
+    ap.add_argument("--no-knn", action="store_true")
+    ap.add_argument("--knn-exact-queries", type=int, default=16)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()
