@@ -470,7 +470,7 @@ static const int EL_STEP[EL_NSTEPS][2] = {{1, 1}, {1, 2}, {2, 1}, {1, 3}, {3, 1}
 /* q(u): the periodic Catmull-Rom interpolant of the midpoint samples (the */
 /* cubic Hermite curve through them with central-difference tangents, C1,   */
 /* so that the energy is continuously differentiable in g); dq = dq/du.     */
-static void el_interp(const double* q, int N, double u, double* v, double* dq)
+static void el_interp2(const double* q, int N, double u, double* v, double* dq, double* ddq)
 {
     const double x = u - 0.5;
     const double fl = floor(x);
@@ -483,6 +483,7 @@ static void el_interp(const double* q, int N, double u, double* v, double* dq)
                          0.5 * (-3.0 * f3 + 4.0 * f2 + f), 0.5 * (f3 - f2)};
     const double d[4] = {0.5 * (-3.0 * f2 + 4.0 * f - 1.0), 0.5 * (9.0 * f2 - 10.0 * f),
                          0.5 * (-9.0 * f2 + 8.0 * f + 1.0), 0.5 * (3.0 * f2 - 2.0 * f)};
+    const double dd[4] = {-3.0 * f + 2.0, 9.0 * f - 5.0, -9.0 * f + 4.0, 3.0 * f - 1.0};
     const int id[4] = {jm, j, j1, j2};
     v[0] = v[1] = 0.0;
     for (int c = 0; c < 4; ++c) {
@@ -496,6 +497,18 @@ static void el_interp(const double* q, int N, double u, double* v, double* dq)
             dq[1] += d[c] * q[2 * id[c] + 1];
         }
     }
+    if (ddq) {
+        ddq[0] = ddq[1] = 0.0;
+        for (int c = 0; c < 4; ++c) {
+            ddq[0] += dd[c] * q[2 * id[c]];
+            ddq[1] += dd[c] * q[2 * id[c] + 1];
+        }
+    }
+}
+
+static void el_interp(const double* q, int N, double u, double* v, double* dq)
+{
+    el_interp2(q, N, u, v, dq, NULL);
 }
 
 /* one cell's term |q1s_k - sqrt(D) q2(M)|^2 for gamma from x to y on it    */
@@ -603,22 +616,37 @@ static double el_refine(const double* q1, const double* q2, int N, int s, double
     double* lo = (double*)malloc(cn);
     double* di = (double*)malloc(cn);
     double* up = (double*)malloc(cn);
+    double* Saa = (double*)malloc(cn);  /* <r_k, d2 r_k / d g_k^2>           */
+    double* Sbb = (double*)malloc(cn);  /* <r_k, d2 r_k / d g_{k+1}^2>       */
+    double* Sab = (double*)malloc(cn);  /* <r_k, d2 r_k / d g_k d g_{k+1}>   */
     double lambda = 1e-3;
     for (int it = 0; it < iters && n >= 1; ++it) {
-        double Hcc = 0.0, Hcp = 0.0, Hpp = 0.0, Gc = 0.0, Gp = 0.0;
+        double Hcc = 0.0, Hcp = 0.0, Hpp = 0.0, Gc = 0.0, Gp = 0.0, Scc = 0.0, Spp = 0.0;
         for (int k = 0; k < N; ++k) {
-            double v[2], dv[2];
+            double v[2], dv[2], ddv[2];
             const double D = g[k + 1] - g[k];
-            el_interp(q2, N, 0.5 * (g[k] + g[k + 1]), v, dv);
+            el_interp2(q2, N, 0.5 * (g[k] + g[k + 1]), v, dv, ddv);
             const double m = sqrt(D);
             R[2 * k] = q1s[2 * k] - m * v[0];
             R[2 * k + 1] = q1s[2 * k + 1] - m * v[1];
-            /* r = q1s - sqrt(D) q2(M): dr/dD = -q2/(2 sqrt D), dr/dM = -sqrt(D) q2' */
+            /* r = q1s - sqrt(D) q2(M), with D = g_{k+1} - g_k, M = (g_k + g_{k+1})/2:
+             * r_D = -q2/(2 sqrt D), r_M = -sqrt(D) q2', r_DD = q2/(4 D^{3/2}),
+             * r_DM = -q2'/(2 sqrt D), r_MM = -sqrt(D) q2'';
+             * d/dg_k = -d/dD + d/dM / 2, d/dg_{k+1} = d/dD + d/dM / 2              */
+            double saa = 0.0, sbb = 0.0, sab = 0.0;
             for (int c = 0; c < 2; ++c) {
                 const double rD = -v[c] / (2.0 * m), rM = -m * dv[c];
+                const double rDD = v[c] / (4.0 * D * m), rDM = -dv[c] / (2.0 * m);
+                const double rMM = -m * ddv[c];
                 Ar[2 * k + c] = -rD + 0.5 * rM;
                 Br[2 * k + c] = rD + 0.5 * rM;
+                saa += R[2 * k + c] * (rDD - rDM + 0.25 * rMM);
+                sbb += R[2 * k + c] * (rDD + rDM + 0.25 * rMM);
+                sab += R[2 * k + c] * (-rDD + 0.25 * rMM);
             }
+            Saa[k] = saa;
+            Sbb[k] = sbb;
+            Sab[k] = sab;
             const double ux = Ar[2 * k] + Br[2 * k], uy = Ar[2 * k + 1] + Br[2 * k + 1];
             const double px = -q1s[2 * k + 1], py = q1s[2 * k];  /* dr/dphi = i q1s */
             Hcc += ux * ux + uy * uy;
@@ -626,6 +654,8 @@ static double el_refine(const double* q1, const double* q2, int N, int s, double
             Hpp += px * px + py * py;
             Gc += R[2 * k] * ux + R[2 * k + 1] * uy;
             Gp += R[2 * k] * px + R[2 * k + 1] * py;
+            Scc += saa + 2.0 * sab + sbb;
+            Spp -= R[2 * k] * q1s[2 * k] + R[2 * k + 1] * q1s[2 * k + 1];  /* d2r/dphi2 = -q1s */
         }
         /* rows i = 1..n (unknown h_i) */
         for (int i = 1; i <= n; ++i) {
@@ -636,14 +666,16 @@ static double el_refine(const double* q1, const double* q2, int N, int s, double
             const double* p0 = q1s + 2 * (i - 1);
             const double* p1 = q1s + 2 * i;
             di[i] = (b0[0] * b0[0] + b0[1] * b0[1] + a1[0] * a1[0] + a1[1] * a1[1]) *
-                    (1.0 + lambda);
+                        (1.0 + lambda) +
+                    Sbb[i - 1] + Saa[i];
             x[i] = -(R[2 * (i - 1)] * b0[0] + R[2 * (i - 1) + 1] * b0[1] +
                      R[2 * i] * a1[0] + R[2 * i + 1] * a1[1]);
             Cc[i] = b0[0] * (a0[0] + b0[0]) + b0[1] * (a0[1] + b0[1]) +
-                    a1[0] * (a1[0] + b1[0]) + a1[1] * (a1[1] + b1[1]);
+                    a1[0] * (a1[0] + b1[0]) + a1[1] * (a1[1] + b1[1]) +
+                    Sab[i - 1] + Sbb[i - 1] + Saa[i] + Sab[i];
             Cp[i] = b0[0] * -p0[1] + b0[1] * p0[0] + a1[0] * -p1[1] + a1[1] * p1[0];
-            lo[i] = i > 1 ? a0[0] * b0[0] + a0[1] * b0[1] : 0.0;
-            up[i] = i < n ? a1[0] * b1[0] + a1[1] * b1[1] : 0.0;
+            lo[i] = i > 1 ? a0[0] * b0[0] + a0[1] * b0[1] + Sab[i - 1] : 0.0;
+            up[i] = i < n ? a1[0] * b1[0] + a1[1] * b1[1] + Sab[i] : 0.0;
             yc[i] = Cc[i];
             yp[i] = Cp[i];
         }
@@ -664,7 +696,7 @@ static double el_refine(const double* q1, const double* q2, int N, int s, double
             yp[i] = (yp[i] - up[i] * yp[i + 1]) / di[i];
         }
         /* Schur complement S (2x2) and its right-hand side */
-        double S00 = Hcc * (1.0 + lambda), S01 = Hcp, S11 = Hpp * (1.0 + lambda);
+        double S00 = Hcc * (1.0 + lambda) + Scc, S01 = Hcp, S11 = Hpp * (1.0 + lambda) + Spp;
         double r0 = -Gc, r1 = -Gp;
         for (int i = 1; i <= n; ++i) {
             S00 -= Cc[i] * yc[i];
@@ -711,7 +743,7 @@ static double el_refine(const double* q1, const double* q2, int N, int s, double
         }
     }
     free(q1s); free(qt); free(Ar); free(Br); free(R); free(x); free(yc); free(yp);
-    free(Cc); free(Cp); free(gt); free(lo); free(di); free(up);
+    free(Cc); free(Cp); free(gt); free(lo); free(di); free(up); free(Saa); free(Sbb); free(Sab);
     return E;
 }
 

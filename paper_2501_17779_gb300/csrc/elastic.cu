@@ -24,11 +24,14 @@
 //                     (a) first iteration only: dynamic programme over lattice paths
 //                         (0,0) -> (N,N) with steps (a,b), a,b <= 3, coprime,
 //                         in the band |i - j| <= B, minimising E exactly;
-//                     (b) 16 Levenberg-Marquardt steps on (g_0..g_{N-1},
-//                         theta): Gauss-Newton normal matrix tridiagonal in
-//                         the interior nodes with a border for the offset g_0
-//                         and the angle, solved by parallel cyclic reduction
-//                         (three right-hand sides) and a 2x2 Schur complement;
+//                     (b) damped Newton (Levenberg-Marquardt) steps on
+//                         (g_0..g_{N-1}, theta): the Hessian (Gauss-Newton
+//                         part plus the residual-curvature terms) is
+//                         tridiagonal in the interior nodes with a border for
+//                         the offset g_0 and the angle, solved by parallel
+//                         cyclic reduction (three right-hand sides) and
+//                         a 2x2 Schur complement; at most 64 steps, ending
+//                         after an accepted step gaining <= 1e-12 E;
 //                   (t0,R)-step: the rigid alignment of Sec. 2 of
 //                     w_k = sqrt(D_k) q2(M_k) against q1 over all grid shifts,
 //                     by FFT (the correlation as in the rigid kernels), the
@@ -131,7 +134,7 @@ struct ElasticArgs {
 // periodic Catmull-Rom value (and derivative in u) of the midpoint samples q at
 // u (cell units; sample k sits at u = k + 1/2)
 __device__ __forceinline__ void cr_eval(const double2* __restrict__ q, int N, double u, double2& v,
-                                        double2* dv)
+                                        double2* dv, double2* ddv = nullptr)
 {
     const double x = u - 0.5;
     const double fl = floor(x);
@@ -149,6 +152,11 @@ __device__ __forceinline__ void cr_eval(const double2* __restrict__ q, int N, do
         const double d2 = 0.5 * (-9.0 * f2 + 8.0 * f + 1.0), d3 = 0.5 * (3.0 * f2 - 2.0 * f);
         dv->x = d0 * p0.x + d1 * p1.x + d2 * p2.x + d3 * p3.x;
         dv->y = d0 * p0.y + d1 * p1.y + d2 * p2.y + d3 * p3.y;
+    }
+    if (ddv) {
+        const double e0 = -3.0 * f + 2.0, e1 = 9.0 * f - 5.0, e2 = -9.0 * f + 4.0, e3 = 3.0 * f - 1.0;
+        ddv->x = e0 * p0.x + e1 * p1.x + e2 * p2.x + e3 * p3.x;
+        ddv->y = e0 * p0.y + e1 * p1.y + e2 * p2.y + e3 * p3.y;
     }
 }
 
@@ -309,36 +317,45 @@ __device__ void build_q2f(const double2* q2, int N, double2* q2f)
 }
 
 // ---------------------------------------------------------- refinement ----
-// Parallel cyclic reduction of the symmetric tridiagonal system with rows
-// r = 1..n (lower lo[r], diagonal di[r], upper up[r]) on three right-hand
-// sides x, y1, y2 (all overwritten by the solutions), in float32: it gives
-// the Levenberg-Marquardt step direction, which the FP64 energy test then
-// accepts or rejects.  Out-of-range rows act as identity rows.
+// 1/x for finite x != 0 with |x| in (2^-100, 2^100): float32 seed, two
+// Newton steps in FP64 (r <- r (2 - x r)), relative error at rounding level
+__device__ __forceinline__ double rcp_fast(double x)
+{
+    double r = (double)__frcp_rn((float)x);
+    r = r * fma(-x, r, 2.0);
+    r = r * fma(-x, r, 2.0);
+    return r;
+}
+
+// Parallel cyclic reduction of the tridiagonal system with rows r = 1..n
+// (lower lo[r], diagonal di[r], upper up[r]) on three right-hand sides x, y1,
+// y2 (all overwritten by the solutions), FP64.  Out-of-range rows act as
+// identity rows.
 template <int T, int NMAX>
-__device__ void pcr3(int n, float* lo, float* di, float* up, float* x, float* y1, float* y2)
+__device__ void pcr3(int n, double* lo, double* di, double* up, double* x, double* y1, double* y2)
 {
     constexpr int RMAX = (NMAX - 1 + T - 1) / T;  // rows per thread (n <= NMAX - 1)
     for (int h = 1; h < n; h <<= 1) {
-        float nl[RMAX], nd[RMAX], nu[RMAX], nx[RMAX], n1[RMAX], n2[RMAX];
+        double nl[RMAX], nd[RMAX], nu[RMAX], nx[RMAX], n1[RMAX], n2[RMAX];
 #pragma unroll
         for (int q = 0; q < RMAX; ++q) {
             const int r = 1 + threadIdx.x + q * T;
             if (r <= n) {
-                float dd = di[r], xx = x[r], a1 = y1[r], a2 = y2[r], l2 = 0.0f, u2 = 0.0f;
+                double dd = di[r], xx = x[r], a1 = y1[r], a2 = y2[r], l2 = 0.0, u2 = 0.0;
                 if (r - h >= 1) {
-                    const float al = -lo[r] / di[r - h];
-                    dd = fmaf(al, up[r - h], dd);
-                    xx = fmaf(al, x[r - h], xx);
-                    a1 = fmaf(al, y1[r - h], a1);
-                    a2 = fmaf(al, y2[r - h], a2);
+                    const double al = -lo[r] * rcp_fast(di[r - h]);
+                    dd = fma(al, up[r - h], dd);
+                    xx = fma(al, x[r - h], xx);
+                    a1 = fma(al, y1[r - h], a1);
+                    a2 = fma(al, y2[r - h], a2);
                     l2 = al * lo[r - h];
                 }
                 if (r + h <= n) {
-                    const float ga = -up[r] / di[r + h];
-                    dd = fmaf(ga, lo[r + h], dd);
-                    xx = fmaf(ga, x[r + h], xx);
-                    a1 = fmaf(ga, y1[r + h], a1);
-                    a2 = fmaf(ga, y2[r + h], a2);
+                    const double ga = -up[r] * rcp_fast(di[r + h]);
+                    dd = fma(ga, lo[r + h], dd);
+                    xx = fma(ga, x[r + h], xx);
+                    a1 = fma(ga, y1[r + h], a1);
+                    a2 = fma(ga, y2[r + h], a2);
                     u2 = ga * up[r + h];
                 }
                 nl[q] = l2; nd[q] = dd; nu[q] = u2; nx[q] = xx; n1[q] = a1; n2[q] = a2;
@@ -355,7 +372,7 @@ __device__ void pcr3(int n, float* lo, float* di, float* up, float* x, float* y1
         __syncthreads();
     }
     for (int r = 1 + threadIdx.x; r <= n; r += T) {
-        const float inv = 1.0f / di[r];
+        const double inv = rcp_fast(di[r]);
         x[r] *= inv;
         y1[r] *= inv;
         y2[r] *= inv;
@@ -366,7 +383,8 @@ __device__ void pcr3(int n, float* lo, float* di, float* up, float* x, float* y1
 struct LmArrays {
     double2 *R, *A, *Bv;
     double *Cc, *Cp;
-    float *di, *xv, *lo, *up, *yc, *yp;
+    double *Saa, *Sbb, *Sab;   // <r_k, second derivatives of r_k> (full Newton terms)
+    double *di, *xv, *lo, *up, *yc, *yp;
 };
 
 // Levenberg-Marquardt refinement of (g, theta) for the shift s; returns N E
@@ -382,24 +400,36 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
     double En = energy_n<T>(q1, q2, N, s, cs, g, red);
     double lambda = 1e-3;
     for (int it = 0; it < kLmIters; ++it) {
-        double h[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // Hcc, Hcp, Hpp, Gc, Gp
+        // Hcc, Hcp, Hpp, Gc, Gp (Gauss-Newton parts), Scc, Spp (second-order parts)
+        double h[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int k = tid; k < N; k += T) {
-            double2 v, dv;
-            cr_eval(q2, N, 0.5 * (g[k] + g[k + 1]), v, &dv);
+            double2 v, dv, ddv;
+            cr_eval(q2, N, 0.5 * (g[k] + g[k + 1]), v, &dv, &ddv);
             const double D = g[k + 1] - g[k];
             const double rs = rsqrt_fast(D);
             const double m = D * rs;
             const double hm = 0.5 * rs;
             const double2 u = rot(cs, q1[(k + s) & (N - 1)]);
             const double2 r = make_double2(fma(-m, v.x, u.x), fma(-m, v.y, u.y));
-            // dr/dD = -q2 / (2 sqrt D), dr/dM = -sqrt(D) q2'
+            // r = u - sqrt(D) q2(M): r_D = -q2/(2 sqrt D), r_M = -sqrt(D) q2',
+            // r_DD = q2/(4 D^{3/2}), r_DM = -q2'/(2 sqrt D), r_MM = -sqrt(D) q2'';
+            // d/dg_k = -d/dD + d/dM / 2, d/dg_{k+1} = d/dD + d/dM / 2
             const double2 rD = make_double2(-v.x * hm, -v.y * hm);
             const double2 rM = make_double2(-m * dv.x, -m * dv.y);
+            const double q4 = 0.5 * hm * rs * rs;  // 1 / (4 D^{3/2})
+            const double2 rDD = make_double2(v.x * q4, v.y * q4);
+            const double2 rDM = make_double2(-dv.x * hm, -dv.y * hm);
+            const double2 rMM = make_double2(-m * ddv.x, -m * ddv.y);
             const double2 a = make_double2(fma(0.5, rM.x, -rD.x), fma(0.5, rM.y, -rD.y));
             const double2 b = make_double2(fma(0.5, rM.x, rD.x), fma(0.5, rM.y, rD.y));
+            const double pDD = r.x * rDD.x + r.y * rDD.y, pDM = r.x * rDM.x + r.y * rDM.y;
+            const double pMM = 0.25 * (r.x * rMM.x + r.y * rMM.y);
             L.R[k] = r;
             L.A[k] = a;
             L.Bv[k] = b;
+            L.Saa[k] = pDD - pDM + pMM;
+            L.Sbb[k] = pDD + pDM + pMM;
+            L.Sab[k] = pMM - pDD;
             const double ux = a.x + b.x, uy = a.y + b.y;
             const double px = -u.y, py = u.x;
             h[0] = fma(ux, ux, fma(uy, uy, h[0]));
@@ -407,24 +437,28 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
             h[2] = fma(px, px, fma(py, py, h[2]));
             h[3] = fma(r.x, ux, fma(r.y, uy, h[3]));
             h[4] = fma(r.x, px, fma(r.y, py, h[4]));
+            h[5] += 4.0 * pMM;                      // <r, r_MM>: c moves M only
+            h[6] -= r.x * u.x + r.y * u.y;          // d2r/dphi2 = -u
         }
-        cta_sums<T, 5>(h, red);  // includes the barrier that publishes R, A, Bv
+        cta_sums<T, 7>(h, red);  // includes the barrier that publishes R, A, Bv, S..
         for (int i = 1 + tid; i <= n; i += T) {
             const double2 b0 = L.Bv[i - 1], a0 = L.A[i - 1], a1 = L.A[i], b1 = L.Bv[i];
             const double2 r0 = L.R[i - 1], r1 = L.R[i];
             const double2 p0 = rot(cs, q1[(i - 1 + s) & (N - 1)]);
             const double2 p1 = rot(cs, q1[(i + s) & (N - 1)]);
-            L.di[i] = (float)((b0.x * b0.x + b0.y * b0.y + a1.x * a1.x + a1.y * a1.y) * (1.0 + lambda));
-            L.xv[i] = (float)(-(r0.x * b0.x + r0.y * b0.y + r1.x * a1.x + r1.y * a1.y));
+            const double sbb0 = L.Sbb[i - 1], sab0 = L.Sab[i - 1], saa1 = L.Saa[i], sab1 = L.Sab[i];
+            L.di[i] = (b0.x * b0.x + b0.y * b0.y + a1.x * a1.x + a1.y * a1.y) * (1.0 + lambda) +
+                      sbb0 + saa1;
+            L.xv[i] = -(r0.x * b0.x + r0.y * b0.y + r1.x * a1.x + r1.y * a1.y);
             const double cc = b0.x * (a0.x + b0.x) + b0.y * (a0.y + b0.y) + a1.x * (a1.x + b1.x) +
-                              a1.y * (a1.y + b1.y);
+                              a1.y * (a1.y + b1.y) + sab0 + sbb0 + saa1 + sab1;
             const double cp = b0.x * -p0.y + b0.y * p0.x + a1.x * -p1.y + a1.y * p1.x;
             L.Cc[i] = cc;
             L.Cp[i] = cp;
-            L.yc[i] = (float)cc;
-            L.yp[i] = (float)cp;
-            L.lo[i] = i > 1 ? (float)(a0.x * b0.x + a0.y * b0.y) : 0.0f;
-            L.up[i] = i < n ? (float)(a1.x * b1.x + a1.y * b1.y) : 0.0f;
+            L.yc[i] = cc;
+            L.yp[i] = cp;
+            L.lo[i] = i > 1 ? a0.x * b0.x + a0.y * b0.y + sab0 : 0.0;
+            L.up[i] = i < n ? a1.x * b1.x + a1.y * b1.y + sab1 : 0.0;
         }
         __syncthreads();
         pcr3<T, NMAX>(n, L.lo, L.di, L.up, L.xv, L.yc, L.yp);
@@ -438,8 +472,8 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
             sc[4] = fma(L.Cp[i], xv, sc[4]);
         }
         cta_sums<T, 5>(sc, red);
-        const double S00 = h[0] * (1.0 + lambda) - sc[0], S01 = h[1] - sc[1];
-        const double S11 = h[2] * (1.0 + lambda) - sc[2];
+        const double S00 = h[0] * (1.0 + lambda) + h[5] - sc[0], S01 = h[1] - sc[1];
+        const double S11 = h[2] * (1.0 + lambda) + h[6] - sc[2];
         const double r0 = -h[3] - sc[3], r1 = -h[4] - sc[4];
         const double det = S00 * S11 - S01 * S01;
         double dc = 0.0, dphi = 0.0;
@@ -449,8 +483,7 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
         }
         // step on the interior nodes, then the slope-keeping shortening
         for (int k = tid; k <= N; k += T)
-            gt[k] = (k == 0 || k == N) ? 0.0
-                                       : (double)L.xv[k] - (double)L.yc[k] * dc - (double)L.yp[k] * dphi;
+            gt[k] = (k == 0 || k == N) ? 0.0 : L.xv[k] - L.yc[k] * dc - L.yp[k] * dphi;
         __syncthreads();
         double al = 1.0;
         for (int k = tid; k < N; k += T) {
@@ -529,8 +562,8 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
     double2* q1s = Y + N;
     double* g = reinterpret_cast<double*>(q1s + N);
     double* gt = g + (N + 1);
-    double* ar = gt + (N + 1);                 // 8 (N+1): solver arrays / DP ring
-    double* red = ar + 8 * (N + 1);            // (T/32 + 1) * 8
+    double* ar = gt + (N + 1);                 // 11 (N+1): solver arrays / DP ring
+    double* red = ar + 11 * (N + 1);           // (T/32 + 1) * 8
     long long* sk = reinterpret_cast<long long*>(red + (T / 32 + 1) * 8);
     int* si = reinterpret_cast<int*>(sk + T / 32);
     int* ib = si + T / 32;                     // [4] broadcast ints
@@ -548,11 +581,9 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
     LmArrays L;
     L.R = X; L.A = Y; L.Bv = q1s;
     L.Cc = ar; L.Cp = ar + (N + 1);
-    {
-        float* f = reinterpret_cast<float*>(ar + 2 * (N + 1));
-        L.di = f; L.xv = f + (N + 1); L.lo = f + 2 * (N + 1); L.up = f + 3 * (N + 1);
-        L.yc = f + 4 * (N + 1); L.yp = f + 5 * (N + 1);
-    }
+    L.di = ar + 2 * (N + 1); L.xv = ar + 3 * (N + 1); L.lo = ar + 4 * (N + 1);
+    L.up = ar + 5 * (N + 1); L.yc = ar + 6 * (N + 1); L.yp = ar + 7 * (N + 1);
+    L.Saa = ar + 8 * (N + 1); L.Sbb = ar + 9 * (N + 1); L.Sab = ar + 10 * (N + 1);
     const double nanv = __longlong_as_double(0x7ff8000000000000LL);
 
     for (int64_t pair = blockIdx.x; pair < a.P; pair += gridDim.x) {
@@ -745,7 +776,7 @@ ElLayout el_layout(const fa_handle* h, int64_t Mtot, int64_t P, int N, int band)
     const int W = B < N ? 2 * B + 1 : N;
     L.q2f_elems = (int64_t)kNFrac * (N + 2);
     L.bp_bytes = (int64_t)N * W;
-    size_t fixed = 6 * (size_t)N * sizeof(double2) + 10 * (size_t)(N + 1) * sizeof(double) +
+    size_t fixed = 6 * (size_t)N * sizeof(double2) + 13 * (size_t)(N + 1) * sizeof(double) +
                    (kElT / 32 + 1) * 8 * sizeof(double) + (kElT / 32) * (sizeof(long long) + sizeof(int)) +
                    4 * sizeof(int) + 16;
     size_t sm = fixed;
