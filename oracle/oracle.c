@@ -445,14 +445,17 @@ int oracle_max_threads(void)
 /*          (t0,R)-step keeps gamma and lowers E, and the refinement's free  */
 /*          offset g_0 follows it);                                         */
 /*      (b) a continuous refinement of all g_k (g_0 too) jointly with theta:*/
-/*          Levenberg-Marquardt steps on the residuals                      */
-/*          r_k = q1s_k - sqrt(D_k) q2(M_k) (Gauss-Newton normal matrix,     */
-/*          tridiagonal in g with a border for theta), each step shortened  */
+/*          damped Newton (Levenberg-Marquardt) steps on E = (1/N) sum      */
+/*          |r_k|^2, r_k = q1s_k - sqrt(D_k) q2(M_k): the Hessian (the        */
+/*          Gauss-Newton part, damped, plus the residual-curvature terms)   */
+/*          is tridiagonal in g with a border for theta; each step shortened*/
 /*          to keep every D_k above half its value and accepted only if E   */
 /*          decreases; at most 64 steps, ending after an accepted step that  */
 /*          lowers E by <= 1e-12 E or once the damping exceeds 1e6.          */
 /*          Without theta in it the alternation converges only              */
-/*          linearly (gamma partly absorbs a rotation error).               */
+/*          linearly (gamma partly absorbs a rotation error); without the   */
+/*          curvature terms the steps converge only linearly where rotation */
+/*          and the offset nearly trade off (round shapes).                 */
 /*  - the (t0,R)-step is the rigid alignment of Sec. 2 (O1's criterion) of  */
 /*    w_k = sqrt(D_k) q2(M_k) against q1 over all grid shifts s.            */
 /* ------------------------------------------------------------------------ */
@@ -590,9 +593,10 @@ static void el_move(const double* q1, int N, int s, double theta, double* q1s)
 /* periodically, gamma(t+1) = gamma(t) + 1, so that together with the grid  */
 /* shift s the start point t0 is continuous as in Eq. dist2-energy) and the */
 /* rotation increment phi; residuals r_k = e^{i phi} q1s_k -                */
-/* sqrt(D_k) q2(M_k).  The Gauss-Newton normal matrix is tridiagonal in h   */
-/* with a two-column border (c, phi): Thomas algorithm on three right-hand  */
-/* sides, then a 2x2 Schur complement.  Returns the energy of the refined   */
+/* sqrt(D_k) q2(M_k).  Newton matrix: J^T J with its diagonal scaled by     */
+/* (1 + lambda), plus sum_k <r_k, d2 r_k>; it is tridiagonal in h with a    */
+/* two-column border (c, phi): Thomas algorithm on three right-hand sides,  */
+/* then a 2x2 Schur complement.  Returns the energy of the refined          */
 /* (theta, g).                                                              */
 static double el_refine(const double* q1, const double* q2, int N, int s, double* theta,
                         double* g, int iters)
