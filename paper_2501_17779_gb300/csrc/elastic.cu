@@ -332,18 +332,21 @@ __device__ __forceinline__ double rcp_fast(double x)
 // y2 (all overwritten by the solutions), FP64.  Out-of-range rows act as
 // identity rows.
 template <int T, int NMAX>
-__device__ void pcr3(int n, double* lo, double* di, double* up, double* x, double* y1, double* y2)
+__device__ void pcr3(int n, double* lo, double* di, double* up, double* x, double* y1, double* y2,
+                     double* inv)
 {
     constexpr int RMAX = (NMAX - 1 + T - 1) / T;  // rows per thread (n <= NMAX - 1)
     for (int h = 1; h < n; h <<= 1) {
         double nl[RMAX], nd[RMAX], nu[RMAX], nx[RMAX], n1[RMAX], n2[RMAX];
+        for (int r = 1 + threadIdx.x; r <= n; r += T) inv[r] = rcp_fast(di[r]);
+        __syncthreads();
 #pragma unroll
         for (int q = 0; q < RMAX; ++q) {
             const int r = 1 + threadIdx.x + q * T;
             if (r <= n) {
                 double dd = di[r], xx = x[r], a1 = y1[r], a2 = y2[r], l2 = 0.0, u2 = 0.0;
                 if (r - h >= 1) {
-                    const double al = -lo[r] * rcp_fast(di[r - h]);
+                    const double al = -lo[r] * inv[r - h];
                     dd = fma(al, up[r - h], dd);
                     xx = fma(al, x[r - h], xx);
                     a1 = fma(al, y1[r - h], a1);
@@ -351,7 +354,7 @@ __device__ void pcr3(int n, double* lo, double* di, double* up, double* x, doubl
                     l2 = al * lo[r - h];
                 }
                 if (r + h <= n) {
-                    const double ga = -up[r] * rcp_fast(di[r + h]);
+                    const double ga = -up[r] * inv[r + h];
                     dd = fma(ga, lo[r + h], dd);
                     xx = fma(ga, x[r + h], xx);
                     a1 = fma(ga, y1[r + h], a1);
@@ -384,7 +387,7 @@ struct LmArrays {
     double2 *R, *A, *Bv;
     double *Cc, *Cp;
     double *Saa, *Sbb, *Sab;   // <r_k, second derivatives of r_k> (full Newton terms)
-    double *di, *xv, *lo, *up, *yc, *yp;
+    double *di, *xv, *lo, *up, *yc, *yp, *inv;
 };
 
 // Levenberg-Marquardt refinement of (g, theta) for the shift s; returns N E
@@ -395,8 +398,10 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
 {
     const int tid = threadIdx.x;
     const int n = N - 1;
-    double2 cs;
-    sincos(theta, &cs.y, &cs.x);
+    double* bc = red + (T / 32 + 1) * 8 - 2;  // broadcast slot (the reductions use fewer)
+    if (tid == 0) sincos(theta, &bc[1], &bc[0]);
+    __syncthreads();
+    double2 cs = make_double2(bc[0], bc[1]);
     double En = energy_n<T>(q1, q2, N, s, cs, g, red);
     double lambda = 1e-3;
     for (int it = 0; it < kLmIters; ++it) {
@@ -461,7 +466,7 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
             L.up[i] = i < n ? a1.x * b1.x + a1.y * b1.y + sab1 : 0.0;
         }
         __syncthreads();
-        pcr3<T, NMAX>(n, L.lo, L.di, L.up, L.xv, L.yc, L.yp);
+        pcr3<T, NMAX>(n, L.lo, L.di, L.up, L.xv, L.yc, L.yp, L.inv);
         double sc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // Cc.yc, Cc.yp, Cp.yp, Cc.x, Cp.x
         for (int i = 1 + tid; i <= n; i += T) {
             const double yc = L.yc[i], yp = L.yp[i], xv = L.xv[i];
@@ -493,9 +498,9 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
         al = cta_min<T>(al, red);
         for (int k = tid; k <= N; k += T) gt[k] = fma(al, dc + gt[k], g[k]);
         const double tht = fma(al, dphi, theta);
-        double2 ct;
-        sincos(tht, &ct.y, &ct.x);
+        if (tid == 0) sincos(tht, &bc[1], &bc[0]);
         __syncthreads();
+        const double2 ct = make_double2(bc[0], bc[1]);
         const double Et = energy_n<T>(q1, q2, N, s, ct, gt, red);
         bool stop;
         if (Et < En) {
@@ -562,8 +567,8 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
     double2* q1s = Y + N;
     double* g = reinterpret_cast<double*>(q1s + N);
     double* gt = g + (N + 1);
-    double* ar = gt + (N + 1);                 // 11 (N+1): solver arrays / DP ring
-    double* red = ar + 11 * (N + 1);           // (T/32 + 1) * 8
+    double* ar = gt + (N + 1);                 // 12 (N+1): solver arrays / DP ring
+    double* red = ar + 12 * (N + 1);           // (T/32 + 1) * 8
     long long* sk = reinterpret_cast<long long*>(red + (T / 32 + 1) * 8);
     int* si = reinterpret_cast<int*>(sk + T / 32);
     int* ib = si + T / 32;                     // [4] broadcast ints
@@ -584,6 +589,7 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
     L.di = ar + 2 * (N + 1); L.xv = ar + 3 * (N + 1); L.lo = ar + 4 * (N + 1);
     L.up = ar + 5 * (N + 1); L.yc = ar + 6 * (N + 1); L.yp = ar + 7 * (N + 1);
     L.Saa = ar + 8 * (N + 1); L.Sbb = ar + 9 * (N + 1); L.Sab = ar + 10 * (N + 1);
+    L.inv = ar + 11 * (N + 1);
     const double nanv = __longlong_as_double(0x7ff8000000000000LL);
 
     for (int64_t pair = blockIdx.x; pair < a.P; pair += gridDim.x) {
@@ -776,7 +782,7 @@ ElLayout el_layout(const fa_handle* h, int64_t Mtot, int64_t P, int N, int band)
     const int W = B < N ? 2 * B + 1 : N;
     L.q2f_elems = (int64_t)kNFrac * (N + 2);
     L.bp_bytes = (int64_t)N * W;
-    size_t fixed = 6 * (size_t)N * sizeof(double2) + 13 * (size_t)(N + 1) * sizeof(double) +
+    size_t fixed = 6 * (size_t)N * sizeof(double2) + 14 * (size_t)(N + 1) * sizeof(double) +
                    (kElT / 32 + 1) * 8 * sizeof(double) + (kElT / 32) * (sizeof(long long) + sizeof(int)) +
                    4 * sizeof(int) + 16;
     size_t sm = fixed;
