@@ -39,6 +39,10 @@ P_PAIRS = 4096
 N_NODES = 1024
 N_MIN, N_MAX = 500, 2000
 SEED = 1002
+# DRAM bytes per launch of the bench workload's kernels, from one ncu capture of the
+# current kernel versions (profiles/*_4096pairs_n1024.md); update when a kernel changes
+DRAM_TRAFFIC_PER_LAUNCH = {"resample_kernel": 1.971814e9 + 1.082025e9,
+                           "align_fft_kernel": 1.35009e8 + 6.549e6}
 METRIC = "aligned curve pairs/s at N=1024 (FFT vs direct O(N²), 1 GB300); roofline fraction"
 WORKLOAD = ("4096 pairs of raw curves (N_in ~ U{500..2000}, +-40% node jitter, <=16 harmonics), "
             "GPU arc-length resampling to N=1024 + FFT alignment over all shifts, FP64")
@@ -361,9 +365,12 @@ def run_gpu(args):
                              "flops_per_launch": fl_al},
     }
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    traffic = args.traffic if args.traffic is not None else DRAM_TRAFFIC_PER_LAUNCH.get(dom)
     roof = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["tflops"], "peak": fp64_peak,
             "unit": "TFLOP/s", "frac": kernels[dom]["tflops"] / fp64_peak,
-            "traffic": args.traffic, "peak_kind": "FP64 FMA throughput measured in this run "
+            "traffic": traffic, "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum "
+            f"of one ncu capture of this kernel version (profiles/{dom}_4096pairs_n1024.md)",
+            "peak_kind": "FP64 FMA throughput measured in this run "
             f"(nominal {FP64_NOMINAL_TFLOPS})", "of": "measured"}
 
     # end to end through the C ABI with pinned host buffers
