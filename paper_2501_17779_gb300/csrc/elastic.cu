@@ -1,5 +1,6 @@
 // elastic.cu -- fa_elastic_distance: the elastic shape distance of Sec. 3,
-// FP64, one CTA per curve pair (persistent grid).
+// FP64, one CTA per curve pair (persistent grid, pairs taken from an atomic
+// counter).
 //
 // Representation.  A curve is N nodes, node k at parameter t = k/N, scaled
 // to a unit-length closed polygon.  Its SRV function q = beta'/|beta'|^{1/2}
@@ -117,6 +118,7 @@ struct ElasticArgs {
     const int64_t* idx1;    // pair -> curve of set 1 (nullable: identity)
     const int64_t* idx2;    // pair -> curve of set 2 (nullable: identity)
     int64_t M1, M2, P;
+    unsigned long long* next;  // work counter (zeroed before the launch)
     int N, logn, band, max_iter;
     double2* q2f_ws;        // per-CTA slices, used when q2f_smem == 0
     uint8_t* bp_ws;
@@ -592,7 +594,18 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
     L.inv = ar + 11 * (N + 1);
     const double nanv = __longlong_as_double(0x7ff8000000000000LL);
 
-    for (int64_t pair = blockIdx.x; pair < a.P; pair += gridDim.x) {
+    // pairs are taken from a global counter (iteration counts differ between
+    // pairs; a fixed stride would leave the slowest CTA as the tail)
+    for (;;) {
+        if (tid == 0) {
+            const unsigned long long t = atomicAdd(a.next, 1ull);
+            ib[2] = (int)(t >> 32);
+            ib[3] = (int)(t & 0xffffffffu);
+        }
+        __syncthreads();
+        const int64_t pair = ((int64_t)(unsigned)ib[2] << 32) | (int64_t)(unsigned)ib[3];
+        __syncthreads();
+        if (pair >= a.P) break;
         const int64_t i1 = a.idx1 ? a.idx1[pair] : pair;
         const int64_t i2 = a.idx2 ? a.idx2[pair] : pair;
         const bool inr = i1 >= 0 && i1 < a.M1 && i2 >= 0 && i2 < a.M2;
@@ -767,7 +780,7 @@ __global__ void uniform_offsets_kernel(int64_t* off, int64_t M, int N)
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct ElLayout {
-    size_t off_offsets, off_rws, off_zr, off_q, off_sigma, off_cst, off_rst, off_slots, total;
+    size_t off_offsets, off_rws, off_zr, off_q, off_sigma, off_cst, off_rst, off_next, off_slots, total;
     size_t smem;
     int q2f_smem, bp_smem, grid;
     int64_t q2f_elems, bp_bytes;
@@ -801,6 +814,7 @@ ElLayout el_layout(const fa_handle* h, int64_t Mtot, int64_t P, int N, int band)
     L.off_sigma = o; o = align256(o + sizeof(double) * (size_t)Mtot * (N + 1));
     L.off_cst = o; o = align256(o + (size_t)Mtot);
     L.off_rst = o; o = align256(o + (size_t)Mtot);
+    L.off_next = o; o = align256(o + sizeof(unsigned long long));
     L.off_slots = o;
     if (!L.q2f_smem) o += align256(sizeof(double2) * (size_t)L.q2f_elems * L.grid);
     if (!L.bp_smem) o += align256((size_t)L.bp_bytes * L.grid);
@@ -830,6 +844,7 @@ int launch_elastic(const fa_handle* h, const double* set1, int64_t M1, const dou
     int8_t* cst = reinterpret_cast<int8_t*>(base + L.off_cst);
     int8_t* rst = reinterpret_cast<int8_t*>(base + L.off_rst);
     unsigned char* slots = base + L.off_slots;
+    unsigned long long* next = reinterpret_cast<unsigned long long*>(base + L.off_next);
 
     // the two curve sets as one list: set 1 then set 2 (resampling reads one
     // point array, so set 2 follows set 1 in it through the offsets when the
@@ -854,7 +869,7 @@ int launch_elastic(const fa_handle* h, const double* set1, int64_t M1, const dou
     if (rc != FA_OK) return rc;
     ElasticArgs A{};
     A.q = q; A.sigma = sigma; A.zr = zr; A.cst = cst; A.idx1 = idx1; A.idx2 = idx2;
-    A.M1 = M1; A.M2 = M2; A.P = P; A.N = N; A.logn = 31 - __builtin_clz((unsigned)N);
+    A.M1 = M1; A.M2 = M2; A.P = P; A.next = next; A.N = N; A.logn = 31 - __builtin_clz((unsigned)N);
     A.band = band; A.max_iter = max_iter;
     A.q2f_elems = L.q2f_elems; A.bp_bytes = L.bp_bytes;
     A.q2f_smem = L.q2f_smem; A.bp_smem = L.bp_smem;
@@ -870,6 +885,8 @@ int launch_elastic(const fa_handle* h, const double* set1, int64_t M1, const dou
             kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
         if (e != cudaSuccess) return cuda_error(e, "elastic: cudaFuncSetAttribute");
     }
+    const cudaError_t me = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+    if (me != cudaSuccess) return cuda_error(me, "elastic counter reset");
     kern<<<L.grid, kElT, L.smem, st>>>(A);
     return cuda_error(cudaGetLastError(), "elastic launch");
 }
