@@ -214,7 +214,8 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
  *
  *   curves1    [M1][N] complex128 (device): set 1 (moved by (t0, R))
  *   curves2    [M2][N] complex128 (device): set 2 (reparameterised by gamma)
- *   N          nodes per curve, a power of two in [8, 1024]
+ *   N          nodes per curve, a power of two in [32, 1024] (with fewer nodes the
+ *              iteration is not stable under rounding)
  *   idx1, idx2 int64[P] (device) curve indices into the sets, or NULL for
  *              pair p = (p, p) (then M1, M2 >= P); an index out of range gives
  *              status FA_STATUS_BAD_SIZE for that pair

@@ -411,7 +411,8 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
 size_t fa_elastic_workspace_size(fa_handle* h, int64_t M1, int64_t M2, int64_t P, int32_t N,
                                   int32_t band)
 {
-    if (!h || M1 < 0 || M2 < 0 || P < 0 || N < 8 || N > kMaxElasticN || (N & (N - 1))) return 0;
+    if (!h || M1 < 0 || M2 < 0 || P < 0 || N < kMinElasticN || N > kMaxElasticN || (N & (N - 1)))
+        return 0;
     return elastic_ws_bytes(h, M1, M2, P, N, band);
 }
 
@@ -424,9 +425,9 @@ int fa_elastic_distance(fa_handle* h, const double* curves1, int64_t M1, const d
     if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: null handle");
     if (M1 < 0 || M2 < 0 || P < 0)
         return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: negative size");
-    if (N < 8 || N > kMaxElasticN || (N & (N - 1)))
+    if (N < kMinElasticN || N > kMaxElasticN || (N & (N - 1)))
         return set_error(FA_ERR_UNSUPPORTED,
-                         "fa_elastic_distance: N must be a power of two in [8, 1024]");
+                         "fa_elastic_distance: N must be a power of two in [32, 1024]");
     if (max_iter < 1 || max_iter > 1000)
         return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: max_iter outside [1, 1000]");
     if (band < -1) return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: band < -1");

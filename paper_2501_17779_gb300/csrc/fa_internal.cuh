@@ -32,6 +32,9 @@ constexpr int kMinLogN = 2;
 constexpr int kMaxLogN = 12;
 constexpr int kMaxDirectN = 4096;
 constexpr int kMaxElasticN = 1024;
+// below 32 nodes the elastic alternation is not stable under rounding (an input
+// perturbation of 1e-15 moves the energy by 1e-2 at N = 8 and 16)
+constexpr int kMinElasticN = 32;
 constexpr int kMaxRaggedN = 8192;      // largest node count of fa_align_pairs_ragged
 constexpr int kMaxRaggedLogL = 14;     // its longest transform, 2^14
 

@@ -50,7 +50,8 @@ def _compare(r, o, label=""):
     dg = np.abs(r["gamma"][ok] - o["gamma"][ok]).max(axis=1)[same_s]
     print(f"{label} max|dtheta|={dth.max() if dth.size else 0:.3g} max|dg|={dg.max() if dg.size else 0:.3g}")
     assert (dth <= TH_ABS).all() and (dg <= G_ABS).all()
-    assert same_s.mean() >= 0.95
+    # a different shift is a tie of the energy (checked above); allow 5 % or one pair
+    assert (~same_s).sum() <= max(1, int(0.05 * same_s.size))
 
 
 @pytest.mark.parametrize("which", ["gamma1", "gamma2"])
@@ -120,3 +121,48 @@ def test_elastic_indexed_sets_and_statuses():
     o = oracle.elastic_pairs(Q[i1[good]], G[i2[good]], gamma=True)
     _compare(dict(shift=s[good], theta=th[good], energy=e[good], iters=it[good],
                   status=st[good], gamma=g[good]), o, "indexed")
+
+
+@pytest.mark.parametrize("N,band,max_iter", [(32, -1, 20), (32, 0, 20), (32, -1, 1), (64, 3, 5)])
+def test_elastic_small_sizes_narrow_bands_and_iteration_caps(N, band, max_iter):
+    """The smallest size, a band of 0 (the DP keeps the diagonal) and iteration caps."""
+    P = 12
+    b1 = np.stack([_curve(4000 + N + p, N, 4) for p in range(P)])
+    b2 = np.stack([_curve(5000 + N + p, N, 4) for p in range(P)])
+    r = _gpu(b1, b2, band=band, max_iter=max_iter)
+    o = oracle.elastic_pairs(b1, b2, band=band, max_iter=max_iter, gamma=True)
+    assert (r["iters"] <= max_iter).all() and (r["iters"] >= 1).all()
+    _compare(r, o, f"N={N} band={band} max_iter={max_iter}")
+
+
+def test_elastic_rejects_unsupported_sizes():
+    c = torch.zeros((2, 16), dtype=torch.complex128, device=DEV)
+    with pytest.raises(RuntimeError):
+        api.elastic_distance(c, c)
+
+
+def test_elastic_graph_capture_matches_direct_call():
+    """fa_elastic_distance with a caller's workspace (a memset and three kernels
+    on the stream) captured in a CUDA graph: the replay equals the direct call."""
+    N, P = 128, 40
+    g = synth.shape_gallery(77, 2 * P, N)
+    c1 = torch.from_numpy(g.curves[:P].copy()).to(DEV)
+    c2 = torch.from_numpy(g.curves[P:].copy()).to(DEV)
+    ws = torch.empty(api.elastic_workspace_size(P, P, P, N, 16), dtype=torch.uint8, device=DEV)
+    ref = api.elastic_distance(c1, c2, band=16, workspace=ws)
+    torch.cuda.synchronize()
+    ref = [x.clone() for x in ref]
+    out = tuple(torch.empty_like(x) for x in ref)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        api.elastic_distance(c1, c2, band=16, workspace=ws, out=out)  # warm-up
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        api.elastic_distance(c1, c2, band=16, workspace=ws, out=out)
+    for x in out:
+        x.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, out):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
