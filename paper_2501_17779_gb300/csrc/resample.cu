@@ -10,10 +10,11 @@
 //      cumulative arc lengths S_l = L u_l, the periodic-spline equations
 //          h_{l-1} M_{l-1} + 2(h_{l-1}+h_l) M_l + h_l M_{l+1}
 //              = 6[(p_{l+1}-p_l)/h_l - (p_l-p_{l-1})/h_{l-1}],   h_l = d_l / L,
-//      multiplied through by L so that they read
-//          d_{l-1} M_{l-1} + 2(d_{l-1}+d_l) M_l + d_l M_{l+1} = 6 L^2 (tau_l - tau_{l-1})
-//      with the unit chord directions tau_l = (p_{l+1}-p_l)/d_l (same M, fewer
-//      FP64 instructions), and the Thomas elimination of the interior with the chunk's two
+//      multiplied through by L and solved for M' = M / (6 L^2), so that they read
+//          d_{l-1} M'_{l-1} + 2(d_{l-1}+d_l) M'_l + d_l M'_{l+1} = tau_l - tau_{l-1}
+//      with the unit chord directions tau_l = (p_{l+1}-p_l)/d_l (fewer FP64
+//      instructions; the evaluation's h_l^2 M / 6 is d_l^2 M'), and the Thomas
+//      elimination of the interior with the chunk's two
 //      neighbouring interface nodes (the last node of the previous chunk and
 //      of this chunk) kept as unknowns: M_i = y_i - I_{j-1} g_i - I_j k_i.
 //   C. a backward sweep without stores gives y, g, k at the first interior
@@ -202,53 +203,63 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
     }
     const double L = __shfl_sync(0xffffffffu, incl, 31);
     const double base = incl - csum;  // arc length before node s_j
-    const double L6sq = 6.0 * L * L;
     __syncwarp();
 
     // ---- B: forward sweep over the interior ---------------------------------
+    // The system is solved for M' = M / (6 L^2) (right-hand sides tau_l -
+    // tau_{l-1}); the evaluation uses h^2 M' = h^2 M / (6 L^2).  The first
+    // row needs no special case: with c' = 0, y' = 0, g' = -1 the general
+    // recurrence gives exactly den = B, y' = R / B, g' = h_{l-1} / B.
     // interface-node equation data kept for the reduced system
     double Ae = 0, Be = 0, Ce = 0;
     double2 Re = d2(0, 0), yL = d2(0, 0);
     double gL = 0, kL = 0;
     if (act) {
+        const double* __restrict__ Dr = D;
+        const double* __restrict__ IHr = IH;
+        double* __restrict__ Ur = U;
+        double2* __restrict__ F0r = F0;
+        double2* __restrict__ F1r = F1;
         const int lp = (sj == 0) ? n - 1 : sj - 1;
-        double hprev = D[lp];
+        double hprev = Dr[lp];
         double2 pcur = __ldg(p + sj);
-        double2 tprev = scl2(sub2(pcur, __ldg(p + lp)), IH[lp]);
+        double2 tprev = scl2(sub2(pcur, __ldg(p + lp)), IHr[lp]);
         double S = base;
-        double cp = 0, gp = 0;
+        double cp = 0, gp = -1.0;
         double2 yp = d2(0, 0);
+        // operands of the next row, loaded one row ahead
+        double h = Dr[sj], ih = IHr[sj];
+        double2 pn = __ldg(p + sj + 1);  // sj + 1 <= ej < n
         for (int i = sj; i < ej; ++i) {
-            const double h = D[i];
-            U[i] = S;
+            const int i2 = (i + 2 < n) ? i + 2 : i + 2 - n;
+            const double hn = Dr[i + 1], ihn = IHr[i + 1];  // i + 1 <= ej < n
+            const double2 pnn = __ldg(p + i2);
+            Ur[i] = S;
             S += h;
-            const double2 pn = __ldg(p + i + 1);  // i + 1 <= ej < n
-            const double2 tau = scl2(sub2(pn, pcur), IH[i]);
-            const double2 R = scl2(sub2(tau, tprev), L6sq);
+            const double2 tau = scl2(sub2(pn, pcur), ih);
+            const double2 R = sub2(tau, tprev);
             const double B = 2.0 * (hprev + h);
-            const bool first = (i == sj);
-            const double den = first ? B : fma(-hprev, cp, B);
+            const double den = fma(-hprev, cp, B);
             const double r = rcp_nr(den);
             const double ncp = h * r;
-            const double2 nyp = first ? scl2(R, r)
-                                      : d2((R.x - hprev * yp.x) * r, (R.y - hprev * yp.y) * r);
-            const double ngp = first ? hprev * r : -hprev * gp * r;
-            F0[i] = d2(ncp, ngp);
-            F1[i] = nyp;
+            const double2 nyp = d2((R.x - hprev * yp.x) * r, (R.y - hprev * yp.y) * r);
+            const double ngp = -hprev * gp * r;
+            F0r[i] = d2(ncp, ngp);
+            F1r[i] = nyp;
             cp = ncp; gp = ngp; yp = nyp;
             hprev = h; tprev = tau; pcur = pn;
+            h = hn; ih = ihn; pn = pnn;
         }
         // last interior node's values: M_L = y'_L - I_{j-1} g'_L - I_j c'_L
         yL = yp; gL = gp; kL = cp;
         // interface node e_j
-        const double h = D[ej];
-        U[ej] = S;
+        Ur[ej] = S;
         const int en = (ej + 1 == n) ? 0 : ej + 1;
-        const double2 tau = scl2(sub2(__ldg(p + en), pcur), IH[ej]);
-        Re = scl2(sub2(tau, tprev), L6sq);
+        const double2 tau = scl2(sub2(__ldg(p + en), pcur), IHr[ej]);
+        Re = sub2(tau, tprev);
         Ae = hprev;
-        Ce = h;
-        Be = 2.0 * (hprev + h);
+        Ce = Dr[ej];
+        Be = 2.0 * (hprev + Ce);
     }
 
     // ---- C: backward sweep (no stores) for the first interior node ----------
@@ -319,7 +330,6 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
     const bool pow2 = (Nout & (Nout - 1)) == 0;
     const double invN = 1.0 / (double)Nout;
     const double LN = L * invN;                  // arc length per output step
-    const double c6 = 1.0 / L6sq;                // h^2/6 = d^2 / (6 L^2)
     const int per = (Nout + 31) / 32;
     const int k0 = lane * per;
     const int k1 = min(k0 + per, Nout);
@@ -349,7 +359,7 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
             const double d = D[l];
             const double b = (st - U[l]) * IH[l];  // (t - u_l) / h_l
             const double a = 1.0 - b;
-            const double h6 = d * d * c6;
+            const double h6 = d * d;  // h^2 M / 6 = d^2 M' (M' = M / (6 L^2))
             const double ca = a * fma(a, a, -1.0) * h6;
             const double cb = b * fma(b, b, -1.0) * h6;
             const double2 S = d2(fma(ca, Ml.x, fma(cb, Mn.x, fma(b, pn.x - pl.x, pl.x))),
