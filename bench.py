@@ -630,7 +630,7 @@ def main():
     ap.add_argument("--ragged-pairs", type=int, default=100_000)
     ap.add_argument("--no-elastic", action="store_true")
     ap.add_argument("--no-knn", action="store_true")
-    ap.add_argument("--knn-exact-queries", type=int, default=16)
+    ap.add_argument("--knn-exact-queries", type=int, default=32)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()
