@@ -440,7 +440,8 @@ int oracle_max_threads(void)
 /*      (a) a dynamic programme over lattice paths from (0,0) to (N,N)      */
 /*          with steps (a,b), 1 <= a,b <= 3, gcd(a,b) = 1 (slopes b/a in    */
 /*          [1/3, 3]), optionally kept in the band |i - j| <= B, minimising */
-/*          E exactly over those paths; run on the first iteration only     */
+/*          E over those paths (its sums in float32: it only picks the      */
+/*          starting path); run on the first iteration only                 */
 /*          (later the refined gamma carries over: a new shift s from the   */
 /*          (t0,R)-step keeps gamma and lowers E, and the refinement's free  */
 /*          offset g_0 follows it);                                         */
@@ -532,32 +533,43 @@ static double el_energy(const double* q1s, const double* q2, int N, const double
     return E / (double)N;
 }
 
-/* (a) lattice-path dynamic programme; the minimising path's node values   */
-/* are written to g[0..N] and its energy is returned                        */
+/* (a) lattice-path dynamic programme.  Its path costs are accumulated in   */
+/* float32: the DP only chooses the refinement's starting path, and every   */
+/* reported value is FP64.  Each cell's term is fmaf(dx, dx, fmaf(dy, dy,   */
+/* acc)) with dx = fmaf(-m, v_x, u_x), m = sqrt(b/a) rounded to float, and   */
+/* the inputs q1s and q2(M) rounded from FP64 to float: the same operations  */
+/* in the same order as the library's kernel, so that both choose the same  */
+/* path.  The minimising path's node values are written to g[0..N]; its     */
+/* FP64 energy is returned.                                                 */
 static double el_dp(const double* q1s, const double* q2, int N, int band, double* g)
 {
     const int M = N + 1;
-    double* V = (double*)malloc(sizeof(double) * (size_t)M * M);
+    float* V = (float*)malloc(sizeof(float) * (size_t)M * M);
     signed char* arg = (signed char*)malloc((size_t)M * M);
     for (int x = 0; x < M * M; ++x) { V[x] = INFINITY; arg[x] = -1; }
-    V[0] = 0.0;
+    V[0] = 0.0f;
     for (int i = 1; i <= N; ++i)
         for (int j = 1; j <= N; ++j) {
             if (band >= 0 && abs(i - j) > band) continue;
-            double best = INFINITY;
+            float best = INFINITY;
             int bi = -1;
             for (int st = 0; st < EL_NSTEPS; ++st) {
                 const int a = EL_STEP[st][0], b = EL_STEP[st][1];
                 if (i - a < 0 || j - b < 0) continue;
-                const double prev = V[(i - a) * M + (j - b)];
+                const float prev = V[(i - a) * M + (j - b)];
                 if (prev == INFINITY) continue;
-                double c = 0.0;
+                const float m = (float)sqrt((double)b / (double)a);
+                float acc = 0.0f;
                 for (int p = 0; p < a; ++p) {
                     const double x = (double)(j - b) + (double)(p * b) / (double)a;
                     const double y = (double)(j - b) + (double)((p + 1) * b) / (double)a;
-                    c += el_term(q1s, q2, N, i - a + p, x, y);
+                    double v[2];
+                    el_interp(q2, N, 0.5 * (x + y), v, NULL);
+                    const float ux = (float)q1s[2 * (i - a + p)], uy = (float)q1s[2 * (i - a + p) + 1];
+                    const float dx = fmaf(-m, (float)v[0], ux), dy = fmaf(-m, (float)v[1], uy);
+                    acc = fmaf(dx, dx, fmaf(dy, dy, acc));
                 }
-                c = prev + c / (double)N;
+                const float c = prev + acc;
                 if (c < best) { best = c; bi = st; }
             }
             V[i * M + j] = best;
@@ -571,9 +583,8 @@ static double el_dp(const double* q1s, const double* q2, int N, int band, double
         i -= a;
         j -= b;
     }
-    const double E = V[N * M + N];
     free(V); free(arg);
-    return E;
+    return el_energy(q1s, q2, N, g);
 }
 
 /* q1s_k = e^{i theta} q1[(k + s) mod N]  (the motion R q1(t + t0))        */

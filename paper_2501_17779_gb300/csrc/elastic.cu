@@ -211,48 +211,34 @@ __device__ __forceinline__ double2 rot(double2 c, double2 u)
     return make_double2(c.x * u.x - c.y * u.y, c.y * u.x + c.x * u.y);
 }
 
-// E(g, theta) * N for the shift s
-template <int T>
-__device__ double energy_n(const double2* q1, const double2* q2, int N, int s, double2 cs,
-                           const double* g, double* red)
-{
-    double acc[1] = {0.0};
-    for (int k = threadIdx.x; k < N; k += T) {
-        double2 v;
-        cr_eval(q2, N, 0.5 * (g[k] + g[k + 1]), v, nullptr);
-        const double D = g[k + 1] - g[k];
-        const double m = D * rsqrt_fast(D);
-        const double2 u = rot(cs, q1[(k + s) & (N - 1)]);
-        const double dx = fma(-m, v.x, u.x), dy = fma(-m, v.y, u.y);
-        acc[0] = fma(dx, dx, fma(dy, dy, acc[0]));
-    }
-    cta_sums<T, 1>(acc, red);
-    return acc[0];
-}
-
 // ----------------------------------------------------- dynamic programme ----
+// The path costs are accumulated in float32 (the DP only chooses the
+// refinement's starting path; every reported value is FP64): each cell's term
+// is fmaf(dx, dx, fmaf(dy, dy, acc)) with dx = fmaf(-m, v_x, u_x), m = sqrt(b/a)
+// rounded to float, and q1s, q2(M) rounded from FP64 -- the oracle performs the
+// same operations in the same order.
 template <int ST>
-__device__ __forceinline__ void dp_steps(int i, int j, const double* __restrict__ V,
-                                         int ring_stride, const double2* __restrict__ q1s,
-                                         const double2* __restrict__ q2f, int fstride,
-                                         double& best, int& arg)
+__device__ __forceinline__ void dp_steps(int i, int j, const float* __restrict__ V,
+                                         int ring_stride, const float2* __restrict__ q1s,
+                                         const float2* __restrict__ q2f, int fstride,
+                                         float& best, int& arg)
 {
     if constexpr (ST < kNSteps) {
         constexpr int a = step_a(ST), b = step_b(ST);
         if (i >= a && j >= b) {
-            const double prev = V[((i - a) & 3) * ring_stride + (j - b)];
-            constexpr double m = step_m(ST);
-            double acc = 0.0;
+            const float prev = V[((i - a) & 3) * ring_stride + (j - b)];
+            constexpr float m = (float)step_m(ST);
+            float acc = 0.0f;
 #pragma unroll
             for (int p = 0; p < a; ++p) {
-                const double2 u = q1s[i - a + p];
+                const float2 u = q1s[i - a + p];
                 // q2f rows hold samples -1 .. N; entry x sits at index x + 1
-                const double2 v = q2f[frac_index(piece_tw(ST, p)) * fstride +
-                                      (j - b + piece_jo(ST, p) + 1)];
-                const double dx = fma(-m, v.x, u.x), dy = fma(-m, v.y, u.y);
-                acc = fma(dx, dx, fma(dy, dy, acc));
+                const float2 v = q2f[frac_index(piece_tw(ST, p)) * fstride +
+                                     (j - b + piece_jo(ST, p) + 1)];
+                const float dx = fmaf(-m, v.x, u.x), dy = fmaf(-m, v.y, u.y);
+                acc = fmaf(dx, dx, fmaf(dy, dy, acc));
             }
-            const double c = prev + acc;
+            const float c = prev + acc;
             if (c < best) { best = c; arg = ST; }
         }
         dp_steps<ST + 1>(i, j, V, ring_stride, q1s, q2f, fstride, best, arg);
@@ -261,20 +247,20 @@ __device__ __forceinline__ void dp_steps(int i, int j, const double* __restrict_
 
 // node values g of the minimising lattice path for q1s (shared), q2f prepared
 template <int T>
-__device__ void elastic_dp(int N, int B, const double2* q1s, const double2* q2f, double* V,
+__device__ void elastic_dp(int N, int B, const float2* q1s, const float2* q2f, float* V,
                            uint8_t* bp, double* g)
 {
     const int tid = threadIdx.x;
     const int rs = N + 1;
     const int W = B < N ? 2 * B + 1 : N;
-    for (int x = tid; x <= N; x += T) V[x] = x == 0 ? 0.0 : HUGE_VAL;
+    for (int x = tid; x <= N; x += T) V[x] = x == 0 ? 0.0f : HUGE_VALF;
     __syncthreads();
     for (int i = 1; i <= N; ++i) {
         const int jlo = max(1, i - B), jhi = min(N, i + B);
         const int base = B < N ? i - B : 1;
-        double* Vi = V + (i & 3) * rs;
+        float* Vi = V + (i & 3) * rs;
         for (int j = tid; j <= N; j += T) {
-            double best = HUGE_VAL;
+            float best = HUGE_VALF;
             if (j >= jlo && j <= jhi) {
                 int arg = 255;
                 dp_steps<0>(i, j, V, rs, q1s, q2f, rs + 1, best, arg);
@@ -304,16 +290,17 @@ __device__ void elastic_dp(int N, int B, const double2* q1s, const double2* q2f,
     __syncthreads();
 }
 
-// q2f[f][x + 1] = q2(x + 1/2 + frac_f) for x = -1 .. N (Catmull-Rom)
+// q2f[f][x + 1] = q2(x + 1/2 + frac_f) for x = -1 .. N (Catmull-Rom, FP64,
+// rounded to float)
 template <int T>
-__device__ void build_q2f(const double2* q2, int N, double2* q2f)
+__device__ void build_q2f(const double2* q2, int N, float2* q2f)
 {
     const int rs = N + 2;
     for (int e = threadIdx.x; e < kNFrac * rs; e += T) {
         const int f = e / rs, x = e - f * rs - 1;
         double2 v;
         cr_eval(q2, N, (double)x + 0.5 + (double)frac_tw(f) / 12.0, v, nullptr);
-        q2f[e] = v;
+        q2f[e] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
     }
     __syncthreads();
 }
@@ -385,75 +372,96 @@ __device__ void pcr3(int n, double* lo, double* di, double* up, double* x, doubl
     __syncthreads();
 }
 
-struct LmArrays {
-    double2 *R, *A, *Bv;
-    double *Cc, *Cp;
+struct CellBuf {
+    double2 *R, *A, *Bv;       // r_k, d r_k / d g_k, d r_k / d g_{k+1}
     double *Saa, *Sbb, *Sab;   // <r_k, second derivatives of r_k> (full Newton terms)
+};
+
+struct LmArrays {
+    double *Cc, *Cp;
     double *di, *xv, *lo, *up, *yc, *yp, *inv;
 };
 
-// Levenberg-Marquardt refinement of (g, theta) for the shift s; returns N E
+// One pass over the cells at node values g and rotation cs: residuals, their
+// first and second derivatives into buf, and the CTA sums
+//   h[0..2] = Hcc, Hcp, Hpp (Gauss-Newton border), h[3..4] = Gc, Gp (gradient),
+//   h[5..6] = Scc, Spp (second-order border terms), h[7] = N E (the energy).
+template <int T>
+__device__ __forceinline__ void cell_pass(const double2* q1, const double2* q2, int N, int s,
+                                          double2 cs, const double* g, const CellBuf& buf,
+                                          double (&h)[8], double* red)
+{
+#pragma unroll
+    for (int c = 0; c < 8; ++c) h[c] = 0.0;
+    for (int k = threadIdx.x; k < N; k += T) {
+        double2 v, dv, ddv;
+        cr_eval(q2, N, 0.5 * (g[k] + g[k + 1]), v, &dv, &ddv);
+        const double D = g[k + 1] - g[k];
+        const double rs = rsqrt_fast(D);
+        const double m = D * rs;
+        const double hm = 0.5 * rs;
+        const double2 u = rot(cs, q1[(k + s) & (N - 1)]);
+        const double2 r = make_double2(fma(-m, v.x, u.x), fma(-m, v.y, u.y));
+        // r = u - sqrt(D) q2(M): r_D = -q2/(2 sqrt D), r_M = -sqrt(D) q2',
+        // r_DD = q2/(4 D^{3/2}), r_DM = -q2'/(2 sqrt D), r_MM = -sqrt(D) q2'';
+        // d/dg_k = -d/dD + d/dM / 2, d/dg_{k+1} = d/dD + d/dM / 2
+        const double2 rD = make_double2(-v.x * hm, -v.y * hm);
+        const double2 rM = make_double2(-m * dv.x, -m * dv.y);
+        const double q4 = 0.5 * hm * rs * rs;  // 1 / (4 D^{3/2})
+        const double2 rDD = make_double2(v.x * q4, v.y * q4);
+        const double2 rDM = make_double2(-dv.x * hm, -dv.y * hm);
+        const double2 rMM = make_double2(-m * ddv.x, -m * ddv.y);
+        const double2 a = make_double2(fma(0.5, rM.x, -rD.x), fma(0.5, rM.y, -rD.y));
+        const double2 b = make_double2(fma(0.5, rM.x, rD.x), fma(0.5, rM.y, rD.y));
+        const double pDD = r.x * rDD.x + r.y * rDD.y, pDM = r.x * rDM.x + r.y * rDM.y;
+        const double pMM = 0.25 * (r.x * rMM.x + r.y * rMM.y);
+        buf.R[k] = r;
+        buf.A[k] = a;
+        buf.Bv[k] = b;
+        buf.Saa[k] = pDD - pDM + pMM;
+        buf.Sbb[k] = pDD + pDM + pMM;
+        buf.Sab[k] = pMM - pDD;
+        const double ux = a.x + b.x, uy = a.y + b.y;
+        const double px = -u.y, py = u.x;
+        h[0] = fma(ux, ux, fma(uy, uy, h[0]));
+        h[1] = fma(ux, px, fma(uy, py, h[1]));
+        h[2] = fma(px, px, fma(py, py, h[2]));
+        h[3] = fma(r.x, ux, fma(r.y, uy, h[3]));
+        h[4] = fma(r.x, px, fma(r.y, py, h[4]));
+        h[5] += 4.0 * pMM;                      // <r, r_MM>: c moves M only
+        h[6] -= r.x * u.x + r.y * u.y;          // d2r/dphi2 = -u
+        h[7] = fma(r.x, r.x, fma(r.y, r.y, h[7]));
+    }
+    cta_sums<T, 8>(h, red);  // includes the barrier that publishes buf
+}
+
+// Levenberg-Marquardt refinement of (g, theta) for the shift s; returns N E.
+// The trial point's cell pass also serves as the next step's when the step is
+// accepted (two buffers, swapped), so each step costs one pass over the cells.
 template <int T, int NMAX>
 __device__ double elastic_refine(const double2* q1, const double2* q2, int N, int s,
-                                 double& theta, double* g, double* gt, const LmArrays& L,
-                                 double* red)
+                                 double& theta, double* g0, double* gt0, CellBuf cur,
+                                 CellBuf alt, const LmArrays& L, double* red)
 {
     const int tid = threadIdx.x;
     const int n = N - 1;
-    double* bc = red + (T / 32 + 1) * 8 - 2;  // broadcast slot (the reductions use fewer)
+    double* g = g0;
+    double* gt = gt0;
+    double* bc = red + (T / 32 + 2) * 8 - 2;  // broadcast slot (the reductions use fewer)
     if (tid == 0) sincos(theta, &bc[1], &bc[0]);
     __syncthreads();
     double2 cs = make_double2(bc[0], bc[1]);
-    double En = energy_n<T>(q1, q2, N, s, cs, g, red);
+    double h[8];
+    cell_pass<T>(q1, q2, N, s, cs, g, cur, h, red);
+    double En = h[7];
     double lambda = 1e-3;
     for (int it = 0; it < kLmIters; ++it) {
-        // Hcc, Hcp, Hpp, Gc, Gp (Gauss-Newton parts), Scc, Spp (second-order parts)
-        double h[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int k = tid; k < N; k += T) {
-            double2 v, dv, ddv;
-            cr_eval(q2, N, 0.5 * (g[k] + g[k + 1]), v, &dv, &ddv);
-            const double D = g[k + 1] - g[k];
-            const double rs = rsqrt_fast(D);
-            const double m = D * rs;
-            const double hm = 0.5 * rs;
-            const double2 u = rot(cs, q1[(k + s) & (N - 1)]);
-            const double2 r = make_double2(fma(-m, v.x, u.x), fma(-m, v.y, u.y));
-            // r = u - sqrt(D) q2(M): r_D = -q2/(2 sqrt D), r_M = -sqrt(D) q2',
-            // r_DD = q2/(4 D^{3/2}), r_DM = -q2'/(2 sqrt D), r_MM = -sqrt(D) q2'';
-            // d/dg_k = -d/dD + d/dM / 2, d/dg_{k+1} = d/dD + d/dM / 2
-            const double2 rD = make_double2(-v.x * hm, -v.y * hm);
-            const double2 rM = make_double2(-m * dv.x, -m * dv.y);
-            const double q4 = 0.5 * hm * rs * rs;  // 1 / (4 D^{3/2})
-            const double2 rDD = make_double2(v.x * q4, v.y * q4);
-            const double2 rDM = make_double2(-dv.x * hm, -dv.y * hm);
-            const double2 rMM = make_double2(-m * ddv.x, -m * ddv.y);
-            const double2 a = make_double2(fma(0.5, rM.x, -rD.x), fma(0.5, rM.y, -rD.y));
-            const double2 b = make_double2(fma(0.5, rM.x, rD.x), fma(0.5, rM.y, rD.y));
-            const double pDD = r.x * rDD.x + r.y * rDD.y, pDM = r.x * rDM.x + r.y * rDM.y;
-            const double pMM = 0.25 * (r.x * rMM.x + r.y * rMM.y);
-            L.R[k] = r;
-            L.A[k] = a;
-            L.Bv[k] = b;
-            L.Saa[k] = pDD - pDM + pMM;
-            L.Sbb[k] = pDD + pDM + pMM;
-            L.Sab[k] = pMM - pDD;
-            const double ux = a.x + b.x, uy = a.y + b.y;
-            const double px = -u.y, py = u.x;
-            h[0] = fma(ux, ux, fma(uy, uy, h[0]));
-            h[1] = fma(ux, px, fma(uy, py, h[1]));
-            h[2] = fma(px, px, fma(py, py, h[2]));
-            h[3] = fma(r.x, ux, fma(r.y, uy, h[3]));
-            h[4] = fma(r.x, px, fma(r.y, py, h[4]));
-            h[5] += 4.0 * pMM;                      // <r, r_MM>: c moves M only
-            h[6] -= r.x * u.x + r.y * u.y;          // d2r/dphi2 = -u
-        }
-        cta_sums<T, 7>(h, red);  // includes the barrier that publishes R, A, Bv, S..
         for (int i = 1 + tid; i <= n; i += T) {
-            const double2 b0 = L.Bv[i - 1], a0 = L.A[i - 1], a1 = L.A[i], b1 = L.Bv[i];
-            const double2 r0 = L.R[i - 1], r1 = L.R[i];
+            const double2 b0 = cur.Bv[i - 1], a0 = cur.A[i - 1], a1 = cur.A[i], b1 = cur.Bv[i];
+            const double2 r0 = cur.R[i - 1], r1 = cur.R[i];
             const double2 p0 = rot(cs, q1[(i - 1 + s) & (N - 1)]);
             const double2 p1 = rot(cs, q1[(i + s) & (N - 1)]);
-            const double sbb0 = L.Sbb[i - 1], sab0 = L.Sab[i - 1], saa1 = L.Saa[i], sab1 = L.Sab[i];
+            const double sbb0 = cur.Sbb[i - 1], sab0 = cur.Sab[i - 1], saa1 = cur.Saa[i], sab1 = cur.Sab[i];
             L.di[i] = (b0.x * b0.x + b0.y * b0.y + a1.x * a1.x + a1.y * a1.y) * (1.0 + lambda) +
                       sbb0 + saa1;
             L.xv[i] = -(r0.x * b0.x + r0.y * b0.y + r1.x * a1.x + r1.y * a1.y);
@@ -503,10 +511,15 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
         if (tid == 0) sincos(tht, &bc[1], &bc[0]);
         __syncthreads();
         const double2 ct = make_double2(bc[0], bc[1]);
-        const double Et = energy_n<T>(q1, q2, N, s, ct, gt, red);
+        double ht[8];
+        cell_pass<T>(q1, q2, N, s, ct, gt, alt, ht, red);
+        const double Et = ht[7];
         bool stop;
         if (Et < En) {
-            for (int k = tid; k <= N; k += T) g[k] = gt[k];
+            double* tg = g; g = gt; gt = tg;
+            const CellBuf tb = cur; cur = alt; alt = tb;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) h[c] = ht[c];
             theta = tht;
             cs = ct;
             stop = En - Et <= kLmTol * En;
@@ -516,8 +529,11 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
             lambda *= 8.0;
             stop = lambda > kLmStall;
         }
-        __syncthreads();
         if (stop) break;
+    }
+    if (g != g0) {
+        for (int k = tid; k <= N; k += T) g0[k] = g[k];
+        __syncthreads();
     }
     return En;
 }
@@ -570,8 +586,8 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
     double* g = reinterpret_cast<double*>(q1s + N);
     double* gt = g + (N + 1);
     double* ar = gt + (N + 1);                 // 12 (N+1): solver arrays / DP ring
-    double* red = ar + 12 * (N + 1);           // (T/32 + 1) * 8
-    long long* sk = reinterpret_cast<long long*>(red + (T / 32 + 1) * 8);
+    double* red = ar + 12 * (N + 1);           // (T/32 + 2) * 8
+    long long* sk = reinterpret_cast<long long*>(red + (T / 32 + 2) * 8);
     int* si = reinterpret_cast<int*>(sk + T / 32);
     int* ib = si + T / 32;                     // [4] broadcast ints
     unsigned char* tail = reinterpret_cast<unsigned char*>(ib + 4);
@@ -586,12 +602,21 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
     }
     bp = a.bp_smem ? reinterpret_cast<uint8_t*>(tail) : a.bp_ws + (int64_t)blockIdx.x * a.bp_bytes;
     LmArrays L;
-    L.R = X; L.A = Y; L.Bv = q1s;
     L.Cc = ar; L.Cp = ar + (N + 1);
     L.di = ar + 2 * (N + 1); L.xv = ar + 3 * (N + 1); L.lo = ar + 4 * (N + 1);
     L.up = ar + 5 * (N + 1); L.yc = ar + 6 * (N + 1); L.yp = ar + 7 * (N + 1);
-    L.Saa = ar + 8 * (N + 1); L.Sbb = ar + 9 * (N + 1); L.Sab = ar + 10 * (N + 1);
     L.inv = ar + 11 * (N + 1);
+    // the refinement's two cell buffers: one in the transform buffers, the other
+    // in the Catmull-Rom table's space (9N doubles of its 16(N+2)), which the
+    // lattice DP no longer needs once it has run
+    CellBuf cb0, cb1;
+    cb0.R = X; cb0.A = Y; cb0.Bv = q1s;
+    cb0.Saa = ar + 8 * (N + 1); cb0.Sbb = ar + 9 * (N + 1); cb0.Sab = ar + 10 * (N + 1);
+    cb1.R = q2f; cb1.A = q2f + N; cb1.Bv = q2f + 2 * N;
+    {
+        double* d = reinterpret_cast<double*>(q2f + 3 * N);
+        cb1.Saa = d; cb1.Sbb = d + N; cb1.Sab = d + 2 * N;
+    }
     const double nanv = __longlong_as_double(0x7ff8000000000000LL);
 
     // pairs are taken from a global counter (iteration counts differ between
@@ -637,7 +662,7 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
             Q1[k] = q1[k];
         }
         __syncthreads();
-        build_q2f<T>(q2, N, q2f);
+        build_q2f<T>(q2, N, reinterpret_cast<float2*>(q2f));
         fft_rt<T, NMAX>(Y, a.logn, a.tf);
         for (int k = tid; k < N; k += T) q1s[k] = zr2[k];  // the direct c(s*) reads it
         __syncthreads();
@@ -670,11 +695,16 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
             if (it == 1) {
                 double2 cs;
                 sincos(theta, &cs.y, &cs.x);
-                for (int k = tid; k < N; k += T) q1s[k] = rot(cs, q1[(k + s) & (N - 1)]);
+                float2* q1f = reinterpret_cast<float2*>(q1s);
+                for (int k = tid; k < N; k += T) {
+                    const double2 u = rot(cs, q1[(k + s) & (N - 1)]);
+                    q1f[k] = make_float2(__double2float_rn(u.x), __double2float_rn(u.y));
+                }
                 __syncthreads();
-                elastic_dp<T>(N, B, q1s, q2f, ar, bp, g);
+                elastic_dp<T>(N, B, q1f, reinterpret_cast<const float2*>(q2f),
+                              reinterpret_cast<float*>(ar), bp, g);
             }
-            elastic_refine<T, NMAX>(q1, q2, N, s, theta, g, gt, L, red);
+            elastic_refine<T, NMAX>(q1, q2, N, s, theta, g, gt, cb0, cb1, L, red);
             // (t0, R)-step on w_k = sqrt(D_k) q2(M_k)
             for (int k = tid; k < N; k += T) {
                 double2 v;
@@ -796,7 +826,7 @@ ElLayout el_layout(const fa_handle* h, int64_t Mtot, int64_t P, int N, int band)
     L.q2f_elems = (int64_t)kNFrac * (N + 2);
     L.bp_bytes = (int64_t)N * W;
     size_t fixed = 6 * (size_t)N * sizeof(double2) + 14 * (size_t)(N + 1) * sizeof(double) +
-                   (kElT / 32 + 1) * 8 * sizeof(double) + (kElT / 32) * (sizeof(long long) + sizeof(int)) +
+                   (kElT / 32 + 2) * 8 * sizeof(double) + (kElT / 32) * (sizeof(long long) + sizeof(int)) +
                    4 * sizeof(int) + 16;
     size_t sm = fixed;
     L.q2f_smem = sm + L.q2f_elems * sizeof(double2) <= kSmemBudget;
