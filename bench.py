@@ -41,8 +41,8 @@ N_MIN, N_MAX = 500, 2000
 SEED = 1002
 # DRAM bytes per launch of the bench workload's kernels, from one ncu capture of the
 # current kernel versions (profiles/*_4096pairs_n1024.md); update when a kernel changes
-DRAM_TRAFFIC_PER_LAUNCH = {"resample_kernel": 1.971814e9 + 1.082025e9,
-                           "align_fft_kernel": 1.35009e8 + 6.549e6}
+DRAM_TRAFFIC_PER_LAUNCH = {"resample_kernel": 1.963065e9 + 1.066591e9,
+                           "align_fft_kernel": 1.34767e8 + 6.174e6}
 METRIC = "aligned curve pairs/s at N=1024 (FFT vs direct O(N²), 1 GB300); roofline fraction"
 WORKLOAD = ("4096 pairs of raw curves (N_in ~ U{500..2000}, +-40% node jitter, <=16 harmonics), "
             "GPU arc-length resampling to N=1024 + FFT alignment over all shifts, FP64")
