@@ -329,9 +329,9 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     direct_ms = e0.elapsed_time(e1) / reps
 
-    # FA_PREC_MIXED variant of the alignment step on the same curves (FP32
-    # transforms, FP64 re-score of the shifts FP32 cannot rule out, FP64
-    # theta/energy); also checks it picks the FP64 search's shifts
+    # FA_PREC_MIXED variant of the alignment step on the same curves (the three
+    # transforms in double-float, c(s*), theta and the energy in FP64); also
+    # checks it picks the FP64 search's shifts
     with torch.cuda.stream(stream):
         align()
         ref_shift = shift.clone()
@@ -346,6 +346,48 @@ def run_gpu(args):
     same = shift == ref_shift
     mixed_agree = float(same.double().mean().item())
     mixed_tie_ok = bool(((energy - ref_energy).abs()[~same] <= 1e-9).all().item())
+    ref_theta = None
+    with torch.cuda.stream(stream):
+        align()
+        ref_theta = theta.clone()
+    torch.cuda.synchronize(dev)
+
+    # FP32-storage variant of the whole step: resampled nodes stored as
+    # complex64 (FA_STORE_FP32), aligned in FP64 from them (FA_Z_F32); errors
+    # against the FP64-storage results of the same curves
+    z32 = torch.empty((C, N), dtype=torch.complex64, device=dev)
+    ws32_bytes = int(L.fa_resample_workspace_size(C, n_pts, N, flags | _lib.STORE_FP32))
+    ws32 = torch.empty(ws32_bytes, dtype=torch.uint8, device=dev)
+    sh32 = torch.empty(P, dtype=torch.int32, device=dev)
+    th32 = torch.empty(P, dtype=torch.float64, device=dev)
+    en32 = torch.empty(P, dtype=torch.float64, device=dev)
+    st32 = torch.empty(P, dtype=torch.int8, device=dev)
+
+    def step32():
+        _lib.check(L.fa_resample_arclength(h, pts.data_ptr(), offs.data_ptr(), C, n_pts, N,
+                                           flags | _lib.STORE_FP32, z32.data_ptr(), rst.data_ptr(),
+                                           ws32.data_ptr(), ws32_bytes, sptr))
+        _lib.check(L.fa_align_pairs(h, z32.data_ptr(), z32.data_ptr() + P * N * 8, P, N,
+                                    _lib.Z_F32, _lib.FFT, _lib.PREC_FP64, sh32.data_ptr(),
+                                    th32.data_ptr(), en32.data_ptr(), st32.data_ptr(), sptr))
+
+    with torch.cuda.stream(stream):
+        step32()
+        e0.record(stream)
+        for _ in range(K):
+            step32()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    f32_ms = e0.elapsed_time(e1) / K
+    same32 = sh32 == ref_shift
+    dth32 = torch.remainder(th32 - ref_theta + np.pi, 2 * np.pi) - np.pi
+    fp32_storage = {
+        "ms_per_step": f32_ms, "pairs_per_s": world * P / (f32_ms * 1e-3),
+        "shift_agreement_with_fp64": float(same32.double().mean().item()),
+        "max_abs_dtheta_where_shift_agrees": float(dth32.abs()[same32].max().item()),
+        "max_rel_denergy": float(((en32 - ref_energy).abs() / ref_energy.abs()).max().item()),
+        "dtype": "f64 compute, complex64 resampled nodes"}
+    del z32, ws32
 
     # FP64 peak measured in this run (denominator of the roofline)
     peak_lib = ctypes.CDLL(str(pbuild.build_probe()))
@@ -572,10 +614,14 @@ def run_gpu(args):
             oracle.build()
             nthreads = os.cpu_count() or 1
             secs = oracle_sample(rp, args.cpu_pairs, N, nthreads)
+            n1 = min(128, args.cpu_pairs)
+            secs1 = oracle_sample(rp, n1, N, 1)
             cpu = {"value": args.cpu_pairs / secs, "unit": "pairs/s", "cores": nthreads,
                    "kind": "oracle", "sample": f"first {args.cpu_pairs} of the 4096 pairs "
                    "(resampling + O(N^2) Kabsch search), one pass, "
-                   f"{secs * nthreads:.1f} core-seconds"}
+                   f"{secs * nthreads:.1f} core-seconds",
+                   "single_core": {"value": n1 / secs1, "unit": "pairs/s", "cores": 1,
+                                   "sample": f"first {n1} pairs"}}
         line = {
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
@@ -595,7 +641,8 @@ def run_gpu(args):
                 "align_speedup_vs_fp64": al_avg / mixed_ms,
                 "align_speedup_vs_direct": direct_ms / mixed_ms,
                 "shift_agreement_with_fp64": mixed_agree, "disagreements_within_tie": mixed_tie_ok,
-                "dtype": "double-float (f32x2) search + f64 c(s*)/theta/energy"}},
+                "dtype": "double-float (f32x2) search + f64 c(s*)/theta/energy"},
+                "fp32_storage": fp32_storage},
             "all_pairs": allp,
             "ragged": rag,
             "elastic": ela,
