@@ -28,6 +28,8 @@
 //      perimeter of the resampled nodes.
 // Per-node intermediates live in a caller- or handle-provided workspace
 // (global memory, L1/L2 resident while a warp works on its curve).
+#include <algorithm>
+
 #include "fa_internal.cuh"
 
 namespace fa {
@@ -124,15 +126,14 @@ __device__ void fill_nan(void* zout, int64_t base, int Nout, int lane)
     for (int k = lane; k < Nout; k += 32) store_out<F32OUT>(zout, base + k, d2(q, q));
 }
 
+// one curve by one warp (every branch below is warp-uniform)
 template <bool F32OUT>
-__global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
-    resample_kernel(const double2* __restrict__ pts, const int64_t* __restrict__ offsets,
-                    int64_t C, int Nout, int flags, void* __restrict__ zout,
-                    int8_t* __restrict__ status, Ws ws)
+__device__ __forceinline__ void resample_curve(int64_t curve, int lane,
+                                               const double2* __restrict__ pts,
+                                               const int64_t* __restrict__ offsets, int Nout,
+                                               int flags, void* __restrict__ zout,
+                                               int8_t* __restrict__ status, const Ws& ws)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t curve = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    if (curve >= C) return;  // whole warp leaves together
     const int64_t o = offsets[curve];
     int n = (int)(offsets[curve + 1] - o);
     const double2* p = pts + o;
@@ -402,6 +403,26 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
     if (lane == 0) status[curve] = FA_STATUS_OK;
 }
 
+// Persistent grid: each warp takes the next curve from a counter until none is
+// left (curve sizes differ, so a fixed assignment would leave the last wave of
+// CTAs as a tail).
+template <bool F32OUT>
+__global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
+    resample_kernel(const double2* __restrict__ pts, const int64_t* __restrict__ offsets,
+                    int64_t C, int Nout, int flags, void* __restrict__ zout,
+                    int8_t* __restrict__ status, Ws ws, unsigned long long* __restrict__ next)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(next, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= (unsigned long long)C) break;
+        resample_curve<F32OUT>((int64_t)c, lane, pts, offsets, Nout, flags, zout, status, ws);
+        __syncwarp();
+    }
+}
+
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -411,14 +432,13 @@ size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags)
     const size_t np = (size_t)(n_pts > 0 ? n_pts : 0);
     size_t b = 3 * align256(np * sizeof(double)) + 3 * align256(np * sizeof(double2));
     if (flags & FA_STORE_FP32) b += align256((size_t)C * (size_t)N_out * sizeof(double2));
-    return b;
+    return b + 256;  // the work counter
 }
 
 int launch_resample(const fa_handle* h, const double* pts, const int64_t* offsets, int64_t C,
                     int64_t n_pts, int N_out, int flags, void* z_out, int8_t* status, void* wsp,
                     cudaStream_t st)
 {
-    (void)h;
     if (C == 0) return FA_OK;
     const size_t np = (size_t)(n_pts > 0 ? n_pts : 0);
     char* b = static_cast<char*>(wsp);
@@ -430,14 +450,26 @@ int launch_resample(const fa_handle* h, const double* pts, const int64_t* offset
     ws.F1 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.M = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.Z = (flags & FA_STORE_FP32) ? reinterpret_cast<double2*>(b) : nullptr;
-    const int64_t blocks = (C + kWarps - 1) / kWarps;
+    if (flags & FA_STORE_FP32) b += align256((size_t)C * (size_t)N_out * sizeof(double2));
+    unsigned long long* next = reinterpret_cast<unsigned long long*>(b);
+    int sms = h ? h->num_sms : 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 1;
+    }
+    const int64_t blocks = std::min<int64_t>((C + kWarps - 1) / kWarps,
+                                             (int64_t)sms * FA_RESAMPLE_MIN_BLOCKS);
     const double2* p = reinterpret_cast<const double2*>(pts);
+    const cudaError_t me = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+    if (me != cudaSuccess) return cuda_error(me, "resample counter reset");
     if (flags & FA_STORE_FP32)
         resample_kernel<true><<<(unsigned)blocks, kWarps * 32, 0, st>>>(p, offsets, C, N_out, flags,
-                                                                       z_out, status, ws);
+                                                                       z_out, status, ws, next);
     else
         resample_kernel<false><<<(unsigned)blocks, kWarps * 32, 0, st>>>(p, offsets, C, N_out,
-                                                                        flags, z_out, status, ws);
+                                                                        flags, z_out, status, ws, next);
     return cuda_error(cudaGetLastError(), "resample launch");
 }
 
