@@ -110,13 +110,15 @@ static int ensure_ws(fa_handle* h, size_t bytes)
 
 // A pair inherits the resampling status of its curves: a curve that could not
 // be resampled makes the pair's outputs NaN with that status.
-__global__ void merge_status_kernel(const int8_t* __restrict__ rst, int64_t P,
+// pairs p < count: curve statuses rst[p] and rst[p + second] (the pair's two
+// curves) override the alignment's outputs
+__global__ void merge_status_kernel(const int8_t* __restrict__ rst, int64_t count, int64_t second,
                                     int32_t* __restrict__ shift, double* __restrict__ theta,
                                     double* __restrict__ energy, int8_t* __restrict__ status)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    const int8_t s = rst[p] != FA_STATUS_OK ? rst[p] : rst[P + p];
+    if (p >= count) return;
+    const int8_t s = rst[p] != FA_STATUS_OK ? rst[p] : rst[second + p];
     if (s != FA_STATUS_OK) {
         shift[p] = -1;
         theta[p] = __longlong_as_double(0x7ff8000000000000LL);
@@ -171,6 +173,10 @@ int fa_destroy(fa_handle* h)
         if (h->tdf[L]) cudaFree(h->tdf[L]);
     }
     if (h->ws) cudaFree(h->ws);
+    for (int k = 0; k < 4; ++k)
+        if (h->pipe[k]) cudaStreamDestroy(h->pipe[k]);
+    for (int k = 0; k < 5; ++k)
+        if (h->pipe_ev[k]) cudaEventDestroy(h->pipe_ev[k]);
     delete h;
     return FA_OK;
 }
@@ -493,39 +499,85 @@ extern "C" int fa_align_curves_host(fa_handle* h, const double* pts, const int64
     const size_t b_th = a256((size_t)P * sizeof(double));
     const size_t b_st = a256((size_t)P);
     const size_t b_ws = a256(resample_ws_bytes(C, n_pts, N, rflags));
+    const size_t b_cnt = 256;  // the resampling launches' work counters
     if (N < 4 || N > (1 << 20))
         return set_error(FA_ERR_UNSUPPORTED, "fa_align_curves_host: N outside [4, 2^20]");
     DeviceGuard g(h->device);
     if (g.rc != FA_OK) return g.rc;
-    int rc = ensure_ws(h, b_off + b_pts + b_z + b_rst + b_sh + 2 * b_th + b_st + b_ws);
+    int rc = ensure_ws(h, b_off + b_pts + b_z + b_rst + b_sh + 2 * b_th + b_st + b_cnt + b_ws);
     if (rc != FA_OK) return rc;
     char* w = static_cast<char*>(h->ws);
     int64_t* d_off = reinterpret_cast<int64_t*>(w); w += b_off;
     double* d_pts = reinterpret_cast<double*>(w); w += b_pts;
-    void* d_z = w; w += b_z;
+    char* d_z = w; w += b_z;
     int8_t* d_rst = reinterpret_cast<int8_t*>(w); w += b_rst;
     int32_t* d_sh = reinterpret_cast<int32_t*>(w); w += b_sh;
     double* d_th = reinterpret_cast<double*>(w); w += b_th;
     double* d_en = reinterpret_cast<double*>(w); w += b_th;
     int8_t* d_st = reinterpret_cast<int8_t*>(w); w += b_st;
+    unsigned long long* d_cnt = reinterpret_cast<unsigned long long*>(w); w += b_cnt;
     void* d_ws = w;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // Pipeline: the pairs in up to four chunks, each on its own stream (upload
+    // of its curves, resampling, alignment, download), so that the copy engine
+    // uploads chunk k+1 while the SMs work on chunk k.  The chunks touch
+    // disjoint parts of every buffer, the resampling workspace included (it is
+    // addressed by absolute node index); each launch has its own counter.
+    const int nchunk = P >= 2048 ? 4 : (P >= 1024 ? 2 : 1);
+    if (nchunk > 1 && !h->pipe[0]) {
+        for (int k = 0; k < 4; ++k) {
+            cudaError_t e1 = cudaStreamCreateWithFlags(&h->pipe[k], cudaStreamNonBlocking);
+            if (e1 != cudaSuccess) return cuda_error(e1, "fa_align_curves_host: stream");
+        }
+        for (int k = 0; k < 5; ++k) {
+            cudaError_t e1 = cudaEventCreateWithFlags(&h->pipe_ev[k], cudaEventDisableTiming);
+            if (e1 != cudaSuccess) return cuda_error(e1, "fa_align_curves_host: event");
+        }
+    }
     cudaError_t e = cudaMemcpyAsync(d_off, offsets, (size_t)(C + 1) * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && n_pts > 0)
-        e = cudaMemcpyAsync(d_pts, pts, (size_t)n_pts * sizeof(double2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nchunk > 1) e = cudaEventRecord(h->pipe_ev[4], st);
     if (e != cudaSuccess) return cuda_error(e, "fa_align_curves_host: upload");
-    rc = fa_resample_arclength(h, d_pts, d_off, C, n_pts, N, rflags, d_z, d_rst, d_ws, b_ws, stream);
-    if (rc != FA_OK) return rc;
-    const char* z2 = static_cast<const char*>(d_z) + (size_t)P * (size_t)N * zb;
-    rc = fa_align_pairs(h, d_z, z2, P, N, ztype, method, prec, d_sh, d_th, d_en, d_st, stream);
-    if (rc != FA_OK) return rc;
-    merge_status_kernel<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(d_rst, P, d_sh, d_th, d_en, d_st);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(shift, d_sh, (size_t)P * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(theta, d_th, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(energy, d_en, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(status, d_st, (size_t)P, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const size_t zrow = (size_t)N * zb;
+    for (int k = 0; k < nchunk; ++k) {
+        const int64_t a = P * k / nchunk, b = P * (k + 1) / nchunk, m = b - a;
+        cudaStream_t cs = nchunk > 1 ? h->pipe[k] : st;
+        if (nchunk > 1) {
+            e = cudaStreamWaitEvent(cs, h->pipe_ev[4], 0);
+            if (e != cudaSuccess) return cuda_error(e, "fa_align_curves_host: wait");
+        }
+        // this chunk's curves: [a, b) and [P + a, P + b)
+        for (int half = 0; half < 2; ++half) {
+            const int64_t c0 = half * P + a, c1 = half * P + b;
+            const int64_t o0 = offsets[c0], o1 = offsets[c1];
+            if (o1 > o0) {
+                e = cudaMemcpyAsync(d_pts + 2 * o0, pts + 2 * o0, (size_t)(o1 - o0) * sizeof(double2),
+                                    cudaMemcpyHostToDevice, cs);
+                if (e != cudaSuccess) return cuda_error(e, "fa_align_curves_host: upload");
+            }
+            rc = launch_resample(h, d_pts, d_off + c0, m, n_pts, N, rflags, d_z + (size_t)c0 * zrow,
+                                 d_rst + c0, d_ws, cs, d_cnt + 2 * k + half, c0);
+            if (rc != FA_OK) return rc;
+        }
+        rc = fa_align_pairs(h, d_z + (size_t)a * zrow, d_z + (size_t)(P + a) * zrow, m, N, ztype,
+                            method, prec, d_sh + a, d_th + a, d_en + a, d_st + a, cs);
+        if (rc != FA_OK) return rc;
+        merge_status_kernel<<<(unsigned)((m + 255) / 256), 256, 0, cs>>>(
+            d_rst + a, m, P, d_sh + a, d_th + a, d_en + a, d_st + a);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(shift + a, d_sh + a, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(theta + a, d_th + a, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(energy + a, d_en + a, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(status + a, d_st + a, (size_t)m, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess && nchunk > 1) e = cudaEventRecord(h->pipe_ev[k], cs);
+        if (e == cudaSuccess && nchunk > 1) e = cudaStreamWaitEvent(st, h->pipe_ev[k], 0);
+        if (e != cudaSuccess) return cuda_error(e, "fa_align_curves_host");
+    }
+    e = cudaStreamSynchronize(st);
     return cuda_error(e, "fa_align_curves_host");
 }

@@ -24,6 +24,9 @@ struct fa_handle {
     // handle-owned scratch, used when the caller passes no workspace
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    // streams and events of the pipelined host entry point (created on first use)
+    cudaStream_t pipe[4] = {};
+    cudaEvent_t pipe_ev[5] = {};
 };
 
 namespace fa {
@@ -121,9 +124,14 @@ int launch_align_ragged(const fa_handle* h, const void* z1, const void* z2, cons
                         int64_t P, int max_n, int ztype, int threads, int32_t* shift,
                         double* theta, double* energy, int8_t* status, void* ws,
                         cudaStream_t st);
+// counter: the kernel's 8-byte work counter, or nullptr for the one at the end
+// of ws; stage_curve0: the first curve's row in ws's complex128 staging area
+// (FA_STORE_FP32).  Launches that share one workspace concurrently (disjoint
+// curves of one CSR array, offsets absolute) pass their own counter and row.
 int launch_resample(const fa_handle* h, const double* pts, const int64_t* offsets, int64_t C,
                     int64_t n_pts, int N_out, int flags, void* z_out, int8_t* status, void* ws,
-                    cudaStream_t st);
+                    cudaStream_t st, unsigned long long* counter = nullptr,
+                    int64_t stage_curve0 = 0);
 size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags);
 int build_twiddles(fa_handle* h);
 size_t elastic_ws_bytes(const fa_handle* h, int64_t M1, int64_t M2, int64_t P, int N, int band);

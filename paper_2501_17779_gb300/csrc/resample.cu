@@ -437,7 +437,7 @@ size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags)
 
 int launch_resample(const fa_handle* h, const double* pts, const int64_t* offsets, int64_t C,
                     int64_t n_pts, int N_out, int flags, void* z_out, int8_t* status, void* wsp,
-                    cudaStream_t st)
+                    cudaStream_t st, unsigned long long* counter, int64_t stage_curve0)
 {
     if (C == 0) return FA_OK;
     const size_t np = (size_t)(n_pts > 0 ? n_pts : 0);
@@ -449,9 +449,9 @@ int launch_resample(const fa_handle* h, const double* pts, const int64_t* offset
     ws.F0 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.F1 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.M = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
-    ws.Z = (flags & FA_STORE_FP32) ? reinterpret_cast<double2*>(b) : nullptr;
+    ws.Z = (flags & FA_STORE_FP32) ? reinterpret_cast<double2*>(b) + stage_curve0 * N_out : nullptr;
     if (flags & FA_STORE_FP32) b += align256((size_t)C * (size_t)N_out * sizeof(double2));
-    unsigned long long* next = reinterpret_cast<unsigned long long*>(b);
+    unsigned long long* next = counter ? counter : reinterpret_cast<unsigned long long*>(b);
     int sms = h ? h->num_sms : 0;
     if (sms <= 0) {
         int dev = 0;

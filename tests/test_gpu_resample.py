@@ -118,6 +118,28 @@ def test_host_pipeline_matches_device_path():
         np.testing.assert_array_equal(a.numpy(), b.cpu().numpy())
 
 
+def test_host_pipeline_chunks_match_device_path():
+    """2304 pairs run as four pipelined chunks (one stream each): identical to
+    resampling and aligning everything at once; a non-finite curve in the
+    third chunk's second half flags its pair only."""
+    P = 2304
+    rp = synth.raw_pairs(9, P=P, n_min=300, n_max=700)
+    bad = P + P // 2 + 5  # curve of pair P/2 + 5 (third chunk), second member
+    rp.pts[rp.offsets[bad] + 3] = np.nan
+    pts = torch.from_numpy(rp.pts).pin_memory()
+    offs = torch.from_numpy(rp.offsets).pin_memory()
+    hs = [x.numpy() for x in api.align_curves_host(pts, offs, 256)]
+    z, st = _gpu_resample(rp.pts, rp.offsets, 256)
+    t = torch.from_numpy(z).to(DEV)
+    ds = [x.cpu().numpy() for x in api.align_pairs(t[:P].contiguous(), t[P:].contiguous())]
+    ok = np.ones(P, bool)
+    ok[P // 2 + 5] = False
+    for a, b in zip(hs, ds):
+        np.testing.assert_array_equal(a[ok], b[ok])
+    assert hs[3][P // 2 + 5] == 2 and hs[0][P // 2 + 5] == -1 and np.isnan(hs[2][P // 2 + 5])
+    assert (hs[3][ok] == 0).all()
+
+
 def test_host_pipeline_fp32_storage_bounds():
     """complex64 storage between resampling and alignment: shift agreement
     >= 99.9% (beyond FP64 ties), |dtheta| <= 1e-5, relative dE <= 1e-5."""
