@@ -305,9 +305,12 @@ int fa_align_pairs_ragged_autotune(fa_handle* h, const void* z1, const void* z2,
  *   shift, theta, energy, status   HOST arrays of P entries; a pair whose
  *                 curve fails resampling gets that curve's status and NaNs
  *
- * Uses the handle's device buffer (grown with cudaMalloc when needed), so
- * calls sharing a handle must not run concurrently.  Returns after the
- * results are in the host arrays (the stream is synchronised).
+ * For P >= 1024 the pairs run in two or four chunks, each on one of the
+ * handle's own streams (upload of its curves, resampling, alignment,
+ * download), so that uploads overlap the kernels; the caller's stream waits
+ * for all of them.  Uses the handle's device buffer (grown with cudaMalloc
+ * when needed), so calls sharing a handle must not run concurrently.  Returns
+ * after the results are in the host arrays (the stream is synchronised).
  */
 int fa_align_curves_host(fa_handle* h, const double* pts, const int64_t* offsets, int64_t P,
                          int32_t N, int32_t flags, int32_t method, int32_t prec, int32_t* shift,
