@@ -189,8 +189,26 @@ def oracle_sample(rp, n_pairs: int, N: int, nthreads: int):
     pts = np.concatenate(curves)
     t0 = time.perf_counter()
     z, st = oracle.resample(pts, offs, N, nthreads=nthreads)
-    oracle.align_pairs(z[:n_pairs], z[n_pairs:], nthreads=nthreads)
-    return time.perf_counter() - t0
+    res = oracle.align_pairs(z[:n_pairs], z[n_pairs:], nthreads=nthreads)
+    return time.perf_counter() - t0, res
+
+
+def parity_vs_oracle(o, shift, theta, energy) -> dict:
+    """GPU results of the first pairs against the oracle's: shift agreement
+    (a different shift counts as a tie when its energy is within 1e-9 of the
+    oracle's optimum, the parity rule), the largest angle and relative energy
+    differences."""
+    n = o["shift"].size
+    s = shift[:n].cpu().numpy()
+    th = theta[:n].cpu().numpy()
+    e = energy[:n].cpu().numpy()
+    same = s == o["shift"]
+    tie = ~same & (np.abs(e - o["energy"]) <= 1e-9)
+    dth = np.abs(np.angle(np.exp(1j * (th - o["theta"]))))[same]
+    return {"pairs": int(n), "shift_agreement": float(same.mean()),
+            "shift_agreement_or_tie": float((same | tie).mean()),
+            "max_abs_dtheta": float(dth.max()) if dth.size else None,
+            "max_rel_denergy": float((np.abs(e - o["energy"]) / o["energy"]).max())}
 
 
 # ------------------------------------------------------------ reference ----
@@ -205,7 +223,7 @@ def run_reference(args):
     rp = make_workload(0, P=max(args.ref_pairs, 8))
     for _ in range(args.warmup):
         oracle_sample(rp, min(8, args.ref_pairs), N_NODES, nthreads)
-    times = [oracle_sample(rp, args.ref_pairs, N_NODES, nthreads) for _ in range(args.steps)]
+    times = [oracle_sample(rp, args.ref_pairs, N_NODES, nthreads)[0] for _ in range(args.steps)]
     tot = sum(times)
     value = args.ref_pairs * args.steps / tot
     line = {
@@ -343,6 +361,7 @@ def run_gpu(args):
         e1.record(stream)
     torch.cuda.synchronize(dev)
     mixed_ms = e0.elapsed_time(e1) / K
+    mix_res = (shift.clone(), theta.clone(), energy.clone())
     same = shift == ref_shift
     mixed_agree = float(same.double().mean().item())
     mixed_tie_ok = bool(((energy - ref_energy).abs()[~same] <= 1e-9).all().item())
@@ -613,15 +632,19 @@ def run_gpu(args):
 
             oracle.build()
             nthreads = os.cpu_count() or 1
-            secs = oracle_sample(rp, args.cpu_pairs, N, nthreads)
+            secs, ores = oracle_sample(rp, args.cpu_pairs, N, nthreads)
             n1 = min(128, args.cpu_pairs)
-            secs1 = oracle_sample(rp, n1, N, 1)
+            secs1, _ = oracle_sample(rp, n1, N, 1)
+            parity = {"fp64": parity_vs_oracle(ores, ref_shift, ref_theta, ref_energy),
+                      "mixed": parity_vs_oracle(ores, *mix_res),
+                      "fp32_storage": parity_vs_oracle(ores, sh32, th32, en32)}
             cpu = {"value": args.cpu_pairs / secs, "unit": "pairs/s", "cores": nthreads,
                    "kind": "oracle", "sample": f"first {args.cpu_pairs} of the 4096 pairs "
                    "(resampling + O(N^2) Kabsch search), one pass, "
                    f"{secs * nthreads:.1f} core-seconds",
                    "single_core": {"value": n1 / secs1, "unit": "pairs/s", "cores": 1,
-                                   "sample": f"first {n1} pairs"}}
+                                   "sample": f"first {n1} pairs"},
+                   "parity_of_gpu_results": parity}
         line = {
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,

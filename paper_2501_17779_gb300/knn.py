@@ -124,3 +124,24 @@ def recall_at_k(found: torch.Tensor, exact: torch.Tensor) -> float:
     f, x = found.cpu().numpy(), exact.cpu().numpy()
     k = x.shape[1]
     return float(np.mean([len(set(f[q]) & set(x[q])) / k for q in range(x.shape[0])]))
+
+
+def save_pruner(path, net: api.Mlp, stats: Descriptors) -> None:
+    """Save the pruning network's float32 parameters and the descriptor
+    statistics it was trained with (numpy .npz)."""
+    np.savez(path, params=net.get_params(), mean=stats.mean.cpu().numpy(),
+             inv_std=stats.inv_std.cpu().numpy(), n_freq=N_FREQ)
+
+
+def load_pruner(path, device: int | None = None):
+    """Load a network saved by ``save_pruner``: returns (net, stats) with
+    ``stats`` usable as the ``stats`` argument of ``descriptors``."""
+    d = np.load(path)
+    if int(d["n_freq"]) != N_FREQ:
+        raise ValueError("descriptor size differs from this library's")
+    net = api.Mlp(seed=0, device=device)
+    net.set_params(d["params"])
+    dev = net.device
+    stats = Descriptors(torch.empty((0, 2 * N_FREQ), dtype=torch.float32, device=dev),
+                        torch.from_numpy(d["mean"]).to(dev), torch.from_numpy(d["inv_std"]).to(dev))
+    return net, stats

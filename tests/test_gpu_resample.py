@@ -166,3 +166,37 @@ def test_full_size_resample_properties_and_sample():
     pts, offs = _csr(sub)
     zo, _ = oracle.resample(pts, offs, 1024)
     assert np.abs(z[idx] - zo).max() <= TOL
+
+
+def test_table1_error_trend_fast_equals_slow():
+    """Table 1: aligning a curve to its start-shifted, rotated copy after
+    resampling both, the FFT search (GPU) and the exhaustive search (oracle)
+    give the same shift and energy at every N, and the energy falls with N."""
+    import json
+    from pathlib import Path
+
+    gold = json.loads((Path(__file__).parent / "golden" / "table1_trend.json").read_text())
+    rng = np.random.default_rng(5)
+    h = synth.random_harmonics(rng, 8)
+    n = gold["n_raw"]
+    phi = 2 * np.pi * (np.arange(n) + rng.uniform(-0.4, 0.4, n)) / n
+    ref = h.radius(phi) * np.exp(1j * phi)
+    tmp = np.exp(1j * gold["rotation"]) * np.roll(ref, -gold["start_index"])
+    pts = np.concatenate([ref, tmp])
+    offs = np.array([0, n, 2 * n], np.int64)
+    E = []
+    for N in gold["N"]:
+        z, st = _gpu_resample(pts, offs, N)
+        t = torch.from_numpy(z).to(DEV)
+        s, th, e, ast = [x.cpu().numpy() for x in api.align_pairs(t[:1].contiguous(),
+                                                                  t[1:].contiguous())]
+        zo, _ = oracle.resample(pts, offs, N)
+        o = oracle.align_pairs(zo[:1], zo[1:])
+        assert s[0] == o["shift"][0] or o["gap"][0] < 1e-9
+        # the two sides resample separately (nodes within 1e-12), so the energies
+        # agree to that level, far below the trend
+        assert abs(e[0] - o["energy"][0]) <= 1e-7 * o["energy"][0] + 1e-16
+        E.append(o["energy"][0])
+    E = np.array(E)
+    assert (np.diff(E) <= 1e-15).all(), E
+    assert E[0] >= gold["min_drop_64_to_4096"] * E[-1], E
