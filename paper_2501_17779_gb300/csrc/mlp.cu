@@ -83,16 +83,13 @@ __global__ void __launch_bounds__(256) gemm_kernel(const __grid_constant__ GemmA
     const int64_t ke = kb + g.kc < g.K ? kb + g.kc : g.K;
     float acc[4][4] = {};
     for (int64_t k0 = kb; k0 < ke; k0 += BK) {
-        // consecutive threads walk the operand's unit-stride dimension
-        // (m for a transposed A, k otherwise; n for B unless k is unit-stride)
-        const bool a_m_fast = g.sam == 1, b_k_fast = g.sbk == 1 && g.sbn != 1;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int e = tid + r * 256;
-            const int mm = a_m_fast ? (e & 63) : (e >> 4), kk = a_m_fast ? (e >> 6) : (e & 15);
+            const int mm = e >> 4, kk = e & 15;
             const int64_t m = m0 + mm, k = k0 + kk;
             As[kk][mm] = (m < g.M && k < ke) ? to_f(g.A[m * g.sam + k * g.sak]) : 0.0f;
-            const int kk2 = b_k_fast ? (e & 15) : (e >> 6), nn = b_k_fast ? (e >> 4) : (e & 63);
+            const int kk2 = e >> 6, nn = e & 63;
             const int64_t k2 = k0 + kk2, n = n0 + nn;
             Bs[kk2][nn] = (k2 < ke && n < g.N) ? to_f(g.B[k2 * g.sbk + n * g.sbn]) : 0.0f;
         }
