@@ -23,7 +23,8 @@
 //      shuffles.
 //   D. a second backward sweep writes M for every node.
 //   E. the spline is evaluated at t_k = k/N_out (each lane a contiguous block
-//      of outputs; interval search by integer compares on the knots), then
+//      of outputs; interval search by integer compares on the knots; the
+//      chord vectors p_{l+1} - p_l of step A are kept for B and E), then
 //      the outputs are centred at their mean and divided by the closed-polygon
 //      perimeter of the resampled nodes.
 // Per-node intermediates live in a caller- or handle-provided workspace
@@ -37,16 +38,18 @@ namespace {
 
 constexpr int kWarps = 4;  // curves per CTA
 
-// Resident CTAs per SM requested from the compiler: 5 caps the kernel at 96
-// registers (no spills; 20 warps per SM instead of 12), measured 3 % faster.
+// Resident CTAs per SM requested from the compiler: 4 caps the kernel at 128
+// registers (no spills, 16 warps per SM); 5 (96 registers) spills a few words
+// and measured 1 % slower.
 #ifndef FA_RESAMPLE_MIN_BLOCKS
-#define FA_RESAMPLE_MIN_BLOCKS 5
+#define FA_RESAMPLE_MIN_BLOCKS 4
 #endif
 
 struct Ws {
     double* U;     // cumulative arc length S_l = L u_l [n_pts]
     double* D;     // chord lengths d_l                 [n_pts]
     double* IH;    // 1/d_l                             [n_pts]
+    double2* CV;   // chord vectors p_{l+1} - p_l       [n_pts]
     double2* F0;   // forward sweep (c'_l, g'_l)        [n_pts]
     double2* F1;   // forward sweep y'_l (x, y)         [n_pts]
     double2* M;    // spline second derivatives M_l     [n_pts]
@@ -88,6 +91,19 @@ __device__ __forceinline__ double rsqrt_nr(double q)
     const double y0 = widen_f32(y0f), h0 = widen_f32(0.5f * y0f);
     const double e = fma(-q * y0, y0, 1.0);  // 1 - q y0^2
     return fma(h0, e, y0);
+}
+// sqrt(q) = q rsqrt(q) corrected by one Newton-Raphson step on s^2 = q with
+// the FP32 seed's half reciprocal root as the step's divisor: with y0 =
+// q^{-1/2}(1 + e), s0 = q y0, the result s0 + (y0 / 2)(q - s0^2) has relative
+// error -1.5 e^2 + O(e^3), the same as q * rsqrt_nr(q), in one FP64 instruction
+// less.  Valid for q > 0 (same range rule as rsqrt_nr).
+__device__ __forceinline__ double sqrt_nr(double q)
+{
+    if (!f32_range(q)) return sqrt(q);
+    const float y0f = rsqrtf(seed_f32(q));
+    const double y0 = widen_f32(y0f), h0 = widen_f32(0.5f * y0f);
+    const double s0 = q * y0;
+    return fma(h0, fma(-s0, s0, q), s0);
 }
 __device__ __forceinline__ double rcp_nr(double x)
 {
@@ -168,6 +184,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     double* U = ws.U + o;
     double* D = ws.D + o;
     double* IH = ws.IH + o;
+    double2* CV = ws.CV + o;
     double2* F0 = ws.F0 + o;
     double2* F1 = ws.F1 + o;
     double2* M = ws.M + o;
@@ -186,6 +203,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         zero |= !pos;
         D[l] = pos ? q * rs : 0.0;
         IH[l] = rs;
+        CV[l] = d2(dx, dy);
     }
     __syncwarp();
     double csum = 0.0;
@@ -218,26 +236,25 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     if (act) {
         const double* __restrict__ Dr = D;
         const double* __restrict__ IHr = IH;
+        const double2* __restrict__ CVr = CV;
         double* __restrict__ Ur = U;
         double2* __restrict__ F0r = F0;
         double2* __restrict__ F1r = F1;
         const int lp = (sj == 0) ? n - 1 : sj - 1;
         double hprev = Dr[lp];
-        double2 pcur = __ldg(p + sj);
-        double2 tprev = scl2(sub2(pcur, __ldg(p + lp)), IHr[lp]);
+        double2 tprev = scl2(CVr[lp], IHr[lp]);
         double S = base;
         double cp = 0, gp = -1.0;
         double2 yp = d2(0, 0);
         // operands of the next row, loaded one row ahead
         double h = Dr[sj], ih = IHr[sj];
-        double2 pn = __ldg(p + sj + 1);  // sj + 1 <= ej < n
+        double2 cv = CVr[sj];
         for (int i = sj; i < ej; ++i) {
-            const int i2 = (i + 2 < n) ? i + 2 : i + 2 - n;
             const double hn = Dr[i + 1], ihn = IHr[i + 1];  // i + 1 <= ej < n
-            const double2 pnn = __ldg(p + i2);
+            const double2 cvn = CVr[i + 1];
             Ur[i] = S;
             S += h;
-            const double2 tau = scl2(sub2(pn, pcur), ih);
+            const double2 tau = scl2(cv, ih);
             const double2 R = sub2(tau, tprev);
             const double B = 2.0 * (hprev + h);
             const double den = fma(-hprev, cp, B);
@@ -248,18 +265,18 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             F0r[i] = d2(ncp, ngp);
             F1r[i] = nyp;
             cp = ncp; gp = ngp; yp = nyp;
-            hprev = h; tprev = tau; pcur = pn;
-            h = hn; ih = ihn; pn = pnn;
+            hprev = h; tprev = tau;
+            h = hn; ih = ihn; cv = cvn;
         }
         // last interior node's values: M_L = y'_L - I_{j-1} g'_L - I_j c'_L
         yL = yp; gL = gp; kL = cp;
-        // interface node e_j
+        // interface node e_j (the loop, which runs at least once, leaves h,
+        // ih and cv holding chord e_j's values)
         Ur[ej] = S;
-        const int en = (ej + 1 == n) ? 0 : ej + 1;
-        const double2 tau = scl2(sub2(__ldg(p + en), pcur), IHr[ej]);
+        const double2 tau = scl2(cv, ih);
         Re = sub2(tau, tprev);
         Ae = hprev;
-        Ce = Dr[ej];
+        Ce = h;
         Be = 2.0 * (hprev + Ce);
     }
 
@@ -355,16 +372,19 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             const long long sb = __double_as_longlong(st);
             while (l + 1 < n && __double_as_longlong(U[l + 1]) <= sb) ++l;
             const int ln = (l + 1 == n) ? 0 : l + 1;
-            const double2 pl = __ldg(p + l), pn = __ldg(p + ln);
+            const double2 pl = __ldg(p + l), cv = CV[l];  // cv = p_{l+1} - p_l
             const double2 Ml = M[l], Mn = M[ln];
             const double d = D[l];
             const double b = (st - U[l]) * IH[l];  // (t - u_l) / h_l
-            const double a = 1.0 - b;
             const double h6 = d * d;  // h^2 M / 6 = d^2 M' (M' = M / (6 L^2))
-            const double ca = a * fma(a, a, -1.0) * h6;
-            const double cb = b * fma(b, b, -1.0) * h6;
-            const double2 S = d2(fma(ca, Ml.x, fma(cb, Mn.x, fma(b, pn.x - pl.x, pl.x))),
-                                 fma(ca, Ml.y, fma(cb, Mn.y, fma(b, pn.y - pl.y, pl.y))));
+            // cubic weights a(a^2 - 1) h6 and b(b^2 - 1) h6 (a = 1 - b) from
+            // w = b(b - 1) h6 = -ab h6: the second is w(1 + b), the first
+            // w(2 - b) = 3w - w(1 + b)  (5 FP64 instructions instead of 8)
+            const double w = fma(b, b, -b) * h6;
+            const double cb = fma(w, b, w);
+            const double ca = fma(w, 3.0, -cb);
+            const double2 S = d2(fma(ca, Ml.x, fma(cb, Mn.x, fma(b, cv.x, pl.x))),
+                                 fma(ca, Ml.y, fma(cb, Mn.y, fma(b, cv.y, pl.y))));
             raw[k] = S;
             ssum = add2(ssum, S);
         }
@@ -383,7 +403,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             const double2 a = raw[k], b = raw[(k + 1 == Nout) ? 0 : k + 1];
             const double dx = b.x - a.x, dy = b.y - a.y;
             const double q = fma(dx, dx, dy * dy);
-            per_len += __double_as_longlong(q) > 0 ? q * rsqrt_nr(q) : 0.0;
+            per_len += __double_as_longlong(q) > 0 ? sqrt_nr(q) : 0.0;
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) per_len += __shfl_xor_sync(0xffffffffu, per_len, off);
@@ -430,7 +450,7 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags)
 {
     const size_t np = (size_t)(n_pts > 0 ? n_pts : 0);
-    size_t b = 3 * align256(np * sizeof(double)) + 3 * align256(np * sizeof(double2));
+    size_t b = 3 * align256(np * sizeof(double)) + 4 * align256(np * sizeof(double2));
     if (flags & FA_STORE_FP32) b += align256((size_t)C * (size_t)N_out * sizeof(double2));
     return b + 256;  // the work counter
 }
@@ -446,6 +466,7 @@ int launch_resample(const fa_handle* h, const double* pts, const int64_t* offset
     ws.U = reinterpret_cast<double*>(b); b += align256(np * sizeof(double));
     ws.D = reinterpret_cast<double*>(b); b += align256(np * sizeof(double));
     ws.IH = reinterpret_cast<double*>(b); b += align256(np * sizeof(double));
+    ws.CV = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.F0 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.F1 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.M = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
