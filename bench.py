@@ -41,7 +41,7 @@ N_MIN, N_MAX = 500, 2000
 SEED = 1002
 # DRAM bytes per launch of the bench workload's kernels, from one ncu capture of the
 # current kernel versions (profiles/*_4096pairs_n1024.md); update when a kernel changes
-DRAM_TRAFFIC_PER_LAUNCH = {"resample_kernel": 2.117451e9 + 1.201334e9,
+DRAM_TRAFFIC_PER_LAUNCH = {"resample_kernel": 2.112787e9 + 1.206817e9,
                            "align_fft_kernel": 1.34767e8 + 6.174e6}
 METRIC = "aligned curve pairs/s at N=1024 (FFT vs direct O(N²), 1 GB300); roofline fraction"
 WORKLOAD = ("4096 pairs of raw curves (N_in ~ U{500..2000}, +-40% node jitter, <=16 harmonics), "
@@ -75,11 +75,26 @@ def align_fft_flops_per_pair(logn: int) -> int:
 
 
 def resample_flops(n_in: np.ndarray, N: int) -> int:
-    """FP64 flops of fa_resample_arclength (FMA = 2; rsqrt and reciprocal
-    count 1): 46 per input node (chords 8, arc lengths and spline equations
-    with the Thomas elimination 23, two backward sweeps 15) and 42 per output
-    node (evaluation 30, perimeter 8, centring and scaling 4)."""
-    return int(46 * int(n_in.sum()) + 42 * N * n_in.size)
+    """FP64 flops of fa_resample_arclength, counted from the kernel's algorithm
+    (FMA = 2; a reciprocal, reciprocal square root or square root = 1):
+      per input node: chord vector 2, |.|^2 3, rsqrt 1, length 1, chunk sum 1 = 8
+      per interior node (n - P of them, P chunks): arc length 1, unit direction
+        2, right-hand side 2, diagonal 2, pivot 2 + reciprocal 1, c' 1, y' 6,
+        g' 2 (forward sweep 19); first-interior recurrence 7; M sweep 8 = 34
+      per chunk: interface row 6, reduced row 14, 18 per cyclic-reduction
+        level (log2 P - 1 levels), final 2x2 solve 14, minus the recurrence's
+        missing last step 7
+      per output node: parameter 1, local coordinate 2, cubic weights 8,
+        spline value 12, mean sum 2, perimeter chord 7, centring and scaling 4 = 36
+      per curve: warp scans and reductions 640, scalars 10."""
+    n = np.asarray(n_in, np.int64)
+    P = np.full(n.shape, 32, np.int64)
+    for _ in range(5):
+        P = np.where(2 * P > n, P // 2, P)
+    levels = np.log2(np.maximum(P, 1)).astype(np.int64) - 1
+    per_chunk = 6 + 14 + 18 * levels + 14 - 7
+    tot = 8 * n + 34 * (n - P) + per_chunk * P + 36 * N + 650
+    return int(tot.sum())
 
 
 def ragged_flops(sizes: np.ndarray) -> int:
