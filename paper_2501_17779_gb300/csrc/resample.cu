@@ -3,9 +3,9 @@
 //
 // One warp per curve.  Lane j owns a contiguous chunk of nodes
 // [s_j, s_{j+1}) (P chunks, P = 32 for n >= 64).  Steps:
-//   A. chord lengths d_l = |p_{l+1} - p_l| (node-parallel), their sum per
-//      chunk; a warp scan gives each chunk's starting arc length and the
-//      perimeter L.
+//   A. chord lengths d_l = |p_{l+1} - p_l| (node-parallel, with the check for
+//      non-finite nodes), their sum per chunk; a warp scan gives each chunk's
+//      starting arc length and the perimeter L.
 //   B. forward sweep over each chunk's interior nodes (all but its last):
 //      cumulative arc lengths S_l = L u_l, the periodic-spline equations
 //          h_{l-1} M_{l-1} + 2(h_{l-1}+h_l) M_l + h_l M_{l+1}
@@ -24,9 +24,9 @@
 //   D. a second backward sweep writes M for every node.
 //   E. the spline is evaluated at t_k = k/N_out (each lane a contiguous block
 //      of outputs; interval search by integer compares on the knots; the
-//      chord vectors p_{l+1} - p_l of step A are kept for B and E), then
-//      the outputs are centred at their mean and divided by the closed-polygon
-//      perimeter of the resampled nodes.
+//      chord vectors p_{l+1} - p_l of step A are kept for B and E; the
+//      closed-polygon perimeter of the outputs is summed in the same loop),
+//      then the outputs are centred at their mean and divided by it.
 // Per-node intermediates live in a caller- or handle-provided workspace
 // (global memory, L1/L2 resident while a warp works on its curve).
 #include <algorithm>
@@ -156,20 +156,20 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     const int64_t zbase = curve * (int64_t)Nout;
 
     // ---- input checks (whole warp) ----------------------------------------
-    bool nf = false;
-    for (int l = lane; l < n; l += 32) nf |= !finite2(__ldg(p + l));
-    if (__any_sync(0xffffffffu, nf)) {
-        fill_nan<F32OUT>(zout, zbase, Nout, lane);
-        if (lane == 0) status[curve] = FA_STATUS_NONFINITE;
-        return;
-    }
+    // Non-finite nodes take precedence over every other status.  For curves
+    // of 4 or more nodes they are caught in step A, which loads every node
+    // anyway (a dropped closing duplicate equals node 0, which A checks).
+    const int n_in = n;
     if (n >= 2) {
         const double2 a = __ldg(p), b = __ldg(p + n - 1);
         if (a.x == b.x && a.y == b.y) n -= 1;  // explicit closing duplicate (first = last)
     }
     if (n < 4) {
+        bool nf = false;
+        for (int l = lane; l < n_in; l += 32) nf |= !finite2(__ldg(p + l));
+        nf = __any_sync(0xffffffffu, nf);
         fill_nan<F32OUT>(zout, zbase, Nout, lane);
-        if (lane == 0) status[curve] = FA_STATUS_DEGENERATE;
+        if (lane == 0) status[curve] = nf ? FA_STATUS_NONFINITE : FA_STATUS_DEGENERATE;
         return;
     }
 
@@ -192,10 +192,11 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     // ---- A: chords (node-parallel, coalesced), chunk sums, warp scan --------
     // d = q * rsqrt(q) and 1/d = rsqrt(q) from one reciprocal square root
     // (q = |p_{l+1} - p_l|^2 >= 0, so its bit pattern tests > 0 as an integer)
-    bool zero = false;
+    bool zero = false, nf = false;
     for (int l = lane; l < n; l += 32) {
         const double2 pl = __ldg(p + l);
         const double2 pn = __ldg(p + ((l + 1 == n) ? 0 : l + 1));
+        nf |= !finite2(pl);
         const double dx = pn.x - pl.x, dy = pn.y - pl.y;
         const double q = fma(dx, dx, dy * dy);
         const bool pos = __double_as_longlong(q) > 0;
@@ -204,6 +205,11 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         D[l] = pos ? q * rs : 0.0;
         IH[l] = rs;
         CV[l] = d2(dx, dy);
+    }
+    if (__any_sync(0xffffffffu, nf)) {
+        fill_nan<F32OUT>(zout, zbase, Nout, lane);
+        if (lane == 0) status[curve] = FA_STATUS_NONFINITE;
+        return;
     }
     __syncwarp();
     double csum = 0.0;
@@ -356,6 +362,9 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     const int k1 = min(k0 + per, Nout);
     double2* raw = F32OUT ? (ws.Z + zbase) : (static_cast<double2*>(zout) + zbase);
     double2 ssum = d2(0, 0);
+    const bool unit = (flags & FA_UNIT_LENGTH) != 0;
+    double per_len = 0.0;
+    double2 Sfirst = d2(0, 0), Sprev = d2(0, 0);
     if (k0 < k1) {
         // arc-length target of output k: L t_k with t_k = k / N_out
         const double s0 = pow2 ? k0 * LN : L * ((double)k0 / (double)Nout);
@@ -390,6 +399,26 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
                                  fma(ca, Ml.y, fma(cb, Mn.y, fma(b, cv.y, pl.y))));
             raw[k] = S;
             ssum = add2(ssum, S);
+            if (unit) {
+                if (k > k0) {
+                    const double dx = S.x - Sprev.x, dy = S.y - Sprev.y;
+                    const double q = fma(dx, dx, dy * dy);
+                    per_len += __double_as_longlong(q) > 0 ? sqrt_nr(q) : 0.0;
+                } else {
+                    Sfirst = S;
+                }
+                Sprev = S;
+            }
+        }
+    }
+    if (unit) {
+        // the chord from this lane's last output to the next one: the next
+        // lane's first (output k1), or output 0 after the last output
+        const double2 Snext = shfl_d2(Sfirst, k1 < Nout ? lane + 1 : 0, 32);
+        if (k0 < k1) {
+            const double dx = Snext.x - Sprev.x, dy = Snext.y - Sprev.y;
+            const double q = fma(dx, dx, dy * dy);
+            per_len += __double_as_longlong(q) > 0 ? sqrt_nr(q) : 0.0;
         }
     }
 #pragma unroll
@@ -401,13 +430,6 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     const double2 mean = (flags & FA_CENTER) ? d2(ssum.x * invN, ssum.y * invN) : d2(0, 0);
     double scale = 1.0;
     if (flags & FA_UNIT_LENGTH) {
-        double per_len = 0.0;
-        for (int k = lane; k < Nout; k += 32) {
-            const double2 a = raw[k], b = raw[(k + 1 == Nout) ? 0 : k + 1];
-            const double dx = b.x - a.x, dy = b.y - a.y;
-            const double q = fma(dx, dx, dy * dy);
-            per_len += __double_as_longlong(q) > 0 ? sqrt_nr(q) : 0.0;
-        }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) per_len += __shfl_xor_sync(0xffffffffu, per_len, off);
         if (!(per_len > 0.0)) {

@@ -65,12 +65,20 @@ def test_resample_degenerate_and_empty():
     nan = good.copy()
     nan[3] = np.nan + 0j
     closed = np.concatenate([good, good[:1]])
-    pts, offs = _csr([good, good[:3], rep, nan, good[:0], closed])
+    # non-finite nodes outrank every other status: in a curve too short to
+    # resample, in the last node only, and in an explicit closing duplicate
+    tiny_nan = good[:3].copy()
+    tiny_nan[1] = np.nan + 0j
+    last_nan = good.copy()
+    last_nan[-1] = complex(np.nan, 0.0)
+    inf_closed = closed.copy()
+    inf_closed[0] = inf_closed[-1] = complex(np.inf, 0.0)
+    pts, offs = _csr([good, good[:3], rep, nan, good[:0], closed, tiny_nan, last_nan, inf_closed])
     z, st = _gpu_resample(pts, offs, 64)
     zo, sto = oracle.resample(pts, offs, 64)
-    assert list(st) == [0, 1, 1, 2, 1, 0]
+    assert list(st) == [0, 1, 1, 2, 1, 0, 2, 2, 2]
     np.testing.assert_array_equal(st, sto)
-    assert np.isnan(z[1:5]).all()
+    assert np.isnan(z[1:5]).all() and np.isnan(z[6:9]).all()
     assert np.abs(z[[0, 5]] - zo[[0, 5]]).max() <= TOL
     # no curves at all
     zz, ss = api.resample_arclength(torch.zeros(0, dtype=torch.complex128, device=DEV),
