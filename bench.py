@@ -41,7 +41,7 @@ N_MIN, N_MAX = 500, 2000
 SEED = 1002
 # DRAM bytes per launch of the bench workload's kernels, from one ncu capture of the
 # current kernel versions (profiles/*_4096pairs_n1024.md); update when a kernel changes
-DRAM_TRAFFIC_PER_LAUNCH = {"resample_kernel": 2.008698e9 + 1.196450e9,
+DRAM_TRAFFIC_PER_LAUNCH = {"resample_kernel": 1.927507e9 + 1.133223e9,
                            "align_fft_kernel": 1.34767e8 + 6.174e6}
 METRIC = "aligned curve pairs/s at N=1024 (FFT vs direct O(N²), 1 GB300); roofline fraction"
 WORKLOAD = ("4096 pairs of raw curves (N_in ~ U{500..2000}, +-40% node jitter, <=16 harmonics), "

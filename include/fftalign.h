@@ -330,9 +330,9 @@ int fa_align_curves_host(fa_handle* h, const double* pts, const int64_t* offsets
  *
  * Scratch: a fixed device array of FA_NOALLOC_SCRATCH_BYTES (64 MiB) that
  * every GPU which loads the library holds until the process exits.  A batch
- * needs fa_resample_workspace_size(C, n_pts, N_out, flags) bytes of it (88
+ * needs fa_resample_workspace_size(C, n_pts, N_out, flags) bytes of it (72
  * bytes per input node, plus 16 bytes per output node with FA_STORE_FP32:
- * about 760,000 input nodes per call); larger batches are rejected with
+ * about 930,000 input nodes per call); larger batches are rejected with
  * FA_ERR_UNSUPPORTED and a message giving both sizes.  Nothing is allocated,
  * freed or zeroed.
  *

@@ -52,7 +52,7 @@ struct Ws {
     double2* CV;   // chord vectors p_{l+1} - p_l       [n_pts]
     double2* F0;   // forward sweep (c'_l, g'_l)        [n_pts]
     double2* F1;   // forward sweep y'_l (x, y)         [n_pts]
-    double2* M;    // spline second derivatives M_l     [n_pts]
+    double2* M;    // spline second derivatives M_l     [n_pts] (stored over F1)
     double2* Z;    // raw outputs before normalisation  [C*N_out] (FP32 output only)
 };
 
@@ -475,7 +475,7 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags)
 {
     const size_t np = (size_t)(n_pts > 0 ? n_pts : 0);
-    size_t b = 3 * align256(np * sizeof(double)) + 4 * align256(np * sizeof(double2));
+    size_t b = 3 * align256(np * sizeof(double)) + 3 * align256(np * sizeof(double2));
     if (flags & FA_STORE_FP32) b += align256((size_t)C * (size_t)N_out * sizeof(double2));
     return b + 256;  // the work counter
 }
@@ -494,7 +494,7 @@ int launch_resample(const fa_handle* h, const double* pts, const int64_t* offset
     ws.CV = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.F0 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.F1 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
-    ws.M = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
+    ws.M = ws.F1;  // M_i overwrites y'_i: step D reads each y'_i just before it writes M_i
     ws.Z = (flags & FA_STORE_FP32) ? reinterpret_cast<double2*>(b) + stage_curve0 * N_out : nullptr;
     if (flags & FA_STORE_FP32) b += align256((size_t)C * (size_t)N_out * sizeof(double2));
     unsigned long long* next = counter ? counter : reinterpret_cast<unsigned long long*>(b);

@@ -57,7 +57,7 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls():
 def test_noalloc_rejects_batches_beyond_its_scratch():
     L = _lib.load()
     dev = torch.device("cuda", 0)
-    n_pts = 2_000_000  # 88 bytes per node > 64 MiB; nothing is launched
+    n_pts = 2_000_000  # 72 bytes per node > 64 MiB; nothing is launched
     pts = torch.zeros(4, dtype=torch.complex128, device=dev)
     offs = torch.tensor([0, 4], dtype=torch.int64, device=dev)
     z = torch.empty((1, 256), dtype=torch.complex128, device=dev)
