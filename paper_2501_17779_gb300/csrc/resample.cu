@@ -38,9 +38,10 @@ namespace {
 
 constexpr int kWarps = 4;  // curves per CTA
 
-// Resident CTAs per SM requested from the compiler: 4 caps the kernel at 128
-// registers (no spills, 16 warps per SM); 5 (96 registers) spills a few words
-// and measured 1 % slower.
+// Resident CTAs per SM requested from the compiler (it also sizes the grid): 4
+// caps the kernel at 128 registers (no spills, 16 warps per SM).  Measured
+// against it: 2 CTAs +17 %, 3 +3.4 % (less workspace in flight does not make
+// up for fewer warps), 5 +0.9 % and 6 +4.5 % (96 / 80 registers, spills).
 #ifndef FA_RESAMPLE_MIN_BLOCKS
 #define FA_RESAMPLE_MIN_BLOCKS 4
 #endif
