@@ -352,7 +352,7 @@ int fa_resample_arclength_noalloc(const double* pts, const int64_t* offsets, int
  * k-NN retrieval under the elastic distance with learned candidate pruning.
  * Not part of the paper (Sec. 3 defines the distance); the pruning network is
  * this library's addition, with fa_elastic_distance as its fallback and as
- * the judge of its recall.
+ * the measure of its recall.
  * ---------------------------------------------------------------------- */
 
 /*

@@ -3,7 +3,7 @@
 // Not part of the paper: Sec. 3 computes elastic distances; pruning the
 // candidates of a k-NN query by a learned embedding of rotation- and
 // shift-invariant Fourier magnitudes is this library's addition, with the
-// exact elastic distance as its fallback and as the judge of its recall.
+// exact elastic distance as its fallback and as the measure of its recall.
 //
 // Network 64 -> 256 -> 256 -> 64 (ReLU, ReLU, linear); weights used in
 // bfloat16 (float32 master copies for Adam), biases, activations and

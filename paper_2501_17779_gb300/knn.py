@@ -9,7 +9,7 @@ addition, not the paper's: it ranks the gallery by the distance of learned
 embeddings of rotation- and shift-invariant descriptors, and only the best
 ``n_cand`` candidates of each query are measured with the elastic distance.
 The exact search (every gallery curve measured) is the fallback and the
-judge of the pruned search's recall.
+reference that the pruned search's recall is measured against.
 """
 from __future__ import annotations
 
