@@ -186,6 +186,24 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(ms: float, pg=None, device=None) -> float:
+    """The slowest rank's time, known to every rank (an all-reduce MAX over
+    the process group; the identity for one process)."""
+    if pg is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: int, steps: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed in `steps` steps
+    over the slowest rank's time `ms` (milliseconds)."""
+    return world * units_per_rank * steps / (ms * 1e-3)
+
+
 def make_workload(rank: int, P: int = P_PAIRS):
     from paper_2501_17779_gb300 import synth
 
@@ -344,11 +362,8 @@ def run_gpu(args):
     total_ms = t_start.elapsed_time(t_end)
     rs_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
     al_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
-    if pg is not None:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * P * K / (total_ms * 1e-3)
+    total_ms = max_over_ranks(total_ms, pg, dev)
+    value = job_rate(world, P, K, total_ms)
 
     # direct O(N^2) baseline on the same resampled curves (align step only)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -466,10 +481,7 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-    if pg is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, pg, dev)
 
     # all-pairs alignment matrix: M = 2048 curves at N = 512 (fa_align_all_pairs)
     allp = None
@@ -686,7 +698,7 @@ def run_gpu(args):
             "elastic": ela,
             "knn": knnr,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * P / (e2e_ms * 1e-3), "unit": "pairs/s",
+            "e2e": {"value": job_rate(world, P, 1, e2e_ms), "unit": "pairs/s",
                     "h2d_bytes_per_step": int(rp.pts.nbytes + rp.offsets.nbytes),
                     "d2h_bytes_per_step": int(P * (4 + 8 + 8 + 1)), "ms_per_step": e2e_ms},
             "gpu_launches": 2 * K,
