@@ -455,6 +455,8 @@ def run_gpu(args):
         "align_fft_kernel": {"ms": al_avg, "tflops": fl_al / (al_avg * 1e-3) / 1e12,
                              "flops_per_launch": fl_al},
     }
+    for kv in kernels.values():  # each kernel against the same measured FP64 peak
+        kv["frac_of_measured_fp64_peak"] = kv["tflops"] / fp64_peak
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     traffic = args.traffic if args.traffic is not None else DRAM_TRAFFIC_PER_LAUNCH.get(dom)
     roof = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["tflops"], "peak": fp64_peak,
