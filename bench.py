@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import hashlib
 import json
 import os
 import statistics
@@ -32,6 +33,7 @@ import subprocess
 import sys
 import threading
 import time
+from pathlib import Path
 
 import numpy as np
 
@@ -39,10 +41,37 @@ P_PAIRS = 4096
 N_NODES = 1024
 N_MIN, N_MAX = 500, 2000
 SEED = 1002
-# DRAM bytes per launch of the bench workload's kernels, from one ncu capture of the
-# current kernel versions (profiles/*_4096pairs_n1024.md); update when a kernel changes
-DRAM_TRAFFIC_PER_LAUNCH = {"resample_kernel": 1.927507e9 + 1.133223e9,
-                           "align_fft_kernel": 1.34767e8 + 6.174e6}
+# DRAM bytes per launch of the bench workload's kernels come from one ncu capture
+# each, recorded in profiles/dram_traffic.txt with a hash of the kernel's sources
+# at capture time; a kernel whose sources have changed since reports no traffic.
+TRAFFIC_FILE = Path(__file__).resolve().parent / "profiles" / "dram_traffic.txt"
+KERNEL_SOURCES = {
+    "resample_kernel": ("resample.cu", "fa_internal.cuh"),
+    "align_fft_kernel": ("align_fft.cu", "fft_stages.cuh", "align_common.cuh", "fa_internal.cuh"),
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """First 16 hex digits of the SHA-256 of the kernel's source files."""
+    csrc = Path(__file__).resolve().parent / "paper_2501_17779_gb300" / "csrc"
+    hsh = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        hsh.update((csrc / name).read_bytes())
+    return hsh.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """(bytes per launch, note) from the traffic file, or (None, why not)."""
+    if kernel not in KERNEL_SOURCES or not TRAFFIC_FILE.exists():
+        return None, "no capture recorded for this kernel"
+    want = kernel_source_hash(kernel)
+    for line in TRAFFIC_FILE.read_text().splitlines():
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel:
+            if f[1] != want:
+                return None, f"capture is of kernel sources {f[1]}, current {want}: stale"
+            return float(f[2]) + float(f[3]), f"ncu capture of kernel sources {want}"
+    return None, "no capture recorded for this kernel"
 METRIC = "aligned curve pairs/s at N=1024 (FFT vs direct O(N²), 1 GB300); roofline fraction"
 WORKLOAD = ("4096 pairs of raw curves (N_in ~ U{500..2000}, +-40% node jitter, <=16 harmonics), "
             "GPU arc-length resampling to N=1024 + FFT alignment over all shifts, FP64")
@@ -212,7 +241,8 @@ def make_workload(rank: int, P: int = P_PAIRS):
 
 def oracle_sample(rp, n_pairs: int, N: int, nthreads: int):
     """Run the oracle (resampling + exhaustive alignment) on the first
-    n_pairs pairs of a workload; returns seconds of wall time."""
+    n_pairs pairs of a workload; returns seconds of wall time and the
+    result (with the oracle's resampled curves under "z1", "z2")."""
     import oracle
 
     P = rp.offsets.size // 2
@@ -223,25 +253,69 @@ def oracle_sample(rp, n_pairs: int, N: int, nthreads: int):
     t0 = time.perf_counter()
     z, st = oracle.resample(pts, offs, N, nthreads=nthreads)
     res = oracle.align_pairs(z[:n_pairs], z[n_pairs:], nthreads=nthreads)
-    return time.perf_counter() - t0, res
+    secs = time.perf_counter() - t0
+    res["z1"], res["z2"] = z[:n_pairs], z[n_pairs:]
+    return secs, res
 
 
-def parity_vs_oracle(o, shift, theta, energy) -> dict:
-    """GPU results of the first pairs against the oracle's: shift agreement
-    (a different shift counts as a tie when its energy is within 1e-9 of the
-    oracle's optimum, the parity rule), the largest angle and relative energy
-    differences."""
+# Parity bounds of the bench's own comparison (the oracle resamples the raw
+# curves itself).  Resampled nodes agree to NODE_TOL; on equal inputs the FP64
+# aligner agrees to 1e-12 relative energy and 1e-10 rad.  Perturbing every node
+# by at most dz moves the optimal energy E = h sum |z1 - R z2|^2 by at most
+# 2 sqrt(E) (2 dz) + (2 dz)^2, and h c(s*) by at most dz (sqrt(n1) + sqrt(n2)),
+# n_i = h sum |z_i|^2 (Cauchy-Schwarz), so theta = arg c by that over h|c| =
+# (n1 + n2 - E) / 2.  complex64 storage rounds every node by at most
+# 2^-24 max|z| per coordinate; a pair whose shift differs from the oracle's is
+# a tie when the two energies differ by no more than that perturbation allows.
+NODE_TOL = 1e-12
+
+
+def parity_vs_oracle(o, shift, theta, energy, zmax=None) -> dict:
+    """GPU results of the first pairs against the oracle's, with the per-pair
+    bounds above: FP64 paths (zmax None) with node agreement NODE_TOL and
+    FP64 aligner tolerances; complex64 storage (zmax = the largest |z| of the
+    resampled curves, which sizes the rounding) with |dtheta| <= 1e-5 and
+    relative dE <= 1e-5 where the shifts agree, ties counted as agreement."""
     n = o["shift"].size
     s = shift[:n].cpu().numpy()
     th = theta[:n].cpu().numpy()
     e = energy[:n].cpu().numpy()
+    z1, z2 = o["z1"], o["z2"]
+    h = 1.0 / z1.shape[1]
+    n1 = h * (np.abs(z1) ** 2).sum(1)
+    n2 = h * (np.abs(z2) ** 2).sum(1)
+    E = np.maximum(o["energy"], 0.0)
+    if zmax is None:
+        dz, e_rel, th_tol, kind = NODE_TOL, 1e-12, 1e-10, "fp64"
+    else:
+        dz, e_rel, th_tol, kind = NODE_TOL + 2.0 ** -24 * np.sqrt(2.0) * zmax, 1e-5, 1e-5, "c64"
+    e_move = 2.0 * np.sqrt(E) * (2 * dz) + (2 * dz) ** 2
+    e_tol = e_rel * E + (e_move if kind == "fp64" else 0.0)
+    th_bound = th_tol + (dz * (np.sqrt(n1) + np.sqrt(n2)) / np.maximum((n1 + n2 - E) / 2, 1e-300)
+                         if kind == "fp64" else 0.0)
     same = s == o["shift"]
-    tie = ~same & (np.abs(e - o["energy"]) <= 1e-9)
-    dth = np.abs(np.angle(np.exp(1j * (th - o["theta"]))))[same]
+    de = np.abs(e - o["energy"])
+    # a different shift: a tie of the oracle's energies (the parity rule, 1e-9)
+    # or, for complex64 storage, within the energy change its rounding allows
+    tie = ~same & (de <= (1e-9 if kind == "fp64" else 2 * e_move + 1e-9))
+    dth = np.abs(np.angle(np.exp(1j * (th - o["theta"]))))
+    agree_tie = float((same | tie).mean())
+    ok_th = bool((dth[same] <= th_bound if np.ndim(th_bound) == 0 else
+                  dth[same] <= th_bound[same]).all())
+    ok_e = bool((de[same] <= e_tol[same]).all())
+    need = 1.0 if kind == "fp64" else 0.999
     return {"pairs": int(n), "shift_agreement": float(same.mean()),
-            "shift_agreement_or_tie": float((same | tie).mean()),
-            "max_abs_dtheta": float(dth.max()) if dth.size else None,
-            "max_rel_denergy": float((np.abs(e - o["energy"]) / o["energy"]).max())}
+            "shift_agreement_or_tie": agree_tie,
+            "max_abs_dtheta": float(dth[same].max()) if same.any() else None,
+            "max_rel_denergy": float((de / o["energy"]).max()),
+            "max_denergy_over_bound": float((de[same] / e_tol[same]).max()) if same.any() else None,
+            "bound": ("energy: 1e-12 E + 2 sqrt(E) 2dz + (2dz)^2 with dz = 1e-12 (nodes); "
+                      "theta: 1e-10 + dz (sqrt(n1) + sqrt(n2)) / h|c|; shifts: exact or a "
+                      "1e-9 tie, on every pair" if kind == "fp64" else
+                      "relative energy 1e-5 and theta 1e-5 where the shift agrees; shift "
+                      "agreement >= 0.999 counting ties within the energy change complex64 "
+                      "rounding allows (dz = 2^-24 sqrt(2) max|z|)"),
+            "within_bound": bool(ok_th and ok_e and agree_tie >= need)}
 
 
 # ------------------------------------------------------------ reference ----
@@ -404,6 +478,7 @@ def run_gpu(args):
     # FP32-storage variant of the whole step: resampled nodes stored as
     # complex64 (FA_STORE_FP32), aligned in FP64 from them (FA_Z_F32); errors
     # against the FP64-storage results of the same curves
+    zmax = float(z.abs().max().item())
     z32 = torch.empty((C, N), dtype=torch.complex64, device=dev)
     ws32_bytes = int(L.fa_resample_workspace_size(C, n_pts, N, flags | _lib.STORE_FP32))
     ws32 = torch.empty(ws32_bytes, dtype=torch.uint8, device=dev)
@@ -430,9 +505,15 @@ def run_gpu(args):
     f32_ms = e0.elapsed_time(e1) / K
     same32 = sh32 == ref_shift
     dth32 = torch.remainder(th32 - ref_theta + np.pi, 2 * np.pi) - np.pi
+    dz32 = 2.0 ** -24 * np.sqrt(2.0) * zmax
+    move32 = 2.0 * torch.sqrt(ref_energy.clamp(min=0)) * (2 * dz32) + (2 * dz32) ** 2
+    tie32 = ~same32 & ((en32 - ref_energy).abs() <= 2 * move32 + 1e-9)
     fp32_storage = {
         "ms_per_step": f32_ms, "pairs_per_s": world * P / (f32_ms * 1e-3),
         "shift_agreement_with_fp64": float(same32.double().mean().item()),
+        "shift_agreement_with_fp64_or_tie": float((same32 | tie32).double().mean().item()),
+        "tie": "a different shift whose energy is within 2 (2 sqrt(E) 2dz + (2dz)^2) + 1e-9 "
+               "of the FP64 path's, dz = 2^-24 sqrt(2) max|z| (complex64 rounding of the nodes)",
         "max_abs_dtheta_where_shift_agrees": float(dth32.abs()[same32].max().item()),
         "max_rel_denergy": float(((en32 - ref_energy).abs() / ref_energy.abs()).max().item()),
         "dtype": "f64 compute, complex64 resampled nodes"}
@@ -458,11 +539,14 @@ def run_gpu(args):
     for kv in kernels.values():  # each kernel against the same measured FP64 peak
         kv["frac_of_measured_fp64_peak"] = kv["tflops"] / fp64_peak
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
-    traffic = args.traffic if args.traffic is not None else DRAM_TRAFFIC_PER_LAUNCH.get(dom)
+    if args.traffic is not None:
+        traffic, tnote = args.traffic, "given on the command line"
+    else:
+        traffic, tnote = recorded_traffic(dom)
     roof = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["tflops"], "peak": fp64_peak,
             "unit": "TFLOP/s", "frac": kernels[dom]["tflops"] / fp64_peak,
             "traffic": traffic, "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum "
-            f"of one ncu capture of this kernel version (profiles/{dom}_4096pairs_n1024.md)",
+            f"per launch: {tnote}",
             "peak_kind": "FP64 FMA throughput measured in this run "
             f"(nominal {FP64_NOMINAL_TFLOPS})", "of": "measured"}
 
@@ -666,7 +750,8 @@ def run_gpu(args):
             secs1, _ = oracle_sample(rp, n1, N, 1)
             parity = {"fp64": parity_vs_oracle(ores, ref_shift, ref_theta, ref_energy),
                       "mixed": parity_vs_oracle(ores, *mix_res),
-                      "fp32_storage": parity_vs_oracle(ores, sh32, th32, en32)}
+                      "fp32_storage": parity_vs_oracle(ores, sh32, th32, en32,
+                                                       zmax=zmax)}
             cpu = {"value": args.cpu_pairs / secs, "unit": "pairs/s", "cores": nthreads,
                    "kind": "oracle", "sample": f"first {args.cpu_pairs} of the 4096 pairs "
                    "(resampling + O(N^2) Kabsch search), one pass, "
@@ -729,7 +814,7 @@ def main():
     ap.add_argument("--ragged-pairs", type=int, default=100_000)
     ap.add_argument("--no-elastic", action="store_true")
     ap.add_argument("--no-knn", action="store_true")
-    ap.add_argument("--knn-exact-queries", type=int, default=32)
+    ap.add_argument("--knn-exact-queries", type=int, default=256)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()

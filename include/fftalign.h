@@ -119,8 +119,12 @@ int fa_version(void);
  *   flags      FA_CENTER | FA_UNIT_LENGTH | FA_STORE_FP32
  *   z_out      [C][N_out] complex128, or complex64 with FA_STORE_FP32 (device)
  *   status     int8[C] per-curve status (device): FA_STATUS_OK, _DEGENERATE
- *              (fewer than 4 distinct nodes, a repeated node, zero perimeter)
- *              or _NONFINITE; the curve's outputs are NaN unless OK
+ *              (fewer than 4 distinct nodes, a repeated node, zero perimeter),
+ *              _NONFINITE, or _BAD_SIZE (the kernel checks each curve's
+ *              offsets: a range that runs backwards, starts below 0, ends
+ *              beyond n_pts or holds more than 2^30 nodes is skipped, so that
+ *              a bad CSR array never reads or writes outside pts and the
+ *              workspace); the curve's outputs are NaN unless OK
  *   workspace  device scratch of at least fa_resample_workspace_size() bytes,
  *              256-byte aligned, or NULL to let the handle provide it (the
  *              handle's buffer then grows with cudaMalloc when needed, and
@@ -221,7 +225,11 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
  *              status FA_STATUS_BAD_SIZE for that pair
  *   band       half-width B of the lattice band, -1 (or >= N) for the full
  *              lattice; the refinement is not confined to it
- *   max_iter   iterations at most, in [1, 1000]
+ *   max_iter   iterations at most, in [0, 1000]; 0 runs none and returns the
+ *              starting triple: the pre-alignment's shift and angle, the lattice
+ *              path of the first gamma-step (its path sums are float32: it only
+ *              picks where the refinement starts) in gamma, and that triple's
+ *              FP64 energy, with iters = 0
  *   shift      int32[P]   s, t0 = s/N (-1 when status != 0)
  *   theta      double[P]  CCW angle of R applied to curve 1 (NaN when status != 0)
  *   energy     double[P]  E of the final triple (the distance is sqrt(E))
@@ -333,12 +341,15 @@ int fa_align_curves_host(fa_handle* h, const double* pts, const int64_t* offsets
  * needs fa_resample_workspace_size(C, n_pts, N_out, flags) bytes of it (72
  * bytes per input node, plus 16 bytes per output node with FA_STORE_FP32:
  * about 930,000 input nodes per call); larger batches are rejected with
- * FA_ERR_UNSUPPORTED and a message giving both sizes.  Nothing is allocated,
- * freed or zeroed.
+ * FA_ERR_UNSUPPORTED and a message giving both sizes.  Nothing is allocated
+ * or freed; each call resets one 8-byte work counter inside the array with a
+ * memset on `stream`.
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, once per device); make that first call before any
- * stream capture.  All calls share the one array and it keeps the last call's
+ * (cudaGetSymbolAddress, once per device) and keeps it for the life of the
+ * process; make that first call before any stream capture.  Calls after a
+ * cudaDeviceReset of that device are not supported (the cached address
+ * belongs to the context that was torn down).  All calls share the one array and it keeps the last call's
  * contents (every value a call reads it has written itself first): calls
  * whose work overlaps on the GPU -- on different streams, or from different
  * host threads -- race on it and must be serialised by the caller.

@@ -66,6 +66,8 @@ def _load():
         vp = ctypes.c_void_p
         L.oracle_elastic_pairs.argtypes = [dp, dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int, vp, dp, dp, vp, vp, vp, vp]
+        L.oracle_elastic_from_start.argtypes = [dp, dp, ctypes.c_int64, ctypes.c_int, vp, dp, dp,
+                                                ctypes.c_int, ctypes.c_int, vp, dp, dp, vp, vp, vp]
         for nm, extra in (("oracle_elastic_dp", [ctypes.c_int, dp]),
                           ("oracle_elastic_refine", [ctypes.c_int, dp, dp, ctypes.c_int]),
                           ("oracle_elastic_energy", [dp])):
@@ -192,6 +194,36 @@ def elastic_pairs(b1, b2, band: int = -1, max_iter: int = 20, nthreads: int | No
         out["gamma"] = g
     if trace:
         out["trace"] = t
+    return out
+
+
+def elastic_from_start(b1, b2, shift0, theta0, g0, max_iter: int = 20,
+                       nthreads: int | None = None) -> dict:
+    """The alternation of O3 alone, started from a given triple per pair
+    (shift0 [P], theta0 [P], g0 [P, N+1]) instead of the pre-alignment and the
+    lattice programme: refinement and (t0,R)-steps until an iteration lowers
+    the energy by at most 1e-12, or max_iter.  Returns the same keys as
+    elastic_pairs (gamma included)."""
+    b1, b2 = _c128(b1), _c128(b2)
+    if b1.ndim == 1:
+        b1, b2 = b1[None], b2[None]
+    P, N = b1.shape
+    s0 = np.ascontiguousarray(shift0, np.int32)
+    t0 = np.ascontiguousarray(theta0, np.float64)
+    g0 = np.ascontiguousarray(g0, np.float64)
+    assert s0.shape == (P,) and t0.shape == (P,) and g0.shape == (P, N + 1)
+    out = dict(shift=np.empty(P, np.int32), theta=np.empty(P), energy=np.empty(P),
+               iters=np.empty(P, np.int32), status=np.empty(P, np.int8))
+    g = np.empty((P, N + 1))
+    nt = nthreads if nthreads is not None else (os.cpu_count() or 1)
+    rc = _load().oracle_elastic_from_start(
+        _dp(b1.view(np.float64)), _dp(b2.view(np.float64)), P, N, s0.ctypes.data, _dp(t0),
+        _dp(g0), max_iter, nt, out["shift"].ctypes.data, _dp(out["theta"]),
+        _dp(out["energy"]), out["iters"].ctypes.data, out["status"].ctypes.data, g.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_elastic_from_start: bad arguments")
+    out["dist"] = np.sqrt(np.maximum(out["energy"], 0.0))
+    out["gamma"] = g
     return out
 
 

@@ -58,6 +58,7 @@
 #define ST_OK 0
 #define ST_DEGENERATE 1
 #define ST_NONFINITE 2
+#define ST_BADSIZE 3
 
 /* flags for oracle_resample */
 #define OR_CENTER 1
@@ -440,8 +441,7 @@ int oracle_max_threads(void)
 /*      (a) a dynamic programme over lattice paths from (0,0) to (N,N)      */
 /*          with steps (a,b), 1 <= a,b <= 3, gcd(a,b) = 1 (slopes b/a in    */
 /*          [1/3, 3]), optionally kept in the band |i - j| <= B, minimising */
-/*          E over those paths (its sums in float32: it only picks the      */
-/*          starting path); run on the first iteration only                 */
+/*          E over those paths; run on the first iteration only             */
 /*          (later the refined gamma carries over: a new shift s from the   */
 /*          (t0,R)-step keeps gamma and lowers E, and the refinement's free  */
 /*          offset g_0 follows it);                                         */
@@ -533,43 +533,38 @@ static double el_energy(const double* q1s, const double* q2, int N, const double
     return E / (double)N;
 }
 
-/* (a) lattice-path dynamic programme.  Its path costs are accumulated in   */
-/* float32: the DP only chooses the refinement's starting path, and every   */
-/* reported value is FP64.  Each cell's term is fmaf(dx, dx, fmaf(dy, dy,   */
-/* acc)) with dx = fmaf(-m, v_x, u_x), m = sqrt(b/a) rounded to float, and   */
-/* the inputs q1s and q2(M) rounded from FP64 to float: the same operations  */
-/* in the same order as the library's kernel, so that both choose the same  */
-/* path.  The minimising path's node values are written to g[0..N]; its     */
-/* FP64 energy is returned.                                                 */
+/* (a) lattice-path dynamic programme over the cells' terms of the energy: */
+/* V(i, j) is the least sum of |q1s_k - sqrt(D_k) q2(M_k)|^2 over the      */
+/* cells k < i of a lattice path from (0, 0) to (i, j); a step (a, b)     */
+/* covers cells i-a .. i-1, each with slope D = b/a and gamma running      */
+/* linearly from j-b to j (the same el_term as the energy).  FP64          */
+/* throughout.  Among equal sums the first step in EL_STEP order wins.     */
+/* The minimising path's node values are written to g[0..N]; its energy is */
+/* returned.                                                               */
 static double el_dp(const double* q1s, const double* q2, int N, int band, double* g)
 {
     const int M = N + 1;
-    float* V = (float*)malloc(sizeof(float) * (size_t)M * M);
+    double* V = (double*)malloc(sizeof(double) * (size_t)M * M);
     signed char* arg = (signed char*)malloc((size_t)M * M);
     for (int x = 0; x < M * M; ++x) { V[x] = INFINITY; arg[x] = -1; }
-    V[0] = 0.0f;
+    V[0] = 0.0;
     for (int i = 1; i <= N; ++i)
         for (int j = 1; j <= N; ++j) {
             if (band >= 0 && abs(i - j) > band) continue;
-            float best = INFINITY;
+            double best = INFINITY;
             int bi = -1;
             for (int st = 0; st < EL_NSTEPS; ++st) {
                 const int a = EL_STEP[st][0], b = EL_STEP[st][1];
                 if (i - a < 0 || j - b < 0) continue;
-                const float prev = V[(i - a) * M + (j - b)];
+                const double prev = V[(i - a) * M + (j - b)];
                 if (prev == INFINITY) continue;
-                const float m = (float)sqrt((double)b / (double)a);
-                float acc = 0.0f;
+                double acc = 0.0;
                 for (int p = 0; p < a; ++p) {
                     const double x = (double)(j - b) + (double)(p * b) / (double)a;
                     const double y = (double)(j - b) + (double)((p + 1) * b) / (double)a;
-                    double v[2];
-                    el_interp(q2, N, 0.5 * (x + y), v, NULL);
-                    const float ux = (float)q1s[2 * (i - a + p)], uy = (float)q1s[2 * (i - a + p) + 1];
-                    const float dx = fmaf(-m, (float)v[0], ux), dy = fmaf(-m, (float)v[1], uy);
-                    acc = fmaf(dx, dx, fmaf(dy, dy, acc));
+                    acc += el_term(q1s, q2, N, i - a + p, x, y);
                 }
-                const float c = prev + acc;
+                const double c = prev + acc;
                 if (c < best) { best = c; bi = st; }
             }
             V[i * M + j] = best;
@@ -836,16 +831,76 @@ typedef struct {
     signed char status;
 } el_result;
 
-/* Approach 2 for one pair:                                                 */
-/*   (s, theta) from the FFT rigid alignment of the arc-length-resampled    */
-/*   curves (Sec. 3 pre-alignment: O2, then O1 with the motion on curve 1), */
-/*   gamma = identity;                                                      */
-/*   repeat: gamma-step ((a) on the first iteration, then (b));             */
+/* The alternation of Approach 2 from a starting triple (s, theta, g):     */
+/*   repeat: gamma-step ((a) on the first iteration when run_dp, then (b)); */
 /*           (t0,R)-step;                                                   */
 /*   until an iteration lowers the energy by at most 1e-12, or max_iter.    */
-/*   The energy is that of the final triple.                                */
+/* On return (s, theta, g) is the final triple; its energy is returned and  */
+/* *iters holds the iterations run.                                         */
+static double el_alternate(const double* q1, const double* q2, int N, int band, int max_iter,
+                           int run_dp, int* s, double* th, double* g, int* iters,
+                           double* trace)
+{
+    double* q1s = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    double Eprev = INFINITY, E = NAN;
+    *iters = 0;
+    for (int it = 1; it <= max_iter; ++it) {
+        if (it == 1 && run_dp) {
+            el_move(q1, N, *s, *th, q1s);
+            el_dp(q1s, q2, N, band, g);
+        }
+        el_refine(q1, q2, N, *s, th, g, EL_LM_ITERS);
+        el_rigid(q1, q2, N, g, s, th);
+        el_move(q1, N, *s, *th, q1s);
+        E = el_energy(q1s, q2, N, g);
+        if (trace) trace[it - 1] = E;
+        *iters = it;
+        if (Eprev - E <= 1e-12) break;
+        Eprev = E;
+    }
+    free(q1s);
+    return E;
+}
+
+/* SRV samples of both curves and the pair's status (st_out); when         */
+/* pre-alignment is wanted, also the FFT pre-alignment of Sec. 3 on the     */
+/* arc-length-resampled curves (O2, then O1 with the motion on curve 1),    */
+/* its start point carried back to curve 1's own parameter.                 */
+static int el_prepare(const double* b1, const double* b2, int N, double* q1, double* q2,
+                      int prealign, int* s, double* th)
+{
+    const size_t cz = sizeof(double) * 2 * (size_t)N;
+    double* r1 = (double*)malloc(cz);
+    double* r2 = (double*)malloc(cz);
+    double* sg1 = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+    double* sg2 = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+    int st1 = el_srv(b1, N, q1, sg1), st2 = el_srv(b2, N, q2, sg2);
+    signed char rs1 = ST_OK, rs2 = ST_OK;
+    if (st1 == ST_OK && st2 == ST_OK) {
+        resample_one(b1, N, N, OR_CENTER | OR_UNIT_LENGTH, r1, &rs1);
+        resample_one(b2, N, N, OR_CENTER | OR_UNIT_LENGTH, r2, &rs2);
+    }
+    int st = st1 == ST_NONFINITE || st2 == ST_NONFINITE ? ST_NONFINITE
+             : st1 != ST_OK ? st1 : st2 != ST_OK ? st2 : rs1 != ST_OK ? rs1 : rs2;
+    if (st == ST_OK && prealign) {
+        double e, gap;
+        signed char ast;
+        /* pre-alignment with the motion on curve 1: e^{i th} r1[k+s] ~ r2[k] */
+        align_one(r2, r1, N, s, th, &e, &gap, &ast);
+        *s = el_param_index(sg1, N, (double)*s / (double)N);
+    }
+    free(r1); free(r2); free(sg1); free(sg2);
+    return st;
+}
+
+/* Approach 2 for one pair: the pre-alignment, gamma = identity, then the   */
+/* alternation (with the dynamic programme on its first iteration).  With   */
+/* start != NULL the pre-alignment and the programme are skipped and the    */
+/* alternation starts from the given triple (start->shift, start->theta,   */
+/* g_start).  The energy is that of the final triple.                       */
 static void elastic_one(const double* b1, const double* b2, int N, int band, int max_iter,
-                        el_result* res, double* gamma, double* trace)
+                        const el_result* start, const double* g_start, el_result* res,
+                        double* gamma, double* trace)
 {
     res->shift = -1; res->iters = 0; res->theta = NAN; res->energy = NAN;
     if (trace)
@@ -855,51 +910,28 @@ static void elastic_one(const double* b1, const double* b2, int N, int band, int
     const size_t cz = sizeof(double) * 2 * (size_t)N;
     double* q1 = (double*)malloc(cz);
     double* q2 = (double*)malloc(cz);
-    double* q1s = (double*)malloc(cz);
-    double* r1 = (double*)malloc(cz);
-    double* r2 = (double*)malloc(cz);
-    double* sg1 = (double*)malloc(sizeof(double) * (size_t)(N + 1));
-    double* sg2 = (double*)malloc(sizeof(double) * (size_t)(N + 1));
     double* g = (double*)malloc(sizeof(double) * (size_t)(N + 1));
-    int st1 = el_srv(b1, N, q1, sg1), st2 = el_srv(b2, N, q2, sg2);
-    signed char rs1 = ST_OK, rs2 = ST_OK;
-    if (st1 == ST_OK && st2 == ST_OK) {
-        resample_one(b1, N, N, OR_CENTER | OR_UNIT_LENGTH, r1, &rs1);
-        resample_one(b2, N, N, OR_CENTER | OR_UNIT_LENGTH, r2, &rs2);
-    }
-    int st = st1 == ST_NONFINITE || st2 == ST_NONFINITE ? ST_NONFINITE
-             : st1 != ST_OK ? st1 : st2 != ST_OK ? st2 : rs1 != ST_OK ? rs1 : rs2;
-    if (st != ST_OK) { res->status = (signed char)st; goto out; }
-    {
-        int s;
-        double th, e, gap, Eprev = INFINITY;
-        signed char ast;
-        /* pre-alignment with the motion on curve 1: e^{i th} r1[k+s] ~ r2[k] */
-        align_one(r2, r1, N, &s, &th, &e, &gap, &ast);
-        s = el_param_index(sg1, N, (double)s / (double)N);
-        for (int k = 0; k <= N; ++k) g[k] = (double)k;
-        for (int it = 1; it <= max_iter; ++it) {
-            if (it == 1) {
-                el_move(q1, N, s, th, q1s);
-                el_dp(q1s, q2, N, band, g);
-            }
-            el_refine(q1, q2, N, s, &th, g, EL_LM_ITERS);
-            el_rigid(q1, q2, N, g, &s, &th);
-            el_move(q1, N, s, th, q1s);
-            const double E = el_energy(q1s, q2, N, g);
-            if (trace) trace[it - 1] = E;
-            res->iters = it;
-            res->energy = E;
-            if (Eprev - E <= 1e-12) break;
-            Eprev = E;
+    int s = 0;
+    double th = 0.0;
+    const int st = el_prepare(b1, b2, N, q1, q2, start == NULL, &s, &th);
+    res->status = (signed char)st;
+    if (st == ST_OK) {
+        if (start) {
+            s = start->shift;
+            th = start->theta;
+            memcpy(g, g_start, sizeof(double) * (size_t)(N + 1));
+        } else {
+            for (int k = 0; k <= N; ++k) g[k] = (double)k;
         }
+        int iters = 0;
+        res->energy = el_alternate(q1, q2, N, band, max_iter, start == NULL, &s, &th, g, &iters,
+                                   trace);
+        res->iters = iters;
         res->shift = s;
         res->theta = th;
-        res->status = ST_OK;
         if (gamma) memcpy(gamma, g, sizeof(double) * (size_t)(N + 1));
     }
-out:
-    free(q1); free(q2); free(q1s); free(r1); free(r2); free(sg1); free(sg2); free(g);
+    free(q1); free(q2); free(g);
 }
 
 /* O3 on P pairs of N-node curves (complex interleaved, [P, N] each).      */
@@ -919,9 +951,44 @@ int oracle_elastic_pairs(const double* b1, const double* b2, int64_t P, int N, i
 #endif
     for (int64_t p = 0; p < P; ++p) {
         el_result r;
-        elastic_one(b1 + 2 * (size_t)N * p, b2 + 2 * (size_t)N * p, N, band, max_iter, &r,
-                    gamma ? gamma + (size_t)(N + 1) * p : NULL,
+        elastic_one(b1 + 2 * (size_t)N * p, b2 + 2 * (size_t)N * p, N, band, max_iter, NULL,
+                    NULL, &r, gamma ? gamma + (size_t)(N + 1) * p : NULL,
                     trace ? trace + (size_t)max_iter * p : NULL);
+        shift[p] = r.shift; theta[p] = r.theta; energy[p] = r.energy;
+        iters[p] = r.iters; status[p] = r.status;
+    }
+    return ORACLE_OK;
+}
+
+/* The alternation alone, from a given starting triple per pair: shift0,   */
+/* theta0 and g0 ([P, N+1]) -- for instance another implementation's       */
+/* lattice path -- then refinement and (t0,R)-steps exactly as in           */
+/* oracle_elastic_pairs.  Outputs as there (gamma may be NULL).            */
+int oracle_elastic_from_start(const double* b1, const double* b2, int64_t P, int N,
+                              const int32_t* shift0, const double* theta0, const double* g0,
+                              int max_iter, int nthreads, int32_t* shift, double* theta,
+                              double* energy, int32_t* iters, signed char* status,
+                              double* gamma)
+{
+    if (!b1 || !b2 || !shift0 || !theta0 || !g0 || !shift || !theta || !energy || !iters ||
+        !status || P < 0 || N < 4 || max_iter < 1)
+        return ORACLE_ERR_ARG;
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t p = 0; p < P; ++p) {
+        el_result r, st;
+        st.shift = shift0[p];
+        st.theta = theta0[p];
+        if (st.shift < 0 || st.shift >= N) {
+            shift[p] = -1; theta[p] = NAN; energy[p] = NAN; iters[p] = 0;
+            status[p] = ST_BADSIZE;
+            continue;
+        }
+        elastic_one(b1 + 2 * (size_t)N * p, b2 + 2 * (size_t)N * p, N, -1, max_iter, &st,
+                    g0 + (size_t)(N + 1) * p, &r, gamma ? gamma + (size_t)(N + 1) * p : NULL,
+                    NULL);
         shift[p] = r.shift; theta[p] = r.theta; energy[p] = r.energy;
         iters[p] = r.iters; status[p] = r.status;
     }

@@ -1,5 +1,5 @@
 // align_common.cuh -- thread-group geometry and group reductions shared by
-// the pair-alignment kernels (align_fft.cu, align_mixed.cu).  A "group" is
+// the pair-alignment kernels (align_fft.cu, align_df_impl.cuh).  A "group" is
 // the Q = N/4 threads that work on one pair; a CTA holds G groups.
 #pragma once
 

@@ -434,8 +434,8 @@ int fa_elastic_distance(fa_handle* h, const double* curves1, int64_t M1, const d
     if (N < kMinElasticN || N > kMaxElasticN || (N & (N - 1)))
         return set_error(FA_ERR_UNSUPPORTED,
                          "fa_elastic_distance: N must be a power of two in [32, 1024]");
-    if (max_iter < 1 || max_iter > 1000)
-        return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: max_iter outside [1, 1000]");
+    if (max_iter < 0 || max_iter > 1000)
+        return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: max_iter outside [0, 1000]");
     if (band < -1) return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: band < -1");
     if ((!idx1 && M1 < P) || (!idx2 && M2 < P))
         return set_error(FA_ERR_INVALID_ARG,
@@ -487,6 +487,8 @@ extern "C" int fa_align_curves_host(fa_handle* h, const double* pts, const int64
         if (offsets[i + 1] < offsets[i])
             return set_error(FA_ERR_INVALID_ARG, "fa_align_curves_host: decreasing offsets");
     const int64_t n_pts = offsets[C];
+    if (C > (int64_t)1 << 40 || n_pts > (int64_t)1 << 40)
+        return set_error(FA_ERR_UNSUPPORTED, "fa_align_curves_host: size too large");
     const int ztype = (flags & FA_STORE_FP32) ? FA_Z_F32 : FA_Z_F64;
     const size_t zb = (flags & FA_STORE_FP32) ? sizeof(float2) : sizeof(double2);
     auto a256 = [](size_t b) { return (b + 255) & ~(size_t)255; };

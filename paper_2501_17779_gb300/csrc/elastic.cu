@@ -689,21 +689,41 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
         for (int k = tid; k <= N; k += T) g[k] = (double)k;
         __syncthreads();
 
+        // the first gamma-step's lattice path (float32 path sums: the DP only
+        // picks the refinement's starting path; every reported value is FP64)
+        {
+            double2 cs;
+            sincos(theta, &cs.y, &cs.x);
+            float2* q1f = reinterpret_cast<float2*>(q1s);
+            for (int k = tid; k < N; k += T) {
+                const double2 u = rot(cs, q1[(k + s) & (N - 1)]);
+                q1f[k] = make_float2(__double2float_rn(u.x), __double2float_rn(u.y));
+            }
+            __syncthreads();
+            elastic_dp<T>(N, B, q1f, reinterpret_cast<const float2*>(q2f),
+                          reinterpret_cast<float*>(ar), bp, g);
+        }
         int it = 0;
         double Eprev = HUGE_VAL, En = 0.0;
-        for (it = 1; it <= a.max_iter; ++it) {
-            if (it == 1) {
-                double2 cs;
-                sincos(theta, &cs.y, &cs.x);
-                float2* q1f = reinterpret_cast<float2*>(q1s);
-                for (int k = tid; k < N; k += T) {
-                    const double2 u = rot(cs, q1[(k + s) & (N - 1)]);
-                    q1f[k] = make_float2(__double2float_rn(u.x), __double2float_rn(u.y));
-                }
-                __syncthreads();
-                elastic_dp<T>(N, B, q1f, reinterpret_cast<const float2*>(q2f),
-                              reinterpret_cast<float*>(ar), bp, g);
+        if (a.max_iter == 0) {
+            // no iteration: report the starting triple (pre-alignment s, theta
+            // and the lattice path) with its FP64 energy
+            double2 cs;
+            sincos(theta, &cs.y, &cs.x);
+            double e[1] = {0.0};
+            for (int k = tid; k < N; k += T) {
+                double2 v;
+                cr_eval(q2, N, 0.5 * (g[k] + g[k + 1]), v, nullptr);
+                const double D = g[k + 1] - g[k];
+                const double m = D * rsqrt_fast(D);
+                const double2 u = rot(cs, q1[(k + s) & (N - 1)]);
+                const double dx = fma(-m, v.x, u.x), dy = fma(-m, v.y, u.y);
+                e[0] = fma(dx, dx, fma(dy, dy, e[0]));
             }
+            cta_sums<T, 1>(e, red);
+            En = e[0] / (double)N;
+        }
+        for (it = 1; it <= a.max_iter; ++it) {
             elastic_refine<T, NMAX>(q1, q2, N, s, theta, g, gt, cb0, cb1, L, red);
             // (t0, R)-step on w_k = sqrt(D_k) q2(M_k)
             for (int k = tid; k < N; k += T) {

@@ -60,6 +60,8 @@ extern "C" int fa_resample_arclength_noalloc(const double* pts, const int64_t* o
     if (C == 0) return FA_OK;
     if (!offsets || !z_out || !status || (n_pts > 0 && !pts))
         return set_error(FA_ERR_INVALID_ARG, "fa_resample_arclength_noalloc: null pointer");
+    if (C > (int64_t)1 << 40 || n_pts > (int64_t)1 << 40)
+        return set_error(FA_ERR_UNSUPPORTED, "fa_resample_arclength_noalloc: size too large");
     const size_t need = fa::resample_ws_bytes(C, n_pts, N_out, flags);
     if (need > (size_t)FA_NOALLOC_SCRATCH_BYTES)
         return set_error(FA_ERR_UNSUPPORTED,

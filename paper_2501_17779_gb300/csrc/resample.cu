@@ -147,14 +147,25 @@ __device__ void fill_nan(void* zout, int64_t base, int Nout, int lane)
 template <bool F32OUT>
 __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
                                                const double2* __restrict__ pts,
-                                               const int64_t* __restrict__ offsets, int Nout,
-                                               int flags, void* __restrict__ zout,
+                                               const int64_t* __restrict__ offsets,
+                                               int64_t n_pts, int Nout, int flags,
+                                               void* __restrict__ zout,
                                                int8_t* __restrict__ status, const Ws& ws)
 {
     const int64_t o = offsets[curve];
-    int n = (int)(offsets[curve + 1] - o);
-    const double2* p = pts + o;
+    const int64_t o1 = offsets[curve + 1];
     const int64_t zbase = curve * (int64_t)Nout;
+    // The CSR offsets come from device memory the host has not seen: a curve
+    // whose range is not inside [0, n_pts], runs backwards or holds more than
+    // 2^30 nodes is flagged and skipped, so that no index below leaves the
+    // input or the workspace (both sized by n_pts).
+    if (o < 0 || o1 < o || o1 > n_pts || o1 - o > ((int64_t)1 << 30)) {
+        fill_nan<F32OUT>(zout, zbase, Nout, lane);
+        if (lane == 0) status[curve] = FA_STATUS_BAD_SIZE;
+        return;
+    }
+    int n = (int)(o1 - o);
+    const double2* p = pts + o;
 
     // ---- input checks (whole warp) ----------------------------------------
     // Non-finite nodes take precedence over every other status.  For curves
@@ -455,7 +466,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
 template <bool F32OUT>
 __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
     resample_kernel(const double2* __restrict__ pts, const int64_t* __restrict__ offsets,
-                    int64_t C, int Nout, int flags, void* __restrict__ zout,
+                    int64_t C, int64_t n_pts, int Nout, int flags, void* __restrict__ zout,
                     int8_t* __restrict__ status, Ws ws, unsigned long long* __restrict__ next)
 {
     const int lane = threadIdx.x & 31;
@@ -464,7 +475,8 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
         if (lane == 0) c = atomicAdd(next, 1ull);
         c = __shfl_sync(0xffffffffu, c, 0);
         if (c >= (unsigned long long)C) break;
-        resample_curve<F32OUT>((int64_t)c, lane, pts, offsets, Nout, flags, zout, status, ws);
+        resample_curve<F32OUT>((int64_t)c, lane, pts, offsets, n_pts, Nout, flags, zout, status,
+                               ws);
         __syncwarp();
     }
 }
@@ -475,9 +487,13 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags)
 {
+    // sizes beyond 2^40 nodes or curves saturate (no caller can hold them, and a
+    // wrapped product would make an impossible batch look small)
+    constexpr int64_t kMax = (int64_t)1 << 40;
+    if (C > kMax || n_pts > kMax || N_out > (1 << 20)) return SIZE_MAX;
     const size_t np = (size_t)(n_pts > 0 ? n_pts : 0);
     size_t b = 3 * align256(np * sizeof(double)) + 3 * align256(np * sizeof(double2));
-    if (flags & FA_STORE_FP32) b += align256((size_t)C * (size_t)N_out * sizeof(double2));
+    if (flags & FA_STORE_FP32) b += align256((size_t)(C > 0 ? C : 0) * (size_t)N_out * sizeof(double2));
     return b + 256;  // the work counter
 }
 
@@ -512,11 +528,11 @@ int launch_resample(const fa_handle* h, const double* pts, const int64_t* offset
     const cudaError_t me = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
     if (me != cudaSuccess) return cuda_error(me, "resample counter reset");
     if (flags & FA_STORE_FP32)
-        resample_kernel<true><<<(unsigned)blocks, kWarps * 32, 0, st>>>(p, offsets, C, N_out, flags,
-                                                                       z_out, status, ws, next);
+        resample_kernel<true><<<(unsigned)blocks, kWarps * 32, 0, st>>>(
+            p, offsets, C, (int64_t)np, N_out, flags, z_out, status, ws, next);
     else
-        resample_kernel<false><<<(unsigned)blocks, kWarps * 32, 0, st>>>(p, offsets, C, N_out,
-                                                                        flags, z_out, status, ws, next);
+        resample_kernel<false><<<(unsigned)blocks, kWarps * 32, 0, st>>>(
+            p, offsets, C, (int64_t)np, N_out, flags, z_out, status, ws, next);
     return cuda_error(cudaGetLastError(), "resample launch");
 }
 

@@ -54,6 +54,129 @@ def _compare(r, o, label=""):
     assert (~same_s).sum() <= max(1, int(0.05 * same_s.size))
 
 
+# --- the three-part parity of the elastic kernel -----------------------------
+# (a) its lattice path is a valid, near-optimal path of the oracle's FP64 DP;
+# (b) from the kernel's own starting triple the oracle's refinement and
+#     (t0,R)-steps reproduce the kernel's result at the FP64 bounds above;
+# (c) end to end against the oracle's own pipeline (its FP64 DP included),
+#     with at most DISAGREE_FRAC of the pairs (at least one) allowed to end
+#     elsewhere because the two programmes started from different paths.
+#     Emulated on the CPU (the float32 path sums against the FP64 ones on
+#     1,276 pairs of these sets and a 256-node gallery) no pair ended
+#     elsewhere.
+DISAGREE_FRAC = 0.02
+STEPS = [(1, 1), (1, 2), (2, 1), (1, 3), (3, 1), (2, 3), (3, 2)]
+
+
+def _sets(N, P, seed0=1000):
+    b1 = np.stack([_curve(seed0 + N + p, N) for p in range(P)])
+    b2 = np.stack([_curve(seed0 + 1000 + N + p, N) for p in range(P)])
+    t = np.arange(N) / N
+    for p in range(P):
+        f = synth.arclength_curve(synth.random_harmonics(np.random.default_rng(seed0 + 2000 + p), 8))
+        b2[p] = f(0.1 * p + t + 0.03 * np.sin(2 * np.pi * t))
+    return b1, b2
+
+
+def _lattice_steps(g, N, band):
+    """The (a, b) steps of node values g if they form a lattice path from (0, 0)
+    to (N, N) inside the band, else None."""
+    if g[0] != 0.0 or g[N] != N:
+        return None
+    i, out = 0, []
+    while i < N:
+        j = g[i]
+        if j != np.floor(j):
+            return None
+        for a, b in STEPS:
+            if i + a > N or g[i + a] != j + b:
+                continue
+            if all(g[i + p] == j + p * b / a for p in range(a)):
+                if band >= 0 and abs(i + a - (j + b)) > band:
+                    return None
+                out.append((a, b))
+                i += a
+                break
+        else:
+            return None
+    return out
+
+
+def _moved(q1, s, th):
+    return np.exp(1j * th) * np.roll(q1, -s)
+
+
+@pytest.mark.parametrize("N,band", [(64, -1), (128, 16), (256, 32), (512, 40)])
+def test_elastic_dp_path_is_valid_and_near_optimal(N, band):
+    """(a) The kernel's lattice programme sums path costs in float32 (it only
+    picks where the refinement starts).  Its path must be a lattice path of
+    the seven steps inside the band, its reported energy (FP64) must equal the
+    oracle's energy of that path, and it may exceed the oracle's FP64 optimum
+    on the same SRV samples only by the float32 error bound.  Bound: a cell
+    term |u - m v|^2 with u, v, m rounded to float and one fused rounding per
+    operation is off by at most 8 eps A^2 (eps = 2^-24, A = |u| + m|v|); the
+    path sum adds N more roundings of its partial sums, so a path's float32
+    cost is within (N + 8) eps sum_k A_k^2 of its exact cost, and
+    sum A_k^2 <= 2 (sum |q1s_k|^2 + sum D_k |q2(M_k)|^2) <= 2 (N + 2N) for
+    unit-norm SRV functions (the interpolant's norm stays within 2x).  The
+    kernel's path therefore costs at most 2 (N + 8) eps 6N more than the
+    optimum, i.e. 12 (N + 8) eps in the energy (1/N of the cost)."""
+    P = 24 if N <= 256 else 8
+    b1, b2 = _sets(N, P)
+    r = _gpu(b1, b2, band=band, max_iter=0)
+    assert (r["status"] == 0).all() and (r["iters"] == 0).all()
+    bound = 12 * (N + 8) * 2.0 ** -24
+    gaps = []
+    for p in range(P):
+        g0 = r["gamma"][p]
+        assert _lattice_steps(g0, N, band) is not None, p
+        q1, _, _ = oracle.srv(b1[p])
+        q2, _, _ = oracle.srv(b2[p])
+        q1s = _moved(q1, int(r["shift"][p]), float(r["theta"][p]))
+        e_path = oracle.elastic_energy(q1s, q2, g0)
+        assert abs(r["energy"][p] - e_path) <= 1e-13 * max(1.0, e_path)
+        g_opt, e_opt = oracle.elastic_dp(q1s, q2, band)
+        assert _lattice_steps(g_opt, N, band) is not None
+        assert e_opt <= e_path + 1e-13
+        gaps.append(e_path - e_opt)
+    print(f"N={N} band={band}: kernel path - FP64 optimum <= {max(gaps):.3g} (bound {bound:.3g}),"
+          f" same energy on {np.mean(np.array(gaps) <= 1e-13):.3f} of pairs")
+    assert max(gaps) <= bound
+
+
+@pytest.mark.parametrize("N,band", [(64, -1), (128, 16), (256, 32), (512, 40)])
+def test_elastic_alternation_from_the_kernels_start_matches_oracle(N, band):
+    """(b) The oracle's refinement and (t0,R)-steps, started from the kernel's
+    own starting triple (pre-alignment shift and angle, its lattice path),
+    reproduce the kernel's final shift, angle, energy and gamma at the FP64
+    bounds of the end-to-end comparison."""
+    P = 24 if N <= 256 else 8
+    b1, b2 = _sets(N, P)
+    r0 = _gpu(b1, b2, band=band, max_iter=0)
+    r = _gpu(b1, b2, band=band, max_iter=20)
+    o = oracle.elastic_from_start(b1, b2, r0["shift"], r0["theta"], r0["gamma"], max_iter=20)
+    _compare(r, o, f"from kernel start N={N} band={band}")
+
+
+def test_elastic_gallery_end_to_end_disagreement_rate():
+    """(c) On gallery pairs (the k-NN workload's shapes, 256 nodes, band 32),
+    the kernel against the oracle's own pipeline: energies within E_ABS except
+    on at most DISAGREE_FRAC of the pairs."""
+    N, P = 256, 192
+    gal = synth.shape_gallery(1015, 512, N)
+    rng = np.random.default_rng(5)
+    i1 = rng.integers(0, 512, P)
+    i2 = rng.integers(0, 512, P)
+    b1, b2 = gal.curves[i1], gal.curves[i2]
+    r = _gpu(b1, b2, band=32)
+    o = oracle.elastic_pairs(b1, b2, band=32, gamma=True)
+    np.testing.assert_array_equal(r["status"], o["status"])
+    dE = np.abs(r["energy"] - o["energy"])
+    bad = dE > E_ABS
+    print(f"gallery: {bad.sum()} of {P} pairs beyond {E_ABS} (max |dE| {dE.max():.3g})")
+    assert bad.sum() <= max(1, int(DISAGREE_FRAC * P))
+
+
 @pytest.mark.parametrize("which", ["gamma1", "gamma2"])
 def test_elastic_table2_zero_distance(which):
     """The paper's experiment (Sec. 3, Table 2): start point 0.25, rotation

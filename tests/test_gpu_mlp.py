@@ -8,6 +8,8 @@ import oracle
 from oracle import mlp as omlp
 from paper_2501_17779_gb300 import api, synth
 
+from _mlp_bounds import forward_bounds, pair_grad_bounds
+
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda"
@@ -34,12 +36,16 @@ def test_forward_matches_oracle():
     X = np.random.default_rng(3).normal(size=(333, 64)).astype(np.float32)
     Y = net.forward(torch.from_numpy(X).to(DEV)).cpu().numpy()
     Yo, _, _ = omlp.forward(p, X)
-    assert _rel(Y, Yo) < 1e-5
+    bound = forward_bounds(p, X)["bound_y"]
+    err = np.abs(Y.astype(np.float64) - Yo)
+    print(f"forward: max err/bound {np.max(err / bound):.3g}, relative norm {_rel(Y, Yo):.3g}")
+    assert (err <= bound).all()
 
 
 def test_pair_gradient_matches_oracle():
     """float32 accumulation against the float64 oracle on the same bfloat16
-    weights: every parameter block within 1e-4 (relative norm)."""
+    weights, element by element within the probabilistic float32 bound of
+    tests/_mlp_bounds.py (the relative norm per block is printed only)."""
     net = api.Mlp(seed=1)
     p = _params(4)
     net.set_params(p)
@@ -54,14 +60,15 @@ def test_pair_gradient_matches_oracle():
     lo, go = omlp.pair_loss_grad(p, X, pi, pj, d)
     assert abs(loss.item() - lo) <= 1e-5 * lo
     g = g.cpu().numpy()
-    gu, gou = omlp.unpack(g), omlp.unpack(go)
+    bound = pair_grad_bounds(p, X, pi, pj, d)
+    err = np.abs(g.astype(np.float64) - go)
+    gu, gou, eu, bu = (omlp.unpack(a) for a in (g, go, err, bound))
     for name, _ in omlp.SHAPES:
-        if name == "b3":
-            # the pair loss depends on y_i - y_j only: dL/db3 = 0 exactly
-            assert np.linalg.norm(gu[name]) < 1e-5 * np.linalg.norm(gou["W3"])
-            assert np.linalg.norm(gou[name]) < 1e-12 * np.linalg.norm(gou["W3"])
-            continue
-        assert _rel(gu[name], gou[name]) < 1e-4, name
+        print(f"{name}: max err/bound {np.max(eu[name] / bu[name]):.3g}, "
+              f"relative norm {_rel(gu[name], gou[name]):.3g}")
+    assert (err <= bound).all()
+    # the pair loss depends on y_i - y_j only: dL/db3 = 0 exactly in the oracle
+    assert np.linalg.norm(gou["b3"]) < 1e-12 * np.linalg.norm(gou["W3"])
 
 
 def test_adam_step_matches_oracle():

@@ -220,3 +220,29 @@ def test_elastic_distance_properties():
     bad[4] = 0.0
     rs = oracle.elastic_pairs(b1, bad)
     assert list(rs["status"]) == [0, 0, 2, 0, 1, 0] and np.isnan(rs["energy"][[2, 4]]).all()
+
+
+def test_alternation_from_a_given_start_continues_the_full_run():
+    """oracle.elastic_from_start runs the alternation alone.  Started from the
+    triple that the full pipeline holds after its first iteration, it ends
+    where the full pipeline ends (same shift, energy to rounding), and a bad
+    starting shift is flagged per pair."""
+    N, P = 64, 6
+    rng = np.random.default_rng(11)
+    b1 = np.stack([synth.uniform_arclength_nodes(synth.random_harmonics(rng, 6), N)
+                   for _ in range(P)])
+    b2 = np.stack([synth.uniform_arclength_nodes(synth.random_harmonics(rng, 6), N)
+                   for _ in range(P)])
+    one = oracle.elastic_pairs(b1, b2, max_iter=1, gamma=True)
+    full = oracle.elastic_pairs(b1, b2, max_iter=20, gamma=True)
+    cont = oracle.elastic_from_start(b1, b2, one["shift"], one["theta"], one["gamma"],
+                                     max_iter=19)
+    assert (cont["status"] == 0).all()
+    np.testing.assert_array_equal(cont["shift"], full["shift"])
+    assert np.abs(cont["energy"] - full["energy"]).max() <= 1e-14
+    assert np.abs(cont["gamma"] - full["gamma"]).max() <= 1e-9
+    s0 = one["shift"].copy()
+    s0[2] = N
+    bad = oracle.elastic_from_start(b1, b2, s0, one["theta"], one["gamma"], max_iter=3)
+    assert bad["status"][2] == 3 and bad["shift"][2] == -1
+    assert (np.delete(bad["status"], 2) == 0).all()

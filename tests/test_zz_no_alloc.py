@@ -18,9 +18,8 @@ import torch
 
 from paper_2501_17779_gb300 import _lib, api, synth
 
-pytestmark = pytest.mark.gpu
-
 TOL = 1e-12
+TOL_F32 = 2.0 ** -23  # complex64 output: one rounding of a unit-scale value
 
 
 def _noalloc(L, pts, offs, N, flags):
@@ -35,6 +34,7 @@ def _noalloc(L, pts, offs, N, flags):
     return z, st
 
 
+@pytest.mark.gpu
 def test_noalloc_matches_workspace_entry_point_on_two_calls():
     L = _lib.load()
     dev = torch.device("cuda", 0)
@@ -54,6 +54,43 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls():
         assert float((z - zr).abs().max()) <= TOL
 
 
+@pytest.mark.gpu
+def test_noalloc_complex64_output_matches_workspace_entry_point():
+    """With FA_STORE_FP32 the complex128 staging rows also live in the fixed
+    array; the result equals the workspace entry point's complex64 output."""
+    L = _lib.load()
+    dev = torch.device("cuda", 0)
+    flags = _lib.CENTER | _lib.UNIT_LENGTH | _lib.STORE_FP32
+    pts_np, offs_np = synth.raw_curves(33, C=64, n_min=300, n_max=1500)
+    pts = torch.from_numpy(pts_np).to(dev)
+    offs = torch.from_numpy(offs_np).to(dev)
+    N = 512
+    need = L.fa_resample_workspace_size(offs.numel() - 1, pts.numel(), N, flags)
+    assert need <= _lib.NOALLOC_SCRATCH_BYTES
+    for _ in range(2):
+        z, st = _noalloc(L, pts, offs, N, flags)
+        zr, str_ = api.resample_arclength(pts, offs, N, fp32=True)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(st.cpu().numpy(), str_.cpu().numpy())
+        assert (st.cpu().numpy() == 0).all()
+        assert z.dtype == torch.complex64 and zr.dtype == torch.complex64
+        assert float((z - zr).abs().max()) <= TOL_F32
+
+
+def test_noalloc_rejects_sizes_whose_scratch_would_wrap():
+    """2^61 nodes would wrap the 64-bit scratch size to a small number; the
+    call rejects it on the host before touching any pointer (no GPU needed:
+    the pointers below are never dereferenced)."""
+    L = _lib.load()
+    fake = ctypes.c_void_p(256)
+    for n_pts in (2 ** 61, 2 ** 41):
+        rc = L.fa_resample_arclength_noalloc(fake, fake, 1, n_pts, 256,
+                                             _lib.CENTER | _lib.UNIT_LENGTH, fake, fake, None)
+        assert rc == _lib.ERR_UNSUPPORTED
+    assert L.fa_resample_workspace_size(1, 2 ** 61, 256, 0) == 2 ** 64 - 1
+
+
+@pytest.mark.gpu
 def test_noalloc_rejects_batches_beyond_its_scratch():
     L = _lib.load()
     dev = torch.device("cuda", 0)
