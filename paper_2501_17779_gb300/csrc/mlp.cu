@@ -7,14 +7,16 @@
 //
 // Network 64 -> 256 -> 256 -> 64 (ReLU, ReLU, linear); weights used in
 // bfloat16 (float32 master copies for Adam), biases, activations and
-// accumulation in float32.  The layers are a tiled SIMT GEMM (64x64 output
-// tile, 16-deep k slices in shared memory, 4x4 outputs per thread) with the
-// bias/ReLU/mask epilogues fused; weight gradients reduce over the batch with
-// a deterministic split-K.  At these sizes (<= 0.1 GFLOP per layer per step)
-// the network costs well under 1% of the elastic distances it is trained on.
+// accumulation in float32.  Every layer product (forward, back-propagated
+// gradients, weight gradients) runs on the tensor cores (tc_gemm_kernel:
+// tcgen05.mma from shared-memory descriptors, float32 accumulators in tensor
+// memory, float32 operands as three bfloat16 pieces) with the bias/ReLU/mask
+// epilogues fused; weight gradients reduce over the batch with a
+// deterministic split-K.
 //
-// Retrieval: squared embedding distances (the same GEMM tile with a
-// subtract-square inner step), and a per-row radix selection of the k
+// Retrieval: squared embedding distances (a tiled SIMT kernel with a
+// subtract-square inner step, also used for the bias gradients' column sums),
+// and a per-row radix selection of the k
 // smallest keys (8-bit digits over the order-preserving bit pattern, ordered
 // compaction, bitonic sort of the k survivors by (key, position)).
 #include <cuda_bf16.h>
@@ -23,9 +25,12 @@
 #include <cstring>
 #include <vector>
 
+#include <type_traits>
+
 #include "cta_ops.cuh"
 #include "fa_internal.cuh"
 #include "fft_stages.cuh"
+#include "umma.cuh"
 
 struct fa_mlp {
     fa_handle* h = nullptr;
@@ -37,6 +42,7 @@ struct fa_mlp {
     int64_t t = 0;                // Adam step count
     void* ws = nullptr;           // activations and split-K partials
     size_t ws_bytes = 0;
+    int* tc_err = nullptr;        // set by a tensor-core GEMM whose wait timed out
 };
 
 namespace fa {
@@ -131,6 +137,179 @@ __global__ void __launch_bounds__(256) gemm_kernel(const __grid_constant__ GemmA
             C[m * g.scm + n * g.scn] = v;
         }
     }
+}
+
+// ---- the same products on the tensor cores (tcgen05) ------------------------
+// C(m, n) = sum_k A(m, k) B(k, n) + epilogue, A float32, B bfloat16 (the
+// weights, exact) or float32.  float32 operands enter as three bfloat16
+// pieces (hi + mid + lo = the float exactly), bfloat16 weights as one; the
+// MMAs take the piece products that matter at float32 precision (hi hi, hi
+// mid, mid hi, hi lo, mid mid, lo hi for two float operands: the dropped ones
+// are below 2^-25 of the product) and accumulate in float32 in tensor memory.
+// One CTA of 128 threads per 128-row tile and split (blockIdx.z), the whole N
+// (64 or 256 columns) in one accumulator; the K range in chunks of 32, two
+// shared-memory stages: all threads convert and store chunk c + 1 while the
+// tensor core multiplies chunk c.  Thread 0 issues the MMAs; a commit per
+// chunk arrives on that stage's mbarrier, which the threads wait on (bounded)
+// before they overwrite the stage.  Epilogue: warp w reads accumulator lanes
+// 32w..32w+31 (its rows), 32 columns at a time.
+constexpr int kTcThreads = 128;
+constexpr int kTcKC = 32;  // K chunk (elements)
+
+template <typename TB>
+__host__ __device__ constexpr int tc_bpieces() { return std::is_same<TB, float>::value ? 3 : 1; }
+
+template <int NT, typename TB>
+__host__ __device__ constexpr size_t tc_smem_bytes()
+{
+    return 2 * (size_t)(3 * 128 + tc_bpieces<TB>() * NT) * kTcKC * 2 + 64;
+}
+
+__device__ __forceinline__ void tc_store_pieces(uint8_t* base, size_t piece_bytes, int r, int k,
+                                                float x, int npieces)
+{
+    const uint32_t off = umma::tile_off(r, 2 * k, 2 * kTcKC);
+    if (npieces == 1) {
+        *reinterpret_cast<uint16_t*>(base + off) = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+        return;
+    }
+    uint16_t h, m, l;
+    umma::split3_bf16(x, h, m, l);
+    *reinterpret_cast<uint16_t*>(base + off) = h;
+    *reinterpret_cast<uint16_t*>(base + piece_bytes + off) = m;
+    *reinterpret_cast<uint16_t*>(base + 2 * piece_bytes + off) = l;
+}
+
+template <typename TB, int NT, int EPI>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ GemmArgs<float, TB> g, int* __restrict__ err)
+{
+    constexpr int BP = tc_bpieces<TB>();
+    constexpr int NTERMS = BP == 3 ? 6 : 3;
+    constexpr size_t A_PIECE = (size_t)128 * kTcKC * 2, B_PIECE = (size_t)NT * kTcKC * 2;
+    constexpr size_t STAGE = 3 * A_PIECE + BP * B_PIECE;
+    constexpr uint32_t TCOLS = NT < 32 ? 32 : NT;
+    constexpr uint32_t ID = umma::idesc(128, NT, umma::kFmtBF16);
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
+    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(smem + 2 * STAGE + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * 128;
+    const int64_t kb = (int64_t)blockIdx.z * g.kc;
+    const int64_t ke = kb + g.kc < g.K ? kb + g.kc : g.K;
+    const int nchunks = ke > kb ? (int)((ke - kb + kTcKC - 1) / kTcKC) : 0;
+
+    if (tid == 0) {
+        umma::mbar_init(&mbar[0], 1);
+        umma::mbar_init(&mbar[1], 1);
+        umma::fence_mbar_init();
+    }
+    if (warp == 0) umma::tmem_alloc(s_taddr, TCOLS);
+    umma::tc_fence_before();
+    __syncthreads();
+    umma::tc_fence_after();
+    const uint32_t tmem = *s_taddr;
+    bool ok = true;
+
+    for (int c = 0; c < nchunks && ok; ++c) {
+        const int st = c & 1;
+        uint8_t* sa = smem + st * STAGE;
+        uint8_t* sb = sa + 3 * A_PIECE;
+        // the stage's previous MMAs (chunk c - 2) must be done before it is
+        // overwritten; every thread waits, and all agree on the outcome
+        if (c >= 2) ok = __syncthreads_and(umma::mbar_wait(&mbar[st], ((c - 2) >> 1) & 1) ? 1 : 0);
+        if (!ok) break;
+        const int64_t k0 = kb + (int64_t)c * kTcKC;
+        // A chunk: 128 rows x 32 k (walk the unit-stride index fastest)
+        for (int e = tid; e < 128 * kTcKC; e += kTcThreads) {
+            int r, k;
+            if (g.sak == 1) { r = e / kTcKC; k = e % kTcKC; } else { r = e % 128; k = e / 128; }
+            const int64_t m = m0 + r, kk = k0 + k;
+            const float x = (m < g.M && kk < ke) ? g.A[m * g.sam + kk * g.sak] : 0.0f;
+            tc_store_pieces(sa, A_PIECE, r, k, x, 3);
+        }
+        // B chunk: NT rows (n) x 32 k
+        for (int e = tid; e < NT * kTcKC; e += kTcThreads) {
+            int n, k;
+            if (g.sbk == 1) { n = e / kTcKC; k = e % kTcKC; } else { n = e % NT; k = e / NT; }
+            const int64_t kk = k0 + k;
+            const float x = (n < g.N && kk < ke) ? to_f(g.B[kk * g.sbk + n * g.sbn]) : 0.0f;
+            tc_store_pieces(sb, B_PIECE, n, k, x, BP);
+        }
+        umma::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            umma::tc_fence_after();
+            const uint32_t a0 = umma::smem_u32(sa), b0 = umma::smem_u32(sb);
+            constexpr int TA_[6] = {0, 0, 1, 0, 1, 2}, TB_[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+            for (int ks = 0; ks < kTcKC / 16; ++ks) {
+#pragma unroll
+                for (int t = 0; t < NTERMS; ++t) {
+                    const int pa = BP == 3 ? TA_[t] : t, pb = BP == 3 ? TB_[t] : 0;
+                    const uint64_t ad = umma::sdesc(a0 + (uint32_t)(pa * A_PIECE) + ks * 256, 128,
+                                                    kTcKC * 2 * 8);
+                    const uint64_t bd = umma::sdesc(b0 + (uint32_t)(pb * B_PIECE) + ks * 256, 128,
+                                                    kTcKC * 2 * 8);
+                    umma::mma_f16(tmem, ad, bd, ID, (c > 0 || ks > 0 || t > 0) ? 1u : 0u);
+                }
+            }
+            umma::mma_commit(&mbar[st]);
+        }
+    }
+    if (ok && nchunks > 0)
+        ok = __syncthreads_and(
+                 umma::mbar_wait(&mbar[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1) ? 1 : 0) != 0;
+    umma::tc_fence_after();
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+    } else {
+        float* C = g.C + (int64_t)blockIdx.z * g.M * g.N;
+        const int64_t m = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int n0 = 0; n0 < NT; n0 += 32) {
+            float v[32];
+            if (nchunks > 0) {
+                umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0.0f;
+            }
+            if (m < g.M) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t n = n0 + j;
+                    if (n >= g.N) continue;
+                    float x = v[j];
+                    if constexpr (EPI == EPI_BIAS_RELU) x = fmaxf(x + g.bias[n], 0.0f);
+                    if constexpr (EPI == EPI_BIAS) x += g.bias[n];
+                    if constexpr (EPI == EPI_MASK) x = g.mask[m * g.scm + n * g.scn] > 0.0f ? x : 0.0f;
+                    C[m * g.scm + n * g.scn] = x;
+                }
+            }
+        }
+    }
+    umma::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, TCOLS);
+}
+
+template <typename TB, int NT, int EPI>
+int tc_gemm(const GemmArgs<float, TB>& a, int splits, int* err, cudaStream_t st)
+{
+    if (a.M == 0 || a.N == 0) return FA_OK;
+    if (a.N > NT) return set_error(FA_ERR_UNSUPPORTED, "tc_gemm: N above the tile width");
+    GemmArgs<float, TB> g = a;
+    g.kc = (a.K + splits - 1) / splits;
+    g.kc = (g.kc + kTcKC - 1) / kTcKC * kTcKC;
+    auto kern = tc_gemm_kernel<TB, NT, EPI>;
+    constexpr size_t smem = tc_smem_bytes<NT, TB>();
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "tc_gemm: cudaFuncSetAttribute");
+    const dim3 grid((unsigned)((a.M + 127) / 128), 1, (unsigned)splits);
+    kern<<<grid, kTcThreads, smem, st>>>(g, err);
+    return cuda_error(cudaGetLastError(), "tc_gemm launch");
 }
 
 template <typename TA, typename TB, int OP, int EPI>
@@ -475,26 +654,27 @@ int mlp_forward_into(const fa_mlp* m, const float* X, int64_t B, float* H1, floa
     g.M = B; g.N = kDh; g.K = kDin; g.A = X; g.sam = kDin; g.sak = 1;
     g.B = m->pb + kOffW1; g.sbk = 1; g.sbn = kDin; g.C = H1; g.scm = kDh; g.scn = 1;
     g.bias = m->p + kOffB1;
-    int rc = gemm<float, __nv_bfloat16, OP_MUL, EPI_BIAS_RELU>(g, 1, st);
+    int rc = tc_gemm<__nv_bfloat16, kDh, EPI_BIAS_RELU>(g, 1, m->tc_err, st);
     if (rc != FA_OK) return rc;
     g.K = kDh; g.A = H1; g.sam = kDh; g.B = m->pb + kOffW2; g.sbn = kDh; g.C = H2;
     g.bias = m->p + kOffB2;
-    rc = gemm<float, __nv_bfloat16, OP_MUL, EPI_BIAS_RELU>(g, 1, st);
+    rc = tc_gemm<__nv_bfloat16, kDh, EPI_BIAS_RELU>(g, 1, m->tc_err, st);
     if (rc != FA_OK) return rc;
     g.N = kDout; g.A = H2; g.B = m->pb + kOffW3; g.sbn = kDh; g.C = Y; g.scm = kDout;
     g.bias = m->p + kOffB3;
-    return gemm<float, __nv_bfloat16, OP_MUL, EPI_BIAS>(g, 1, st);
+    return tc_gemm<__nv_bfloat16, kDout, EPI_BIAS>(g, 1, m->tc_err, st);
 }
 
 // dW (out x in) = gH^T X over R rows, and db = column sums of gH, through the
 // split-K partials in `part`
 int weight_grad(const float* gH, int64_t R, int out, const float* X, int in, float* dW,
-                float* db, const float* ones, float* part, cudaStream_t st)
+                float* db, const float* ones, float* part, int* tc_err, cudaStream_t st)
 {
     GemmArgs<float, float> g{};
     g.M = out; g.N = in; g.K = R; g.A = gH; g.sam = 1; g.sak = out; g.B = X; g.sbk = in; g.sbn = 1;
     g.C = part; g.scm = in; g.scn = 1;
-    int rc = gemm<float, float, OP_MUL, EPI_NONE>(g, kSplits, st);
+    int rc = in > 64 ? tc_gemm<float, 256, EPI_NONE>(g, kSplits, tc_err, st)
+                     : tc_gemm<float, 64, EPI_NONE>(g, kSplits, tc_err, st);
     if (rc != FA_OK) return rc;
     split_sum_kernel<<<(unsigned)((out * in + 255) / 256), 256, 0, st>>>(part, kSplits,
                                                                         (int64_t)out * in, dW);
@@ -532,6 +712,8 @@ int fa_mlp_create(fa_handle* h, uint64_t seed, fa_mlp** out)
     if (e == cudaSuccess) e = cudaMalloc(&m->v, fb);
     if (e == cudaSuccess) e = cudaMalloc(&m->g, fb);
     if (e == cudaSuccess) e = cudaMalloc(&m->pb, sizeof(__nv_bfloat16) * kNParams);
+    if (e == cudaSuccess) e = cudaMalloc(&m->tc_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(m->tc_err, 0, sizeof(int));
     if (e != cudaSuccess) {
         fa_mlp_destroy(m);
         return cuda_error(e, "fa_mlp_create");
@@ -557,6 +739,7 @@ int fa_mlp_destroy(fa_mlp* m)
     if (!m) return FA_OK;
     DeviceGuard g(m->h->device);
     cudaFree(m->p); cudaFree(m->m); cudaFree(m->v); cudaFree(m->g); cudaFree(m->pb);
+    cudaFree(m->tc_err);
     if (m->ws) cudaFree(m->ws);
     delete m;
     return FA_OK;
@@ -652,38 +835,43 @@ int fa_mlp_pair_grad(fa_mlp* m, const float* X, int64_t rows, const int64_t* pi,
     rc = cuda_error(cudaGetLastError(), "pair loss");
     if (rc != FA_OK) return rc;
     // layer 3
-    rc = weight_grad(gY, R, kDout, H2, kDh, m->g + kOffW3, m->g + kOffB3, ones, part, st);
+    rc = weight_grad(gY, R, kDout, H2, kDh, m->g + kOffW3, m->g + kOffB3, ones, part, m->tc_err,
+                     st);
     if (rc != FA_OK) return rc;
     {
         GemmArgs<float, __nv_bfloat16> g{};
         g.M = R; g.N = kDh; g.K = kDout; g.A = gY; g.sam = kDout; g.sak = 1;
         g.B = m->pb + kOffW3; g.sbk = kDh; g.sbn = 1; g.C = gH2; g.scm = kDh; g.scn = 1;
         g.mask = H2;
-        rc = gemm<float, __nv_bfloat16, OP_MUL, EPI_MASK>(g, 1, st);
+        rc = tc_gemm<__nv_bfloat16, kDh, EPI_MASK>(g, 1, m->tc_err, st);
         if (rc != FA_OK) return rc;
     }
     // layer 2
-    rc = weight_grad(gH2, R, kDh, H1, kDh, m->g + kOffW2, m->g + kOffB2, ones, part, st);
+    rc = weight_grad(gH2, R, kDh, H1, kDh, m->g + kOffW2, m->g + kOffB2, ones, part, m->tc_err,
+                     st);
     if (rc != FA_OK) return rc;
     {
         GemmArgs<float, __nv_bfloat16> g{};
         g.M = R; g.N = kDh; g.K = kDh; g.A = gH2; g.sam = kDh; g.sak = 1;
         g.B = m->pb + kOffW2; g.sbk = kDh; g.sbn = 1; g.C = gH1; g.scm = kDh; g.scn = 1;
         g.mask = H1;
-        rc = gemm<float, __nv_bfloat16, OP_MUL, EPI_MASK>(g, 1, st);
+        rc = tc_gemm<__nv_bfloat16, kDh, EPI_MASK>(g, 1, m->tc_err, st);
         if (rc != FA_OK) return rc;
     }
     // layer 1
-    rc = weight_grad(gH1, R, kDh, Xp, kDin, m->g + kOffW1, m->g + kOffB1, ones, part, st);
+    rc = weight_grad(gH1, R, kDh, Xp, kDin, m->g + kOffW1, m->g + kOffB1, ones, part, m->tc_err,
+                     st);
     if (rc != FA_OK) return rc;
     if (grad) {
         e = cudaMemcpyAsync(grad, m->g, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_error(e, "fa_mlp_pair_grad copy");
     }
-    int hbad = 0;
+    int hbad = 0, htc = 0;
     e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&htc, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_error(e, "fa_mlp_pair_grad");
+    if (htc) return set_error(FA_ERR_CUDA, "fa_mlp_pair_grad: a tensor-core wait timed out");
     if (hbad) return set_error(FA_ERR_INVALID_ARG, "fa_mlp_pair_grad: pair index out of range");
     return FA_OK;
 }

@@ -17,11 +17,11 @@
 //      elimination of the interior with the chunk's two
 //      neighbouring interface nodes (the last node of the previous chunk and
 //      of this chunk) kept as unknowns: M_i = y_i - I_{j-1} g_i - I_j k_i.
-//   C. a backward sweep without stores gives y, g, k at the first interior
-//      node; eliminating the interiors leaves a cyclic tridiagonal system in
-//      the P interface values, solved by parallel cyclic reduction with warp
-//      shuffles.
-//   D. a second backward sweep writes M for every node.
+//   C. the same sweep accumulates the first interior node's back-substitution
+//      coefficients (y, g, k); eliminating the interiors leaves a cyclic
+//      tridiagonal system in the P interface values, solved by parallel
+//      cyclic reduction with warp shuffles.
+//   D. a backward sweep writes M for every node.
 //   E. the spline is evaluated at t_k = k/N_out (each lane a contiguous block
 //      of outputs; interval search by integer compares on the knots; the
 //      chord vectors p_{l+1} - p_l of step A are kept for B and E; the
@@ -57,17 +57,19 @@ struct Ws {
     double2* Z;    // raw outputs before normalisation  [C*N_out] (FP32 output only)
 };
 
-// ---- reciprocal square root and reciprocal by one Newton-Raphson step -------
+// ---- reciprocal square root, reciprocal and square root by one Newton step ---
 // The FP32 seed is built from the double's bits with integer instructions, the
-// FP32 hardware approximation (rsqrtf / __frcp_rn) refines it to ~2^-22, and
-// one FP64 Newton-Raphson step (Newton's method on f(y) = 1/y^2 - q, resp.
-// f(r) = 1/r - x) squares the relative error to below 2e-13 (rsqrt) and 1e-13
-// (reciprocal) -- three and two FP64 instructions instead of a full-precision
-// sequence.  The chord lengths, their reciprocals, the pivots and the
-// perimeter need no more: their errors move the resampled nodes by < 2e-13 of
-// the curve length, inside the 1e-12 parity bound.  Valid for positive
-// normal inputs within the FP32 exponent range, which chords, perimeters and
-// pivots of curves of reasonable size are; other inputs take the CUDA call.
+// FP32 hardware approximation (rsqrtf / __frcp_rn / __fsqrt_rn) refines it to
+// ~2^-22, and one Newton-Raphson step (Newton's method on f(y) = 1/y^2 - q,
+// f(r) = 1/r - x, f(s) = s^2 - q) squares the relative error to below 1e-13.
+// FP64 is the scarce unit on this part (1/64 of the FP32 rate), so the steps
+// keep their FP64 instructions to one or two, doing the rest with float-float
+// and integer arithmetic (see each function).  The chord lengths, their
+// reciprocals, the pivots and the perimeter need no more: their errors move
+// the resampled nodes by < 2e-13 of the curve length, inside the 1e-12 parity
+// bound.  Valid for positive normal inputs of moderate exponent, which
+// chords, perimeters and pivots of curves of reasonable size are; other
+// inputs take the CUDA call.
 __device__ __forceinline__ bool f32_range(double x)
 {
     const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
@@ -85,32 +87,95 @@ __device__ __forceinline__ double widen_f32(float f)  // exact float -> double b
     const unsigned long long e = ((u >> 23) & 0xff) - 127 + 1023;
     return __longlong_as_double((long long)((e << 52) | ((unsigned long long)(u & 0x7fffff) << 29)));
 }
+// float -> double by bits for any finite sign (zero and subnormal floats give 0)
+__device__ __forceinline__ double widen_any(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned ef = (u >> 23) & 0xff;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned long long mag =
+        ef == 0 ? 0ull
+                : ((unsigned long long)(ef - 127 + 1023) << 52) | ((unsigned long long)(u & 0x7fffff) << 29);
+    return __longlong_as_double((long long)(sign | mag));
+}
+// exponent range in which a double splits into two normal floats (see split_pos)
+__device__ __forceinline__ bool split_range(double x)
+{
+    const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+    return e > -70 && e < 120;
+}
+// x = xh + xl to 2^-47 relative: xh the top 24 significand bits (truncated),
+// xl the next 24 bits (rounded), both from the bits with integer instructions
+// (x > 0 inside split_range, where both parts are normal floats).
+__device__ __forceinline__ void split_pos(double x, float& xh, float& xl)
+{
+    xh = seed_f32(x);
+    const long long b = __double_as_longlong(x);
+    const int fe = (int)((b >> 52) & 0x7ff) - 1023 + 127;  // float exponent field of x
+    const int m = (int)(b & 0x1fffffff);                    // the 29 bits below xh
+    xl = fe > 52 ? __fmul_rn(__int2float_rn(m), __uint_as_float((unsigned)(fe - 52) << 23)) : 0.0f;
+}
+// The residual 1 - x y^2 (y a float near x^{-1/2}) or 1 - x y (y near 1/x),
+// evaluated in float-float arithmetic (Dekker's exact product by FMA, then
+// float sums whose operands nearly cancel): the residual is about 2^-22 and
+// comes out with an absolute error near 2^-47, i.e. to about 2^-25 of itself,
+// which is all one Newton-Raphson step needs.
+__device__ __forceinline__ float resid_rsqrt(float xh, float xl, float y)
+{
+    const float yy = __fmul_rn(y, y), yye = __fmaf_rn(y, y, -yy);  // y^2 = yy + yye exactly
+    const float p = __fmul_rn(xh, yy), pe = __fmaf_rn(xh, yy, -p);  // xh yy = p + pe exactly
+    const float t = __fmaf_rn(xh, yye, __fmaf_rn(xl, yy, pe));      // the small products
+    return __fsub_rn(__fsub_rn(1.0f, p), t);                        // 1 - p is exact (p ~ 1)
+}
+__device__ __forceinline__ float resid_rcp(float xh, float xl, float y)
+{
+    const float p = __fmul_rn(xh, y), pe = __fmaf_rn(xh, y, -p);
+    return __fsub_rn(__fsub_rn(1.0f, p), __fmaf_rn(xl, y, pe));
+}
+// 1/sqrt(q) and 1/x by one Newton-Raphson step from an FP32 seed, the step's
+// residual in float-float and its single FP64 instruction the final add:
+// y0 + (y0/2) e with e = 1 - q y0^2 (rsqrt), r0 + r0 e with e = 1 - x r0 (rcp).
+// The seed's relative error e0 <= 2^-22 leaves 1.5 e0^2 < 9e-14 (rsqrt) and
+// e0^2 < 6e-14 (rcp) after the step, plus about 2^-46 from the residual.
 __device__ __forceinline__ double rsqrt_nr(double q)
 {
-    if (!f32_range(q)) return rsqrt(q);
-    const float y0f = rsqrtf(seed_f32(q));
-    const double y0 = widen_f32(y0f), h0 = widen_f32(0.5f * y0f);
-    const double e = fma(-q * y0, y0, 1.0);  // 1 - q y0^2
-    return fma(h0, e, y0);
-}
-// sqrt(q) = q rsqrt(q) corrected by one Newton-Raphson step on s^2 = q with
-// the FP32 seed's half reciprocal root as the step's divisor: with y0 =
-// q^{-1/2}(1 + e), s0 = q y0, the result s0 + (y0 / 2)(q - s0^2) has relative
-// error -1.5 e^2 + O(e^3), the same as q * rsqrt_nr(q), in one FP64 instruction
-// less.  Valid for q > 0 (same range rule as rsqrt_nr).
-__device__ __forceinline__ double sqrt_nr(double q)
-{
-    if (!f32_range(q)) return sqrt(q);
-    const float y0f = rsqrtf(seed_f32(q));
-    const double y0 = widen_f32(y0f), h0 = widen_f32(0.5f * y0f);
-    const double s0 = q * y0;
-    return fma(h0, fma(-s0, s0, q), s0);
+    if (!split_range(q)) return rsqrt(q);
+    float qh, ql;
+    split_pos(q, qh, ql);
+    const float y0f = rsqrtf(qh);
+    const float e = resid_rsqrt(qh, ql, y0f);
+    return widen_f32(y0f) + widen_any(__fmul_rn(__fmul_rn(0.5f, y0f), e));
 }
 __device__ __forceinline__ double rcp_nr(double x)
 {
-    if (__double_as_longlong(x) <= 0 || !f32_range(x)) return __drcp_rn(x);
-    const double r0 = widen_f32(__frcp_rn(seed_f32(x)));
-    return fma(r0, fma(-x, r0, 1.0), r0);
+    if (__double_as_longlong(x) <= 0 || !split_range(x)) return __drcp_rn(x);
+    float xh, xl;
+    split_pos(x, xh, xl);
+    const float r0 = __frcp_rn(xh);
+    const float e = resid_rcp(xh, xl, r0);
+    return widen_f32(r0) + widen_any(__fmul_rn(r0, e));
+}
+// sqrt(q) from the correctly rounded FP32 square root of q's leading float
+// (relative error <= 2^-23) and one Newton-Raphson step s0 + (q - s0^2)/(2 s0)
+// whose divisor is taken in FP32: relative error below 2^-45.  Two FP64
+// instructions.  Valid for q > 0 inside f32_range.
+__device__ __forceinline__ double sqrt_nr(double q)
+{
+    if (!f32_range(q)) return sqrt(q);
+    const float s0f = __fsqrt_rn(seed_f32(q));
+    const double s0 = widen_f32(s0f);
+    return fma(fma(-s0, s0, q), widen_f32(__fdiv_rn(0.5f, s0f)), s0);
+}
+// 2x for x >= 0 with integer instructions only (exact; subnormals shift,
+// normals step the exponent, the largest binade goes to +Inf, Inf/NaN stay)
+__device__ __forceinline__ double twice_pos(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned e = (unsigned)(b >> 52);
+    const unsigned long long r = e == 0 ? b << 1
+                                 : e < 0x7feu ? b + (1ull << 52)
+                                 : e == 0x7feu ? 0x7ff0000000000000ull : b;
+    return __longlong_as_double((long long)r);
 }
 
 __device__ __forceinline__ double2 d2(double x, double y) { return make_double2(x, y); }
@@ -247,10 +312,18 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     // tau_{l-1}); the evaluation uses h^2 M' = h^2 M / (6 L^2).  The first
     // row needs no special case: with c' = 0, y' = 0, g' = -1 the general
     // recurrence gives exactly den = B, y' = R / B, g' = h_{l-1} / B.
+    // Back substitution M_i = y'_i - c'_i M_{i+1} - g'_i I_{j-1} (M_{e_j} = I_j)
+    // gives the first interior node as
+    //   M_{s_j} = sum_i pi_i (y'_i - g'_i I_{j-1}) + pi_{e_j} I_j,
+    //   pi_i = prod_{m = s_j}^{i-1} (-c'_m),
+    // so the sweep also accumulates yF = sum pi_i y'_i, gF = sum pi_i g'_i and
+    // kF = -pi_{e_j}: M_{s_j} = yF - gF I_{j-1} - kF I_j (no second pass).
     // interface-node equation data kept for the reduced system
     double Ae = 0, Be = 0, Ce = 0;
     double2 Re = d2(0, 0), yL = d2(0, 0);
     double gL = 0, kL = 0;
+    double2 yF = d2(0, 0);
+    double gF = 0, kF = 0;
     if (act) {
         const double* __restrict__ Dr = D;
         const double* __restrict__ IHr = IH;
@@ -264,6 +337,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         double S = base;
         double cp = 0, gp = -1.0;
         double2 yp = d2(0, 0);
+        double pi = 1.0;
         // operands of the next row, loaded one row ahead
         double h = Dr[sj], ih = IHr[sj];
         double2 cv = CVr[sj];
@@ -274,7 +348,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             S += h;
             const double2 tau = scl2(cv, ih);
             const double2 R = sub2(tau, tprev);
-            const double B = 2.0 * (hprev + h);
+            const double B = twice_pos(hprev + h);
             const double den = fma(-hprev, cp, B);
             const double r = rcp_nr(den);
             const double ncp = h * r;
@@ -282,10 +356,14 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             const double ngp = -hprev * gp * r;
             F0r[i] = d2(ncp, ngp);
             F1r[i] = nyp;
+            yF = d2(fma(pi, nyp.x, yF.x), fma(pi, nyp.y, yF.y));
+            gF = fma(pi, ngp, gF);
+            pi *= -ncp;
             cp = ncp; gp = ngp; yp = nyp;
             hprev = h; tprev = tau;
             h = hn; ih = ihn; cv = cvn;
         }
+        kF = -pi;
         // last interior node's values: M_L = y'_L - I_{j-1} g'_L - I_j c'_L
         yL = yp; gL = gp; kL = cp;
         // interface node e_j (the loop, which runs at least once, leaves h,
@@ -295,21 +373,9 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         Re = sub2(tau, tprev);
         Ae = hprev;
         Ce = h;
-        Be = 2.0 * (hprev + Ce);
+        Be = twice_pos(hprev + Ce);
     }
 
-    // ---- C: backward sweep (no stores) for the first interior node ----------
-    double2 yF = yL;
-    double gF = gL, kF = kL;
-    if (act) {
-        for (int i = ej - 2; i >= sj; --i) {
-            const double2 f0 = F0[i];
-            const double2 f1 = F1[i];
-            yF = d2(fma(-f0.x, yF.x, f1.x), fma(-f0.x, yF.y, f1.y));
-            gF = fma(-f0.x, gF, f0.y);
-            kF = -f0.x * kF;
-        }
-    }
     // reduced cyclic system over the P interfaces:
     //   al I_{j-1} + be I_j + ga I_{j+1} = de
     const int nxt = (lane + 1) & (P - 1);
@@ -399,12 +465,13 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             const double2 pl = __ldg(p + l), cv = CV[l];  // cv = p_{l+1} - p_l
             const double2 Ml = M[l], Mn = M[ln];
             const double d = D[l];
-            const double b = (st - U[l]) * IH[l];  // (t - u_l) / h_l
-            const double h6 = d * d;  // h^2 M / 6 = d^2 M' (M' = M / (6 L^2))
-            // cubic weights a(a^2 - 1) h6 and b(b^2 - 1) h6 (a = 1 - b) from
-            // w = b(b - 1) h6 = -ab h6: the second is w(1 + b), the first
-            // w(2 - b) = 3w - w(1 + b)  (5 FP64 instructions instead of 8)
-            const double w = fma(b, b, -b) * h6;
+            const double u = st - U[l];  // arc length into the interval
+            const double b = u * IH[l];  // (t - u_l) / h_l
+            // cubic weights a(a^2 - 1) h6 and b(b^2 - 1) h6 (a = 1 - b, h6 =
+            // h^2 M / 6 / M' = d^2 with M' = M / (6 L^2)) from
+            // w = b(b - 1) h6 = -ab h6 = u (u - d): the second is w(1 + b), the
+            // first w(2 - b) = 3w - w(1 + b)  (4 FP64 instructions instead of 8)
+            const double w = u * (u - d);
             const double cb = fma(w, b, w);
             const double ca = fma(w, 3.0, -cb);
             const double2 S = d2(fma(ca, Ml.x, fma(cb, Mn.x, fma(b, cv.x, pl.x))),
@@ -462,7 +529,8 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
 
 // Persistent grid: each warp takes the next curve from a counter until none is
 // left (curve sizes differ, so a fixed assignment would leave the last wave of
-// CTAs as a tail).
+// CTAs as a tail).  The curves are taken in input order: handing out long
+// curves first measured slower (more workspace in flight at once).
 template <bool F32OUT>
 __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
     resample_kernel(const double2* __restrict__ pts, const int64_t* __restrict__ offsets,
@@ -493,7 +561,8 @@ size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags)
     if (C > kMax || n_pts > kMax || N_out > (1 << 20)) return SIZE_MAX;
     const size_t np = (size_t)(n_pts > 0 ? n_pts : 0);
     size_t b = 3 * align256(np * sizeof(double)) + 3 * align256(np * sizeof(double2));
-    if (flags & FA_STORE_FP32) b += align256((size_t)(C > 0 ? C : 0) * (size_t)N_out * sizeof(double2));
+    const size_t c = (size_t)(C > 0 ? C : 0);
+    if (flags & FA_STORE_FP32) b += align256(c * (size_t)N_out * sizeof(double2));
     return b + 256;  // the work counter
 }
 
