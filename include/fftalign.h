@@ -67,7 +67,7 @@ typedef struct fa_handle fa_handle;
 #define FA_FFT 0    /* Algorithm 2 with the convolution theorem: O(N log N)   */
 #define FA_DIRECT 1 /* every shift by its O(N) definition: O(N^2) baseline    */
 
-/* arithmetic of the shift search (theta and the energy are always FP64) */
+/* arithmetic of the shift search (theta and the energy have FP64 accuracy) */
 #define FA_PREC_FP64 0  /* every step in FP64                                  */
 #define FA_PREC_MIXED 1 /* FA_FFT only: the three transforms in double-float
                            arithmetic (pairs of floats, ~48-bit significands)
@@ -77,6 +77,19 @@ typedef struct fa_handle fa_handle;
                            result obeys the same bounds as FA_PREC_FP64.
                            Coordinates must lie within [2^-74, 2^128) in
                            magnitude (or be 0): unit-length curves do        */
+/* fa_align_all_pairs only, N = 256 or 512: the search as a dense GEMM on the
+ * tensor cores (tcgen05; the DFT of every cross-spectrum Z_i conj(Z_j), Sec. 2),
+ * float32 accumulation, the 8 shifts of largest |c|^2 kept per pair, those 8
+ * re-scored by their direct correlation in double-float arithmetic (~1e-14),
+ * theta and the energy at the winner likewise (FP64-bound accuracy).  The
+ * operands enter the tensor core as:                                        */
+#define FA_PREC_TC_BF16X3 2 /* bfloat16 hi + lo pieces, 3 products (~16 bits) */
+#define FA_PREC_TC_FP16X3 3 /* float16 hi + lo pieces, 3 products (~22 bits)  */
+#define FA_PREC_TC_TF32 4   /* one TF32 product (~11 bits)                     */
+#define FA_PREC_TC_TF32X3 5 /* TF32 hi + lo pieces, 3 products (~21 bits)      */
+/* A pair whose best shift lies outside its 8 candidates gets the best of
+ * them: the reduced operand precision decides how often that happens (the
+ * tests and the benchmark report the agreement with FA_PREC_FP64).           */
 
 /* key types of fa_select_k */
 #define FA_KEY_F32 0
@@ -183,7 +196,10 @@ int fa_align_pairs(fa_handle* h, const void* z1, const void* z2, int64_t P, int3
  *              centred and of unit length
  *   M          number of curves, in [0, 65536]
  *   N          nodes per curve, a power of two in [4, 4096]
- *   prec       FA_PREC_FP64 or FA_PREC_MIXED (search in double-float)
+ *   prec       FA_PREC_FP64, FA_PREC_MIXED (search in double-float) or
+ *              FA_PREC_TC_* (search on the tensor cores, N = 256 or 512 and
+ *              2 <= M: the workspace is then
+ *              fa_align_all_pairs_workspace_size_prec(M, N, prec) bytes)
  *   shift      int32[M*M], theta double[M*M], energy double[M*M] (device)
  *   status     int8[M] per-curve status (FA_STATUS_OK or _NONFINITE); rows and
  *              columns of a non-finite curve get shift -1 and NaN
@@ -191,6 +207,11 @@ int fa_align_pairs(fa_handle* h, const void* z1, const void* z2, int64_t P, int3
  *              bytes (M*N*16), 256-byte aligned, or NULL for the handle's
  */
 size_t fa_align_all_pairs_workspace_size(int64_t M, int32_t N);
+/* workspace of fa_align_all_pairs for a given precision: M*N*16 bytes for
+ * FA_PREC_FP64 and FA_PREC_MIXED; for FA_PREC_TC_* the spectra in FP64 and
+ * complex64, the split DFT matrix (4 MB at N = 512) and 16 bytes per ordered
+ * pair for the candidates (M*M*16); 0 for unsupported arguments */
+size_t fa_align_all_pairs_workspace_size_prec(int64_t M, int32_t N, int32_t prec);
 int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_t ztype,
                        int32_t prec, int32_t* shift, double* theta, double* energy,
                        int8_t* status, void* workspace, size_t workspace_bytes, void* stream);

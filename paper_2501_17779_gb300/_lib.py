@@ -31,12 +31,17 @@ FFT = 0
 DIRECT = 1
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_TC_BF16X3 = 2
+PREC_TC_FP16X3 = 3
+PREC_TC_TF32 = 4
+PREC_TC_TF32X3 = 5
 
 EXPORTS = (
     "fa_create", "fa_destroy", "fa_last_error", "fa_version",
     "fa_resample_workspace_size", "fa_resample_arclength", "fa_align_pairs",
     "fa_align_curves_host", "fa_resample_arclength_noalloc",
-    "fa_align_all_pairs_workspace_size", "fa_align_all_pairs",
+    "fa_align_all_pairs_workspace_size", "fa_align_all_pairs_workspace_size_prec",
+    "fa_align_all_pairs",
     "fa_align_pairs_ragged_workspace_size", "fa_align_pairs_ragged",
     "fa_align_pairs_ragged_autotune", "fa_elastic_workspace_size", "fa_elastic_distance",
     "fa_fourier_descriptors", "fa_column_stats", "fa_standardize", "fa_embed_sqdist",
@@ -94,6 +99,8 @@ def load(build_if_missing: bool = False):
     L.fa_align_curves_host.restype = ctypes.c_int
     L.fa_align_all_pairs_workspace_size.argtypes = [i64, i32]
     L.fa_align_all_pairs_workspace_size.restype = sz
+    L.fa_align_all_pairs_workspace_size_prec.argtypes = [i64, i32, i32]
+    L.fa_align_all_pairs_workspace_size_prec.restype = sz
     L.fa_align_all_pairs.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, vp, sz, vp]
     L.fa_align_all_pairs.restype = ctypes.c_int
     L.fa_align_pairs_ragged_workspace_size.argtypes = [vp, i64, i32]

@@ -101,7 +101,9 @@ def resample_arclength(pts: torch.Tensor, offsets: torch.Tensor, N_out: int, *,
 
 
 _METHODS = {"fft": _lib.FFT, "direct": _lib.DIRECT}
-_PRECS = {"fp64": _lib.PREC_FP64, "mixed": _lib.PREC_MIXED}
+_PRECS = {"fp64": _lib.PREC_FP64, "mixed": _lib.PREC_MIXED, "tc_bf16x3": _lib.PREC_TC_BF16X3,
+          "tc_fp16x3": _lib.PREC_TC_FP16X3, "tc_tf32": _lib.PREC_TC_TF32,
+          "tc_tf32x3": _lib.PREC_TC_TF32X3}
 
 
 def align_pairs(z1: torch.Tensor, z2: torch.Tensor, *, method: str = "fft", prec: str = "fp64",
@@ -139,9 +141,11 @@ def align_pairs(z1: torch.Tensor, z2: torch.Tensor, *, method: str = "fft", prec
 def align_all_pairs(z: torch.Tensor, *, prec: str = "fp64", workspace: torch.Tensor | None = None):
     """Alignment matrix of M curves (fa_align_all_pairs).
 
-    z: [M, N] complex128 or complex64 CUDA tensor.  Returns (shift int32 [M, M],
-    theta float64 [M, M], energy float64 [M, M], status int8 [M]); entry
-    (i, j) aligns curve j onto curve i.
+    z: [M, N] complex128 or complex64 CUDA tensor.  prec: "fp64", "mixed", or
+    a tensor-core search "tc_bf16x3", "tc_fp16x3", "tc_tf32", "tc_tf32x3"
+    (N = 256 or 512).  Returns (shift int32 [M, M], theta float64 [M, M],
+    energy float64 [M, M], status int8 [M]); entry (i, j) aligns curve j onto
+    curve i.
     """
     if z.dtype not in (torch.complex128, torch.complex64):
         raise ValueError("z must be complex128 or complex64")
@@ -155,7 +159,7 @@ def align_all_pairs(z: torch.Tensor, *, prec: str = "fp64", workspace: torch.Ten
     energy = torch.empty((M, M), dtype=torch.float64, device=dev)
     status = torch.empty(M, dtype=torch.int8, device=dev)
     L = _lib.load()
-    need = int(L.fa_align_all_pairs_workspace_size(M, N))
+    need = int(L.fa_align_all_pairs_workspace_size_prec(M, N, _PRECS[prec]))
     if workspace is None:
         workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     ztype = _lib.Z_F64 if z.dtype == torch.complex128 else _lib.Z_F32

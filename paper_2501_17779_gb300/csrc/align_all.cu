@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
 }
 
 template <int LOGN, typename ZT>
-int launch_all(const fa_handle* h, const void* z, int64_t M, double2* spec, int8_t* status,
-               int32_t* shift, double* theta, double* energy, cudaStream_t st)
+int launch_spec(const fa_handle* h, const void* z, int64_t M, double2* spec, int8_t* status,
+                int32_t* shift, double* theta, double* energy, cudaStream_t st)
 {
     using Gm = Geo<LOGN>;
     const double2* W = h->tf64[LOGN];
@@ -193,7 +193,19 @@ int launch_all(const fa_handle* h, const void* z, int64_t M, double2* spec, int8
         const int64_t groups = (M + 1) / 2;
         kern<<<(unsigned)((groups + Gm::G - 1) / Gm::G), Gm::T, smem, st>>>(zz, M, W, spec, status,
                                                                             shift, theta, energy);
-        const int rc = cuda_error(cudaGetLastError(), "spectra launch");
+        return cuda_error(cudaGetLastError(), "spectra launch");
+    }
+}
+
+template <int LOGN, typename ZT>
+int launch_all(const fa_handle* h, const void* z, int64_t M, double2* spec, int8_t* status,
+               int32_t* shift, double* theta, double* energy, cudaStream_t st)
+{
+    using Gm = Geo<LOGN>;
+    const double2* W = h->tf64[LOGN];
+    const ZT* zz = static_cast<const ZT*>(z);
+    {
+        const int rc = launch_spec<LOGN, ZT>(h, z, M, spec, status, shift, theta, energy, st);
         if (rc != FA_OK) return rc;
     }
     const int64_t npairs = M * (M - 1) / 2;
@@ -228,6 +240,24 @@ int dispatch(const fa_handle* h, const void* z, int64_t M, int logn, double2* sp
 }  // namespace
 
 size_t align_all_ws_bytes(int64_t M, int N) { return (size_t)M * (size_t)N * sizeof(double2); }
+
+int launch_spectra(const fa_handle* h, const void* z, int64_t M, int logn, int ztype,
+                   double2* spec, int8_t* status, int32_t* shift, double* theta, double* energy,
+                   cudaStream_t st)
+{
+    if (M == 0) return FA_OK;
+    switch (logn) {
+#define FA_CASE(L)                                                                          \
+    case L:                                                                                 \
+        return ztype == FA_Z_F64                                                            \
+                   ? launch_spec<L, double2>(h, z, M, spec, status, shift, theta, energy, st) \
+                   : launch_spec<L, float2>(h, z, M, spec, status, shift, theta, energy, st);
+        FA_CASE(2) FA_CASE(3) FA_CASE(4) FA_CASE(5) FA_CASE(6) FA_CASE(7) FA_CASE(8) FA_CASE(9)
+        FA_CASE(10) FA_CASE(11) FA_CASE(12)
+#undef FA_CASE
+    }
+    return set_error(FA_ERR_UNSUPPORTED, "spectra: unsupported N");
+}
 
 int launch_align_all(const fa_handle* h, const void* z, int64_t M, int logn, int ztype, void* ws,
                      int8_t* status, int32_t* shift, double* theta, double* energy,

@@ -1,0 +1,592 @@
+// align_all_tc.cu -- fa_align_all_pairs with the shift search on the tensor
+// cores: the DFT of every cross-spectrum as one dense GEMM (tcgen05), the
+// best 8 shifts per pair kept in the epilogue, those 8 re-scored exactly, and
+// theta / energy at the winner.
+//
+// For curves i < j with spectra Z = DFT(z) (Sec. 2, convolution theorem),
+//   c_ij(s) = sum_k z_i[k] conj(z_j[k+s]) = (1/N) sum_f P_ij[f] e^{-2 pi i f s / N},
+//   P_ij[f] = Z_i[f] conj(Z_j[f]),
+// so the correlations of all pairs are the product of the matrix of
+// cross-spectra (one row per pair, 2N real columns: Re P, Im P per f) with a
+// fixed real DFT matrix B (2N x 2N: columns Re c(s), Im c(s)):
+//   Re c = sum_f Re P cos + Im P sin,   Im c = sum_f Im P cos - Re P sin
+// (angle 2 pi f s / N).  C[i,j,s] is never stored: each CTA holds 128 pairs
+// (one i, 128 consecutive j) in tensor memory, 128 shifts (256 columns) at a
+// time, and keeps every pair's 8 largest |c(s)|^2 (smallest s first on ties)
+// in registers.
+//
+// Precision variants (operands rounded to the tensor core's input type, float32
+// accumulation in tensor memory):
+//   BF16X3  each operand as bfloat16 hi + lo pieces, products hi hi + hi lo +
+//           lo hi (about 16 significant bits)
+//   FP16X3  the same with float16 pieces (about 22 bits; the cross-spectra
+//           are scaled by 2^14 so that their pieces stay in float16 range)
+//   TF32    one TF32 product (about 11 bits)
+//   TF32X3  TF32 hi + lo pieces, three products (about 21 bits)
+// The 8 candidates of each pair are then re-scored by their direct O(N)
+// correlation in float-float arithmetic (about 48 bits, rel. error ~1e-14),
+// the largest |c(s)|^2 wins (smallest s on ties), theta = arg c(s*) and the
+// energy of Eq. disc-energy by its definition, both at FP64-bound accuracy.
+//
+// GEMM kernel: one CTA of 128 threads per SM, persistent over (i, j-tile)
+// tiles from an atomic counter; per tile, per 128-shift column block, the
+// 2N-long contraction runs in chunks of 64 bytes per row (32 f16 or 16 tf32
+// elements) through three shared-memory stages.  Per chunk: thread 0 starts a
+// bulk copy (cp.async.bulk, completion on an mbarrier) of the pre-tiled DFT
+// block, every thread forms its pair's cross-spectrum piece row (FP32 from the
+// complex64 spectra), thread 0 issues the MMAs and commits them to the stage's
+// mbarrier.  All waits are bounded; a wait that runs out sets an error flag
+// that turns every output of the call into NaN.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "align_common.cuh"
+#include "df.cuh"
+#include "umma.cuh"
+
+namespace fa {
+namespace {
+
+constexpr int kTcT = 128;      // threads per CTA = pairs per tile = TMEM lanes
+constexpr int kRowB = 64;      // bytes per operand row per K chunk
+constexpr int kStages = 3;
+constexpr int kCand = 8;       // candidate shifts kept per pair
+constexpr float kPScale = 16384.0f;  // 2^14: cross-spectra scale (float16 range)
+
+template <int V>
+struct TcVar;
+template <>
+struct TcVar<FA_PREC_TC_BF16X3> {
+    static constexpr int ES = 2, NP = 2;
+    static constexpr uint32_t FMT = 1;  // bfloat16 (kind::f16)
+    static constexpr bool TF32 = false;
+};
+template <>
+struct TcVar<FA_PREC_TC_FP16X3> {
+    static constexpr int ES = 2, NP = 2;
+    static constexpr uint32_t FMT = 0;  // float16 (kind::f16)
+    static constexpr bool TF32 = false;
+};
+template <>
+struct TcVar<FA_PREC_TC_TF32> {
+    static constexpr int ES = 4, NP = 1;
+    static constexpr uint32_t FMT = 2;  // tf32 (kind::tf32)
+    static constexpr bool TF32 = true;
+};
+template <>
+struct TcVar<FA_PREC_TC_TF32X3> {
+    static constexpr int ES = 4, NP = 2;
+    static constexpr uint32_t FMT = 2;
+    static constexpr bool TF32 = true;
+};
+
+// round a float to TF32 (10 fraction bits), to nearest even
+__device__ __forceinline__ uint32_t tf32_rn(float x)
+{
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u;
+    u += 0xfffu + ((u >> 13) & 1u);
+    return u & 0xffffe000u;
+}
+
+// x as NP pieces of the variant's element type (bit patterns, 16 or 32 bits)
+template <int V>
+__device__ __forceinline__ void to_pieces(float x, uint32_t& hi, uint32_t& lo)
+{
+    using T = TcVar<V>;
+    if constexpr (T::TF32) {
+        hi = tf32_rn(x);
+        lo = T::NP > 1 ? tf32_rn(__fsub_rn(x, __uint_as_float(hi))) : 0u;
+    } else if constexpr (T::FMT == 1) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(__fsub_rn(x, __bfloat162float(h))));
+    } else {
+        const __half h = __float2half_rn(x);
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(__float2half_rn(__fsub_rn(x, __half2float(h))));
+    }
+}
+
+// start of row i of the upper triangle in the pair enumeration
+__device__ __forceinline__ int64_t tri_start_tc(int64_t i, int64_t M) { return i * (2 * M - i - 1) / 2; }
+
+// sum_{a=1}^{n} ceil(a / 128): the j-tiles of rows i' < i are F(M-1) - F(M-1-i)
+__host__ __device__ __forceinline__ int64_t ceil_sum128(int64_t n)
+{
+    if (n <= 0) return 0;
+    // sum_{a=1}^{n} ceil(a/q) = sum_{b=0}^{n-1} (floor(b/q) + 1)
+    const int64_t q = 128, k = (n - 1) / q;  // floor((n-1)/q)
+    return n + q * k * (k - 1) / 2 + k * (n - 1 - q * k + 1);
+}
+
+// ---- the pre-tiled DFT matrix ------------------------------------------------
+// Block (cb, kc) holds column block cb (256 columns: Re c(s), Im c(s) for
+// s = 128 cb .. 128 cb + 127) and K chunk kc (64 bytes per row), NP pieces,
+// each piece 256 rows x 64 bytes in the K-major core-matrix layout, so that
+// one bulk copy fills a stage.
+template <int V, int LOGN>
+__global__ void dft_tab_kernel(uint8_t* __restrict__ tab)
+{
+    using T = TcVar<V>;
+    constexpr int N = 1 << LOGN, KC = kRowB / T::ES, NK = 2 * N / KC;
+    constexpr size_t PIECE = (size_t)256 * kRowB, BLOCK = PIECE * T::NP;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (cb, kc, row, k)
+    const int64_t total = (int64_t)(N / 128) * NK * 256 * KC;
+    if (e >= total) return;
+    const int k = (int)(e % KC);
+    const int row = (int)((e / KC) % 256);
+    const int kc = (int)((e / (KC * 256)) % NK);
+    const int cb = (int)(e / ((int64_t)KC * 256 * NK));
+    const int s = cb * 128 + (row & 127);
+    const int kg = kc * KC + k;  // global contraction index: 2 f + (0: Re P, 1: Im P)
+    const int f = kg >> 1;
+    double sn, cs;
+    sincospi(2.0 * (double)((f * s) & (N - 1)) / (double)N, &sn, &cs);
+    double v;
+    if (row < 128) v = (kg & 1) ? sn : cs;   // Re c: Re P cos + Im P sin
+    else v = (kg & 1) ? cs : -sn;            // Im c: Im P cos - Re P sin
+    uint32_t hi, lo;
+    to_pieces<V>((float)v, hi, lo);
+    uint8_t* blk = tab + ((size_t)cb * NK + kc) * BLOCK;
+    const uint32_t off = umma::tile_off(row, k * T::ES, kRowB);
+    if constexpr (T::ES == 2) {
+        *reinterpret_cast<uint16_t*>(blk + off) = (uint16_t)hi;
+        if (T::NP > 1) *reinterpret_cast<uint16_t*>(blk + PIECE + off) = (uint16_t)lo;
+    } else {
+        *reinterpret_cast<uint32_t*>(blk + off) = hi;
+        if (T::NP > 1) *reinterpret_cast<uint32_t*>(blk + PIECE + off) = lo;
+    }
+}
+
+// complex64 spectra scaled by 1/N (Fourier coefficients, |Z/N| <= max|z|)
+template <int LOGN>
+__global__ void spec32_kernel(const double2* __restrict__ spec, int64_t n, float2* __restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double2 v = spec[e];
+    constexpr double s = 1.0 / (double)(1 << LOGN);
+    out[e] = make_float2((float)(v.x * s), (float)(v.y * s));
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            umma::smem_u32(dst)),
+        "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(umma::smem_u32(mbar))
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(umma::smem_u32(mbar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// ---- the GEMM + top-8 kernel --------------------------------------------------
+template <int V, int LOGN>
+__global__ void __launch_bounds__(kTcT, 1)
+    tc_search_kernel(const float2* __restrict__ spec, int64_t M, const uint8_t* __restrict__ tab,
+                     uint16_t* __restrict__ cand, unsigned long long* __restrict__ next,
+                     int* __restrict__ err)
+{
+    using T = TcVar<V>;
+    constexpr int N = 1 << LOGN, KC = kRowB / T::ES, NK = 2 * N / KC, KF = KC / 2;
+    constexpr int NCB = N / 128;  // column blocks of 128 shifts
+    constexpr size_t A_PIECE = (size_t)128 * kRowB, B_PIECE = (size_t)256 * kRowB;
+    constexpr size_t STAGE = (A_PIECE + B_PIECE) * T::NP;
+    constexpr uint32_t B_BYTES = (uint32_t)(B_PIECE * T::NP);
+    constexpr uint32_t ID = umma::idesc(128, 256, T::FMT);
+    constexpr int NT = T::NP == 2 ? 3 : 1;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    float2* zi_s = reinterpret_cast<float2*>(smem + kStages * STAGE);                  // [N]
+    uint64_t* b_full = reinterpret_cast<uint64_t*>(smem + kStages * STAGE + N * 8);    // [kStages]
+    uint64_t* mma_done = b_full + kStages;                                             // [kStages]
+    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(mma_done + kStages);
+    long long* s_tile = reinterpret_cast<long long*>(s_taddr + 2);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            umma::mbar_init(&b_full[s], 1);
+            umma::mbar_init(&mma_done[s], 1);
+        }
+        umma::fence_mbar_init();
+    }
+    if (warp == 0) umma::tmem_alloc(s_taddr, 256);
+    umma::tc_fence_before();
+    __syncthreads();
+    umma::tc_fence_after();
+    const uint32_t tmem = *s_taddr;
+    const int64_t total_tiles = ceil_sum128(M - 1);
+    int64_t g = 0;  // chunks issued by this CTA (stage = g % kStages, use = g / kStages)
+    bool ok = true;
+
+    for (;;) {
+        if (tid == 0) *s_tile = (long long)atomicAdd(next, 1ull);
+        __syncthreads();
+        const int64_t t = *s_tile;
+        if (t >= total_tiles || !ok) break;
+        // tile -> (i, j-tile): largest i with tiles_before(i) <= t
+        int64_t lo = 0, hi = M - 2;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (ceil_sum128(M - 1) - ceil_sum128(M - 1 - mid) <= t) lo = mid; else hi = mid - 1;
+        }
+        const int64_t i = lo;
+        const int64_t j0 = i + 1 + 128 * (t - (ceil_sum128(M - 1) - ceil_sum128(M - 1 - i)));
+        const int64_t j = j0 + tid;
+        const bool valid = j < M;
+        for (int k = tid; k < N; k += kTcT) zi_s[k] = spec[i * N + k];
+        __syncthreads();
+        const float2* zj = spec + (valid ? j : i) * N;
+
+        float best[kCand];
+        int bs[kCand];
+#pragma unroll
+        for (int q = 0; q < kCand; ++q) { best[q] = -1.0f; bs[q] = 0; }
+
+        for (int cb = 0; cb < NCB && ok; ++cb) {
+            for (int kc = 0; kc < NK; ++kc, ++g) {
+                const int st = (int)(g % kStages);
+                const uint32_t use = (uint32_t)(g / kStages);
+                uint8_t* sa = smem + st * STAGE;
+                uint8_t* sb = sa + A_PIECE * T::NP;
+                if (use > 0)
+                    ok = __syncthreads_and(umma::mbar_wait(&mma_done[st], (use - 1) & 1) ? 1 : 0);
+                if (!ok) break;
+                if (tid == 0) {
+                    mbar_expect_tx(&b_full[st], B_BYTES);
+                    bulk_g2s(sb, tab + ((size_t)cb * NK + kc) * B_BYTES, B_BYTES, &b_full[st]);
+                }
+                // this pair's cross-spectrum row: frequencies f0 .. f0 + KF - 1
+                const int f0 = kc * KF;
+                uint32_t ph[KC], pl[KC];
+#pragma unroll
+                for (int q = 0; q < KF; ++q) {
+                    const float2 a = zi_s[f0 + q];
+                    const float2 b = valid ? zj[f0 + q] : make_float2(0.f, 0.f);
+                    const float pr = __fmul_rn(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), kPScale);
+                    const float pi = __fmul_rn(__fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y)), kPScale);
+                    to_pieces<V>(pr, ph[2 * q], pl[2 * q]);
+                    to_pieces<V>(pi, ph[2 * q + 1], pl[2 * q + 1]);
+                }
+#pragma unroll
+                for (int c16 = 0; c16 < kRowB / 16; ++c16) {
+                    uint4 vh, vl;
+                    if constexpr (T::ES == 2) {
+                        const int b0 = c16 * 8;
+                        vh = make_uint4(ph[b0] | (ph[b0 + 1] << 16), ph[b0 + 2] | (ph[b0 + 3] << 16),
+                                        ph[b0 + 4] | (ph[b0 + 5] << 16), ph[b0 + 6] | (ph[b0 + 7] << 16));
+                        vl = make_uint4(pl[b0] | (pl[b0 + 1] << 16), pl[b0 + 2] | (pl[b0 + 3] << 16),
+                                        pl[b0 + 4] | (pl[b0 + 5] << 16), pl[b0 + 6] | (pl[b0 + 7] << 16));
+                    } else {
+                        const int b0 = c16 * 4;
+                        vh = make_uint4(ph[b0], ph[b0 + 1], ph[b0 + 2], ph[b0 + 3]);
+                        vl = make_uint4(pl[b0], pl[b0 + 1], pl[b0 + 2], pl[b0 + 3]);
+                    }
+                    const uint32_t off = umma::tile_off(tid, c16 * 16, kRowB);
+                    *reinterpret_cast<uint4*>(sa + off) = vh;
+                    if (T::NP > 1) *reinterpret_cast<uint4*>(sa + A_PIECE + off) = vl;
+                }
+                umma::fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    bool landed = umma::mbar_wait(&b_full[st], use & 1);
+                    if (!landed) {
+                        atomicExch(err, 1);
+                    } else {
+                        umma::tc_fence_after();
+                        const uint32_t a0 = umma::smem_u32(sa), b0 = umma::smem_u32(sb);
+                        constexpr int PA[3] = {0, 0, 1}, PB[3] = {0, 1, 0};
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+                            for (int tt = 0; tt < NT; ++tt) {
+                                const uint64_t ad = umma::sdesc(a0 + (uint32_t)(PA[tt] * A_PIECE) + ks * 256,
+                                                                128, kRowB * 8);
+                                const uint64_t bd = umma::sdesc(b0 + (uint32_t)(PB[tt] * B_PIECE) + ks * 256,
+                                                                128, kRowB * 8);
+                                const uint32_t acc = (kc > 0 || ks > 0 || tt > 0) ? 1u : 0u;
+                                if constexpr (T::TF32) umma::mma_tf32(tmem, ad, bd, ID, acc);
+                                else umma::mma_f16(tmem, ad, bd, ID, acc);
+                            }
+                        }
+                    }
+                    umma::mma_commit(&mma_done[st]);
+                }
+            }
+            if (!ok) break;
+            // this column block's |c(s)|^2 into the running top 8
+            const int64_t gl = g - 1;
+            ok = __syncthreads_and(
+                     umma::mbar_wait(&mma_done[gl % kStages], (uint32_t)(gl / kStages) & 1) ? 1 : 0) != 0;
+            if (!ok) break;
+            umma::tc_fence_after();
+#pragma unroll 1
+            for (int c0 = 0; c0 < 128; c0 += 32) {
+                float re[32], im[32];
+                umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, re);
+                umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(128 + c0), im);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    float x = __fmaf_rn(re[q], re[q], __fmul_rn(im[q], im[q]));
+                    if (x > best[kCand - 1]) {
+                        int sx = cb * 128 + c0 + q;
+#pragma unroll
+                        for (int r = 0; r < kCand; ++r) {
+                            if (x > best[r]) {
+                                const float tv = best[r];
+                                const int ts = bs[r];
+                                best[r] = x; bs[r] = sx;
+                                x = tv; sx = ts;
+                            }
+                        }
+                    }
+                }
+            }
+            umma::tc_fence_before();
+            __syncthreads();
+        }
+        if (!ok) break;
+        if (valid) {
+            uint4 w;
+            w.x = (uint32_t)bs[0] | ((uint32_t)bs[1] << 16);
+            w.y = (uint32_t)bs[2] | ((uint32_t)bs[3] << 16);
+            w.z = (uint32_t)bs[4] | ((uint32_t)bs[5] << 16);
+            w.w = (uint32_t)bs[6] | ((uint32_t)bs[7] << 16);
+            *reinterpret_cast<uint4*>(cand + ((size_t)i * M + j) * kCand) = w;
+        }
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    umma::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, 256);
+}
+
+// ---- re-score of the candidates, theta and energy (one warp per pair) --------
+template <typename ZT>
+__device__ __forceinline__ cdf ld_df(const ZT* p, int64_t k) { return split_c(p[k]); }
+
+__device__ __forceinline__ dfl shfl_df(dfl v, int off)
+{
+    return {__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)};
+}
+
+template <int LOGN, typename ZT>
+__global__ void __launch_bounds__(256)
+    tc_rescore_kernel(const ZT* __restrict__ z, int64_t M, const uint16_t* __restrict__ cand,
+                      const int8_t* __restrict__ cstatus, const int* __restrict__ err,
+                      int32_t* __restrict__ shift, double* __restrict__ theta,
+                      double* __restrict__ energy)
+{
+    constexpr int N = 1 << LOGN, R = N / 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t npairs = M * (M - 1) / 2;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= npairs) return;
+    int64_t i, j;
+    {
+        const float a = (float)(2 * M - 1);
+        int64_t e = (int64_t)floorf(0.5f * (a - sqrtf(fmaxf(a * a - 8.0f * (float)q, 0.f))));
+        e = max((int64_t)0, min(e, M - 2));
+        while (e > 0 && tri_start_tc(e, M) > q) --e;
+        while (e < M - 2 && tri_start_tc(e + 1, M) <= q) ++e;
+        i = e;
+        j = q - tri_start_tc(i, M) + i + 1;
+    }
+    const int64_t ij = i * M + j, ji = j * M + i;
+    if (cstatus[i] != FA_STATUS_OK || cstatus[j] != FA_STATUS_OK || *err) {
+        if (lane == 0) {
+            const double qn = __longlong_as_double(0x7ff8000000000000LL);
+            shift[ij] = shift[ji] = -1;
+            theta[ij] = theta[ji] = qn;
+            energy[ij] = energy[ji] = qn;
+        }
+        return;
+    }
+    const ZT* zi = z + i * N;
+    const ZT* zj = z + j * N;
+    cdf a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = ld_df(zi, lane + 32 * r);
+    const uint4 cw = *reinterpret_cast<const uint4*>(cand + (size_t)ij * kCand);
+    long long bkey = -1;
+    int sbest = 0;
+    cdf cbest{{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 1
+    for (int c = 0; c < kCand; ++c) {
+        const uint32_t w = c < 2 ? cw.x : c < 4 ? cw.y : c < 6 ? cw.z : cw.w;
+        const int s = (int)((w >> (16 * (c & 1))) & 0xffffu) & (N - 1);
+        cdf acc{{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const cdf b = ld_df(zj, (lane + 32 * r + s) & (N - 1));
+            // a conj(b)
+            acc.re = df_add(acc.re, df_dot2<+1>(a[r].re, b.re, a[r].im, b.im));
+            acc.im = df_add(acc.im, df_dot2<-1>(a[r].im, b.re, a[r].re, b.im));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            acc.re = df_add(acc.re, shfl_df(acc.re, off));
+            acc.im = df_add(acc.im, shfl_df(acc.im, off));
+        }
+        const long long key = df_key(cnorm2(acc));
+        if (key > bkey || (key == bkey && s < sbest)) { bkey = key; sbest = s; cbest = acc; }
+    }
+    // theta = arg c(s*), the rotation e^{i theta} = c / |c| in FP64 (one pair)
+    const double cx = (double)cbest.re.h + (double)cbest.re.l;
+    const double cy = (double)cbest.im.h + (double)cbest.im.l;
+    const double rr = sqrt(fma(cx, cx, cy * cy));
+    const double ux = rr > 0.0 ? cx / rr : 1.0, uy = rr > 0.0 ? cy / rr : 0.0;
+    const dfl rx = split_d(ux), ry = split_d(uy);
+    // energy h sum_k |z_i[k] - e^{i theta} z_j[k + s*]|^2 in float-float
+    dfl e{0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const cdf b = ld_df(zj, (lane + 32 * r + sbest) & (N - 1));
+        const dfl bxr = df_dot2<-1>(rx, b.re, ry, b.im);  // Re(e^{i theta} b)
+        const dfl byr = df_dot2<+1>(ry, b.re, rx, b.im);  // Im(e^{i theta} b)
+        const dfl dx = df_sub(a[r].re, bxr), dy = df_sub(a[r].im, byr);
+        e = df_add(e, df_dot2<+1>(dx, dx, dy, dy));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e = df_add(e, shfl_df(e, off));
+    if (lane == 0) {
+        const double th = atan2(cy, cx);
+        const double en = ((double)e.h + (double)e.l) * (1.0 / N);
+        shift[ij] = sbest;
+        theta[ij] = th;
+        energy[ij] = en;
+        shift[ji] = sbest ? N - sbest : 0;
+        theta[ji] = (th == 3.141592653589793) ? th : -th;
+        energy[ji] = en;
+    }
+}
+
+struct TcLayout {
+    size_t spec64, spec32, tab, cand, ctrl, total;
+};
+
+template <int V, int LOGN>
+TcLayout tc_layout(int64_t M)
+{
+    using T = TcVar<V>;
+    constexpr int N = 1 << LOGN, KC = kRowB / T::ES, NK = 2 * N / KC;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    TcLayout L;
+    size_t o = 0;
+    L.spec64 = o; o = al(o + (size_t)M * N * sizeof(double2));
+    L.spec32 = o; o = al(o + (size_t)M * N * sizeof(float2));
+    L.tab = o; o = al(o + (size_t)(N / 128) * NK * 256 * kRowB * T::NP);
+    L.cand = o; o = al(o + (size_t)M * M * kCand * sizeof(uint16_t));
+    L.ctrl = o; o += 256;
+    L.total = o;
+    return L;
+}
+
+template <int V, int LOGN, typename ZT>
+int launch_tc(const fa_handle* h, const void* z, int64_t M, void* ws, int8_t* status,
+              int32_t* shift, double* theta, double* energy, cudaStream_t st)
+{
+    using T = TcVar<V>;
+    constexpr int N = 1 << LOGN, KC = kRowB / T::ES, NK = 2 * N / KC;
+    const TcLayout L = tc_layout<V, LOGN>(M);
+    uint8_t* base = static_cast<uint8_t*>(ws);
+    double2* spec64 = reinterpret_cast<double2*>(base + L.spec64);
+    float2* spec32 = reinterpret_cast<float2*>(base + L.spec32);
+    uint8_t* tab = base + L.tab;
+    uint16_t* cand = reinterpret_cast<uint16_t*>(base + L.cand);
+    unsigned long long* next = reinterpret_cast<unsigned long long*>(base + L.ctrl);
+    int* err = reinterpret_cast<int*>(base + L.ctrl + 8);
+    int rc = launch_spectra(h, z, M, LOGN, std::is_same<ZT, float2>::value ? FA_Z_F32 : FA_Z_F64,
+                            spec64, status, shift, theta, energy, st);
+    if (rc != FA_OK) return rc;
+    if (M < 2) return FA_OK;
+    cudaError_t e = cudaMemsetAsync(base + L.ctrl, 0, 16, st);
+    if (e != cudaSuccess) return cuda_error(e, "all-pairs tc: memset");
+    const int64_t ns = M * N;
+    spec32_kernel<LOGN><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(spec64, ns, spec32);
+    const int64_t ntab = (int64_t)(N / 128) * NK * 256 * KC;
+    dft_tab_kernel<V, LOGN><<<(unsigned)((ntab + 255) / 256), 256, 0, st>>>(tab);
+    rc = cuda_error(cudaGetLastError(), "all-pairs tc: setup launch");
+    if (rc != FA_OK) return rc;
+    constexpr size_t STAGE = (size_t)(128 + 256) * kRowB * T::NP;
+    const size_t smem = kStages * STAGE + (size_t)N * 8 + 2 * kStages * 8 + 32;
+    auto kern = tc_search_kernel<V, LOGN>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "all-pairs tc: cudaFuncSetAttribute");
+    const int64_t tiles = ceil_sum128(M - 1);
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)(h->num_sms > 0 ? h->num_sms : 1));
+    kern<<<grid, kTcT, smem, st>>>(spec32, M, tab, cand, next, err);
+    rc = cuda_error(cudaGetLastError(), "all-pairs tc: search launch");
+    if (rc != FA_OK) return rc;
+    const int64_t npairs = M * (M - 1) / 2;
+    tc_rescore_kernel<LOGN, ZT><<<(unsigned)((npairs * 32 + 255) / 256), 256, 0, st>>>(
+        static_cast<const ZT*>(z), M, cand, status, err, shift, theta, energy);
+    return cuda_error(cudaGetLastError(), "all-pairs tc: rescore launch");
+}
+
+template <int V, typename ZT>
+int dispatch_tc(const fa_handle* h, const void* z, int64_t M, int logn, void* ws, int8_t* status,
+                int32_t* shift, double* theta, double* energy, cudaStream_t st)
+{
+    switch (logn) {
+    case 8: return launch_tc<V, 8, ZT>(h, z, M, ws, status, shift, theta, energy, st);
+    case 9: return launch_tc<V, 9, ZT>(h, z, M, ws, status, shift, theta, energy, st);
+    }
+    return set_error(FA_ERR_UNSUPPORTED, "fa_align_all_pairs: the tensor-core search needs N = 256 or 512");
+}
+
+template <int V>
+int dispatch_tc_z(const fa_handle* h, const void* z, int64_t M, int logn, int ztype, void* ws,
+                  int8_t* status, int32_t* shift, double* theta, double* energy, cudaStream_t st)
+{
+    if (ztype == FA_Z_F64)
+        return dispatch_tc<V, double2>(h, z, M, logn, ws, status, shift, theta, energy, st);
+    return dispatch_tc<V, float2>(h, z, M, logn, ws, status, shift, theta, energy, st);
+}
+
+}  // namespace
+
+size_t align_all_tc_ws_bytes(int64_t M, int logn, int prec)
+{
+    auto pick = [&](auto v) -> size_t {
+        constexpr int V = decltype(v)::value;
+        if (logn == 8) return tc_layout<V, 8>(M).total;
+        if (logn == 9) return tc_layout<V, 9>(M).total;
+        return 0;
+    };
+    switch (prec) {
+    case FA_PREC_TC_BF16X3: return pick(std::integral_constant<int, FA_PREC_TC_BF16X3>{});
+    case FA_PREC_TC_FP16X3: return pick(std::integral_constant<int, FA_PREC_TC_FP16X3>{});
+    case FA_PREC_TC_TF32: return pick(std::integral_constant<int, FA_PREC_TC_TF32>{});
+    case FA_PREC_TC_TF32X3: return pick(std::integral_constant<int, FA_PREC_TC_TF32X3>{});
+    }
+    return 0;
+}
+
+int launch_align_all_tc(const fa_handle* h, const void* z, int64_t M, int logn, int ztype, int prec,
+                        void* ws, int8_t* status, int32_t* shift, double* theta, double* energy,
+                        cudaStream_t st)
+{
+    if (M == 0) return FA_OK;
+    switch (prec) {
+    case FA_PREC_TC_BF16X3:
+        return dispatch_tc_z<FA_PREC_TC_BF16X3>(h, z, M, logn, ztype, ws, status, shift, theta, energy, st);
+    case FA_PREC_TC_FP16X3:
+        return dispatch_tc_z<FA_PREC_TC_FP16X3>(h, z, M, logn, ztype, ws, status, shift, theta, energy, st);
+    case FA_PREC_TC_TF32:
+        return dispatch_tc_z<FA_PREC_TC_TF32>(h, z, M, logn, ztype, ws, status, shift, theta, energy, st);
+    case FA_PREC_TC_TF32X3:
+        return dispatch_tc_z<FA_PREC_TC_TF32X3>(h, z, M, logn, ztype, ws, status, shift, theta, energy, st);
+    }
+    return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: unknown precision");
+}
+
+}  // namespace fa

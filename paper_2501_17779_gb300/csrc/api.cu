@@ -372,6 +372,16 @@ size_t fa_align_all_pairs_workspace_size(int64_t M, int32_t N)
     return align_all_ws_bytes(M, N);
 }
 
+static bool is_tc_prec(int32_t prec) { return prec >= FA_PREC_TC_BF16X3 && prec <= FA_PREC_TC_TF32X3; }
+
+size_t fa_align_all_pairs_workspace_size_prec(int64_t M, int32_t N, int32_t prec)
+{
+    if (M < 0 || M > (1 << 16) || N <= 0) return 0;
+    if (prec == FA_PREC_FP64 || prec == FA_PREC_MIXED) return align_all_ws_bytes(M, N);
+    if (!is_tc_prec(prec) || (N != 256 && N != 512)) return 0;
+    return align_all_tc_ws_bytes(M, N == 256 ? 8 : 9, prec);
+}
+
 int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_t ztype,
                        int32_t prec, int32_t* shift, double* theta, double* energy,
                        int8_t* status, void* workspace, size_t workspace_bytes, void* stream)
@@ -380,7 +390,7 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
     if (M < 0) return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: negative curve count");
     if (ztype != FA_Z_F64 && ztype != FA_Z_F32)
         return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: unknown ztype");
-    if (prec != FA_PREC_FP64 && prec != FA_PREC_MIXED)
+    if (prec != FA_PREC_FP64 && prec != FA_PREC_MIXED && !is_tc_prec(prec))
         return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: unknown precision");
     int logn = -1;
     for (int L = kMinLogN; L <= kMaxLogN; ++L)
@@ -388,12 +398,16 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
     if (logn < 0)
         return set_error(FA_ERR_UNSUPPORTED,
                          "fa_align_all_pairs: N must be a power of two in [4, 4096]");
+    if (is_tc_prec(prec) && N != 256 && N != 512)
+        return set_error(FA_ERR_UNSUPPORTED,
+                         "fa_align_all_pairs: the tensor-core search needs N = 256 or 512");
     if (M == 0) return FA_OK;
     if (M > (1 << 16))
         return set_error(FA_ERR_UNSUPPORTED, "fa_align_all_pairs: more than 65536 curves");
     if (!z || !shift || !theta || !energy || !status)
         return set_error(FA_ERR_INVALID_ARG, "fa_align_all_pairs: null pointer");
-    const size_t need = align_all_ws_bytes(M, N);
+    const size_t need = is_tc_prec(prec) ? align_all_tc_ws_bytes(M, logn, prec)
+                                         : align_all_ws_bytes(M, N);
     DeviceGuard g(h->device);
     if (g.rc != FA_OK) return g.rc;
     void* ws = workspace;
@@ -409,6 +423,9 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
     }
     if (prec == FA_PREC_MIXED)
         return launch_align_all_df(h, z, M, logn, ztype, ws, status, shift, theta, energy,
+                                   static_cast<cudaStream_t>(stream));
+    if (is_tc_prec(prec))
+        return launch_align_all_tc(h, z, M, logn, ztype, prec, ws, status, shift, theta, energy,
                                    static_cast<cudaStream_t>(stream));
     return launch_align_all(h, z, M, logn, ztype, ws, status, shift, theta, energy,
                             static_cast<cudaStream_t>(stream));

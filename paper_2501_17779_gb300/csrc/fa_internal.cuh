@@ -114,6 +114,16 @@ int launch_align_direct(const fa_handle* h, const void* z1, const void* z2, int6
                         int ztype, int32_t* shift, double* theta, double* energy, int8_t* status,
                         cudaStream_t st);
 size_t align_all_ws_bytes(int64_t M, int N);
+// spectra of M curves (FP64) into spec [M][N]; statuses and the diagonal of the
+// all-pairs outputs
+int launch_spectra(const fa_handle* h, const void* z, int64_t M, int logn, int ztype,
+                   double2* spec, int8_t* status, int32_t* shift, double* theta, double* energy,
+                   cudaStream_t st);
+// the tensor-core all-pairs search (prec = FA_PREC_TC_*), N = 256 or 512
+size_t align_all_tc_ws_bytes(int64_t M, int logn, int prec);
+int launch_align_all_tc(const fa_handle* h, const void* z, int64_t M, int logn, int ztype, int prec,
+                        void* ws, int8_t* status, int32_t* shift, double* theta, double* energy,
+                        cudaStream_t st);
 int launch_align_all(const fa_handle* h, const void* z, int64_t M, int logn, int ztype, void* ws,
                      int8_t* status, int32_t* shift, double* theta, double* energy,
                      cudaStream_t st);

@@ -31,6 +31,7 @@
 // (global memory, L1/L2 resident while a warp works on its curve).
 #include <algorithm>
 
+#include "df.cuh"
 #include "fa_internal.cuh"
 
 namespace fa {
@@ -166,6 +167,21 @@ __device__ __forceinline__ double sqrt_nr(double q)
     const double s0 = widen_f32(s0f);
     return fma(fma(-s0, s0, q), widen_f32(__fdiv_rn(0.5f, s0f)), s0);
 }
+// |(dx, dy)| in float-float: the FP64 components split exactly enough (2^-47),
+// the squared length by exact products, and the square root from the FP32
+// root of the leading part with one Newton step whose residual q - s0^2 is
+// formed exactly (s0^2 = p + pe by FMA, q.h - p exact by Sterbenz) -- about
+// 2^-46 relative.  FP32 and integer instructions only.
+__device__ __forceinline__ dfl df_chord(double2 d)
+{
+    const cdf c = split_c(d);
+    const dfl q = df_dot2<+1>(c.re, c.re, c.im, c.im);
+    if (!(q.h > 0.0f)) return {0.0f, 0.0f};
+    const float s0 = __fsqrt_rn(q.h);
+    const float pp = __fmul_rn(s0, s0), pe = __fmaf_rn(s0, s0, -pp);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(q.h, pp), pe), q.l);
+    return fast_two_sum(s0, __fmul_rn(r, __fdiv_rn(0.5f, s0)));
+}
 // 2x for x >= 0 with integer instructions only (exact; subnormals shift,
 // normals step the exponent, the largest binade goes to +Inf, Inf/NaN stay)
 __device__ __forceinline__ double twice_pos(double x)
@@ -270,10 +286,13 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     // d = q * rsqrt(q) and 1/d = rsqrt(q) from one reciprocal square root
     // (q = |p_{l+1} - p_l|^2 >= 0, so its bit pattern tests > 0 as an integer)
     bool zero = false, nf = false;
+    unsigned emax = 0;  // largest biased exponent of a coordinate
     for (int l = lane; l < n; l += 32) {
         const double2 pl = __ldg(p + l);
         const double2 pn = __ldg(p + ((l + 1 == n) ? 0 : l + 1));
         nf |= !finite2(pl);
+        emax = max(emax, max((unsigned)(__double_as_longlong(pl.x) >> 52) & 0x7ffu,
+                             (unsigned)(__double_as_longlong(pl.y) >> 52) & 0x7ffu));
         const double dx = pn.x - pl.x, dy = pn.y - pl.y;
         const double q = fma(dx, dx, dy * dy);
         const bool pos = __double_as_longlong(q) > 0;
@@ -443,6 +462,16 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     const bool unit = (flags & FA_UNIT_LENGTH) != 0;
     double per_len = 0.0;
     double2 Sfirst = d2(0, 0), Sprev = d2(0, 0);
+    // The node sum (for the mean) and the perimeter of the outputs are
+    // accumulated in float-float (about 48 significant bits; FP64 is the
+    // scarce unit) when every coordinate and the perimeter lie in a range
+    // where the float parts stay normal: coordinates below 2^60 in magnitude,
+    // perimeter in [2^-40, 2^40].  Their errors (2^-47 of each summand, the
+    // chord lengths to 2^-46 of themselves) move the normalised nodes by
+    // < 1e-14.  Other curves sum in FP64.
+    const int eL = (int)((__double_as_longlong(L) >> 52) & 0x7ff) - 1023;
+    const bool dfsum = __reduce_max_sync(0xffffffffu, emax) < 1023u + 60u && eL > -40 && eL < 40;
+    dfl sx{0.f, 0.f}, sy{0.f, 0.f}, per_df{0.f, 0.f};
     if (k0 < k1) {
         // arc-length target of output k: L t_k with t_k = k / N_out
         const double s0 = pow2 ? k0 * LN : L * ((double)k0 / (double)Nout);
@@ -477,18 +506,35 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             const double2 S = d2(fma(ca, Ml.x, fma(cb, Mn.x, fma(b, cv.x, pl.x))),
                                  fma(ca, Ml.y, fma(cb, Mn.y, fma(b, cv.y, pl.y))));
             raw[k] = S;
-            ssum = add2(ssum, S);
-            if (unit) {
-                if (k > k0) {
-                    const double dx = S.x - Sprev.x, dy = S.y - Sprev.y;
-                    const double q = fma(dx, dx, dy * dy);
-                    per_len += __double_as_longlong(q) > 0 ? sqrt_nr(q) : 0.0;
-                } else {
-                    Sfirst = S;
+            if (dfsum) {
+                // the chord's components in FP64 (exact differences of nearby
+                // values), its length and both sums in float-float
+                const cdf Sd = split_c(S);
+                sx = df_add(sx, Sd.re);
+                sy = df_add(sy, Sd.im);
+                if (unit) {
+                    if (k > k0) per_df = df_add(per_df, df_chord(sub2(S, Sprev)));
+                    else Sfirst = S;
+                    Sprev = S;
                 }
-                Sprev = S;
+            } else {
+                ssum = add2(ssum, S);
+                if (unit) {
+                    if (k > k0) {
+                        const double dx = S.x - Sprev.x, dy = S.y - Sprev.y;
+                        const double q = fma(dx, dx, dy * dy);
+                        per_len += __double_as_longlong(q) > 0 ? sqrt_nr(q) : 0.0;
+                    } else {
+                        Sfirst = S;
+                    }
+                    Sprev = S;
+                }
             }
         }
+    }
+    if (dfsum) {  // the lane's float-float partial sums to FP64 (exact: h + l)
+        ssum = d2(widen_any(sx.h) + widen_any(sx.l), widen_any(sy.h) + widen_any(sy.l));
+        per_len = widen_any(per_df.h) + widen_any(per_df.l);
     }
     if (unit) {
         // the chord from this lane's last output to the next one: the next
