@@ -651,7 +651,8 @@ def run_gpu(args):
         del za, outs, mouts, z32, ref32
 
     # uneven batch: 100,000 pairs, n log-uniform in [64, 8192] (multiples of
-    # 16), one persistent launch, autotuned CTA size, replayed as a CUDA graph
+    # 16), one persistent launch per transform-length bucket with the plan the
+    # autotuner chose for it, replayed as a CUDA graph
     rag = None
     if not args.no_ragged:
         from paper_2501_17779_gb300 import synth
@@ -686,8 +687,20 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
         rag_graph_ms = e0.elapsed_time(e1) / 3
         fl_rag = ragged_flops(sizes)
+        plan = api.ragged_plan(local)
+        nz = np.asarray(sizes)
+        Lz = np.where(nz & (nz - 1) == 0, nz, 1 << np.ceil(np.log2(2 * nz - 1)).astype(np.int64))
+        per_bucket = {}
+        for bkt in sorted(set(np.log2(Lz).astype(int).tolist()), reverse=True):
+            t_, g_, ms_ = plan[bkt]
+            sel = nz[np.log2(Lz).astype(int) == bkt]
+            flb = ragged_flops(sel)
+            per_bucket[f"L=2^{bkt}"] = {
+                "pairs": int(sel.size), "threads": t_, "pairs_per_cta": g_, "ms": ms_,
+                "frac_of_fp64_peak": (flb / (ms_ * 1e-3) / 1e12 / fp64_peak) if ms_ > 0 else None}
         rag = {"workload": f"{Pr} pairs, n log-uniform in [64, 8192] (multiples of 16), 4..32 "
-                           "harmonics, FP64, one persistent launch",
+                           "harmonics, FP64, one persistent launch per transform-length bucket",
+               "plans": per_bucket,
                "ms": rag_ms, "graph_ms": rag_graph_ms, "pairs_per_s": Pr / (rag_graph_ms * 1e-3),
                "nodes": int(np.asarray(sizes).sum()),
                "tflops": fl_rag / (rag_graph_ms * 1e-3) / 1e12,

@@ -273,7 +273,8 @@ int fa_elastic_distance(fa_handle* h, const double* curves1, int64_t M1, const d
                         int8_t* status, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
- * Alignment of P pairs with DIFFERENT node counts in one persistent launch.
+ * Alignment of P pairs with DIFFERENT node counts, one persistent launch per
+ * transform-length bucket.
  *
  * Pair p is z1[offsets[p] .. offsets[p+1]) and z2[offsets[p] .. offsets[p+1])
  * (n_p nodes each, same CSR offsets for both curves), otherwise as in
@@ -281,11 +282,16 @@ int fa_elastic_distance(fa_handle* h, const double* curves1, int64_t M1, const d
  * power of two the transforms have length n_p; otherwise the cyclic
  * correlation is computed exactly as a zero-padded linear correlation with
  * transforms of length L = the power of two >= 2 n_p (no chirps, no
- * approximation).  The pairs are sorted on the device by transform length
- * (longest first) and processed by persistent CTAs that take pairs from a
- * shared counter.  Every step is a launch or memset on `stream`, so the call
- * can be captured into a CUDA graph (pass a workspace then, so that nothing
- * is allocated).
+ * approximation).  The pairs are sorted on the device into buckets by
+ * transform length (log2 L, longest first); each bucket is processed by one
+ * persistent launch with the handle's plan for that bucket -- the CTA size
+ * and the number of pairs one CTA transforms side by side (several short
+ * pairs per CTA for L <= 1024, one pair per CTA split into radix-R parts for
+ * L > 4096) -- whose CTAs take pairs from the bucket's counter.  The plans
+ * start from a size rule and are set per bucket by
+ * fa_align_pairs_ragged_autotune.  Every step is a launch or memset on
+ * `stream`, so the call can be captured into a CUDA graph (pass a workspace
+ * then, so that nothing is allocated).
  *
  *   z1, z2     complex128 (FA_Z_F64) or complex64 (FA_Z_F32) arrays of
  *              offsets[P] points (device), each curve centred, unit length
@@ -303,19 +309,36 @@ int fa_align_pairs_ragged(fa_handle* h, const void* z1, const void* z2, const in
                           void* stream);
 
 /*
- * Autotuner of fa_align_pairs_ragged: runs the caller's batch with each CTA
- * size of the persistent kernel (256, 512, 1024 threads), three timed runs
- * each, keeps the fastest in the handle for later calls and returns it in
- * *chosen_threads.  Same arguments and outputs as fa_align_pairs_ragged (the
- * outputs hold the chosen configuration's result afterwards; different CTA
- * sizes sum in a different order and may differ in the last bit).
- * Synchronises the stream; not for use during stream capture.
+ * Autotuner of fa_align_pairs_ragged: for every transform-length bucket the
+ * caller's batch fills, runs that bucket's pairs with each compiled plan that
+ * fits the length (CTA sizes 128..1024 threads, 1..16 pairs per CTA), one
+ * warm-up and three timed runs each, and keeps the fastest plan per bucket in
+ * the handle for later calls (fa_align_pairs_ragged_plan reports them).
+ * *chosen_threads receives the CTA size chosen for the longest bucket
+ * present.  Same arguments and outputs as fa_align_pairs_ragged (the outputs
+ * hold the chosen plans' result afterwards; different plans sum in a
+ * different order and may differ in the last bit).  Synchronises the stream;
+ * not for use during stream capture.
  */
 int fa_align_pairs_ragged_autotune(fa_handle* h, const void* z1, const void* z2,
                                    const int64_t* offsets, int64_t P, int32_t max_n,
                                    int32_t ztype, int32_t* shift, double* theta, double* energy,
                                    int8_t* status, void* workspace, size_t workspace_bytes,
                                    void* stream, int32_t* chosen_threads);
+
+/* The handle's plan for fa_align_pairs_ragged, per bucket b = log2 L in
+ * [0, 16): threads[b] (CTA size), pairs_per_cta[b], and ms[b], the time of
+ * that bucket's launch measured by the last autotuning (0 when not tuned);
+ * entries outside the supported lengths are 0.  Any pointer may be NULL
+ * (HOST arrays of 16 entries). */
+int fa_align_pairs_ragged_plan(fa_handle* h, int32_t* threads, int32_t* pairs_per_cta, float* ms);
+/* Sets the handle's plan for bucket log2 L = bucket (in [2, 14]): one of the
+ * compiled (threads, pairs_per_cta) combinations -- (256|512|1024, 1),
+ * (128|256|512, 2), (128|256|512, 4), (256, 8), (256, 16) -- that fits the
+ * length (pairs_per_cta >= 2 needs pairs_per_cta L <= 2048 and at most L
+ * threads per pair); FA_ERR_UNSUPPORTED otherwise. */
+int fa_align_pairs_ragged_set_plan(fa_handle* h, int32_t bucket, int32_t threads,
+                                   int32_t pairs_per_cta);
 
 /*
  * End-to-end convenience call on HOST buffers: arc-length resampling of 2P

@@ -43,7 +43,9 @@ EXPORTS = (
     "fa_align_all_pairs_workspace_size", "fa_align_all_pairs_workspace_size_prec",
     "fa_align_all_pairs",
     "fa_align_pairs_ragged_workspace_size", "fa_align_pairs_ragged",
-    "fa_align_pairs_ragged_autotune", "fa_elastic_workspace_size", "fa_elastic_distance",
+    "fa_align_pairs_ragged_autotune", "fa_align_pairs_ragged_plan",
+    "fa_align_pairs_ragged_set_plan",
+    "fa_elastic_workspace_size", "fa_elastic_distance",
     "fa_fourier_descriptors", "fa_column_stats", "fa_standardize", "fa_embed_sqdist",
     "fa_select_k", "fa_mlp_num_params", "fa_mlp_create", "fa_mlp_destroy", "fa_mlp_set_params",
     "fa_mlp_get_params", "fa_mlp_forward", "fa_mlp_pair_grad", "fa_mlp_adam_step",
@@ -110,6 +112,10 @@ def load(build_if_missing: bool = False):
     L.fa_align_pairs_ragged_autotune.argtypes = [vp, vp, vp, vp, i64, i32, i32, vp, vp, vp, vp,
                                                  vp, sz, vp, vp]
     L.fa_align_pairs_ragged_autotune.restype = ctypes.c_int
+    L.fa_align_pairs_ragged_plan.argtypes = [vp, vp, vp, vp]
+    L.fa_align_pairs_ragged_plan.restype = ctypes.c_int
+    L.fa_align_pairs_ragged_set_plan.argtypes = [vp, i32, i32, i32]
+    L.fa_align_pairs_ragged_set_plan.restype = ctypes.c_int
     L.fa_resample_arclength_noalloc.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp]
     L.fa_resample_arclength_noalloc.restype = ctypes.c_int
     L.fa_elastic_workspace_size.argtypes = [vp, i64, i64, i64, i32, i32]

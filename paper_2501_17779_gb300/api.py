@@ -178,8 +178,9 @@ def align_pairs_ragged(z1: torch.Tensor, z2: torch.Tensor, offsets: torch.Tensor
     z1, z2: flat complex128/complex64 CUDA tensors of offsets[-1] points; pair p
     is [offsets[p], offsets[p+1]) in both.  offsets: int64 CUDA tensor [P+1].
     max_n bounds every pair's node count (default: computed from offsets, which
-    reads them back to the host).  With ``autotune`` the CTA size is chosen by
-    timed runs first (fa_align_pairs_ragged_autotune).  Returns (shift, theta,
+    reads them back to the host).  With ``autotune`` each bucket's plan (CTA
+    size, pairs per CTA) is chosen by timed runs first
+    (fa_align_pairs_ragged_autotune; see ragged_plan).  Returns (shift, theta,
     energy, status) [P] each.
     """
     if z1.dtype not in (torch.complex128, torch.complex64):
@@ -213,6 +214,25 @@ def align_pairs_ragged(z1: torch.Tensor, z2: torch.Tensor, offsets: torch.Tensor
     else:
         _lib.check(L.fa_align_pairs_ragged(*args))
     return shift, theta, energy, status
+
+
+def ragged_plan(device: int | None = None) -> dict:
+    """The handle's per-bucket plan for align_pairs_ragged (fa_align_pairs_ragged_plan):
+    {log2 L: (CTA size, pairs per CTA, ms of the last autotuning)} for the
+    supported transform lengths."""
+    L = _lib.load()
+    t = (ctypes.c_int32 * 16)()
+    g = (ctypes.c_int32 * 16)()
+    ms = (ctypes.c_float * 16)()
+    _lib.check(L.fa_align_pairs_ragged_plan(handle(device), t, g, ms))
+    return {b: (int(t[b]), int(g[b]), float(ms[b])) for b in range(16) if t[b] > 0}
+
+
+def set_ragged_plan(bucket: int, threads: int, pairs_per_cta: int,
+                    device: int | None = None) -> None:
+    """Pins the plan of one transform-length bucket (fa_align_pairs_ragged_set_plan)."""
+    L = _lib.load()
+    _lib.check(L.fa_align_pairs_ragged_set_plan(handle(device), bucket, threads, pairs_per_cta))
 
 
 def ragged_workspace_size(P: int, max_n: int, device: int | None = None) -> int:

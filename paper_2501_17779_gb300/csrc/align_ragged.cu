@@ -41,7 +41,7 @@ constexpr int kCounterBytes = 256;
 struct RaggedCounters {
     int hist[kBuckets];
     int cursor[kBuckets];
-    int head;
+    int bhead[kBuckets];  // per bucket: items handed out so far
 };
 
 __device__ __forceinline__ int ilog2(int x) { return 31 - __clz(x); }
@@ -53,7 +53,6 @@ __device__ __forceinline__ int ragged_len(int n)
     if ((n & (n - 1)) == 0) return n;
     return 1 << (ilog2(2 * n - 1) + 1);
 }
-
 __global__ void ragged_keys_kernel(const int64_t* __restrict__ off, int64_t P, int max_n,
                                    RaggedCounters* __restrict__ cnt, int32_t* __restrict__ shift,
                                    double* __restrict__ theta, double* __restrict__ energy,
@@ -94,10 +93,10 @@ __global__ void ragged_order_kernel(const int64_t* __restrict__ off, int64_t P, 
 // k < 2n (KIND 1, the periodic extension), zero beyond.
 template <int T, int KIND, typename ZT>
 __device__ void load_dif(double2* X, const ZT* __restrict__ z, int n, int L, int B, int R, int q,
-                         const double2* __restrict__ WL)
+                         const double2* __restrict__ WL, int tl)
 {
     const int lim = (KIND == 0) ? n : 2 * n;
-    for (int t = threadIdx.x; t < B; t += T) {
+    for (int t = tl; t < B; t += T) {
         double2 acc = make_double2(0.0, 0.0);
         for (int r = 0; r < R; ++r) {
             const int k = t + r * B;
@@ -121,6 +120,7 @@ struct RaggedArgs {
     const int64_t* off;
     int64_t P;
     int max_n;
+    int bucket;             // log2 L of the pairs this launch processes
     RaggedCounters* cnt;
     const int* order;
     double2* slots;         // per-CTA scratch: 2 * Lmax complex doubles each
@@ -136,113 +136,197 @@ struct Tables {
     const double2* tw[kMaxRaggedLogL + 1];  // W_L^k for L <= 16384
 };
 
-template <int T, typename ZT>
+// ---- reductions over a group of TG threads (local index tl) ----------------
+// Every group of the CTA calls them at the same time (their barriers are
+// CTA-wide); sk/si/part are the group's own slices of shared memory.
+template <int TG>
+__device__ __forceinline__ void grp_argmax(long long& key, int& idx, long long* sk, int* si, int tl)
+{
+    constexpr int W = TG < 32 ? TG : 32;
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) {
+        const long long k2 = __shfl_xor_sync(0xffffffffu, key, off, W);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, off, W);
+        if (key_better(k2, i2, key, idx)) { key = k2; idx = i2; }
+    }
+    if constexpr (TG > 32) {
+        if ((tl & 31) == 0) { sk[tl >> 5] = key; si[tl >> 5] = idx; }
+        __syncthreads();
+        key = sk[0];
+        idx = si[0];
+#pragma unroll
+        for (int w = 1; w < TG / 32; ++w)
+            if (key_better(sk[w], si[w], key, idx)) { key = sk[w]; idx = si[w]; }
+        __syncthreads();
+    }
+}
+
+template <int TG>
+__device__ __forceinline__ double2 grp_sum(double2 v, double2* part, int tl)
+{
+    part[tl] = v;
+    __syncthreads();
+    if constexpr (TG >= 32) {
+        if (tl < 32) {
+            double2 s = part[tl];
+            for (int i = tl + 32; i < TG; i += 32) { s.x += part[i].x; s.y += part[i].y; }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+                s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+            }
+            if (tl == 0) part[TG] = s;
+        }
+    } else {
+        if (tl == 0) {
+            double2 s = part[0];
+            for (int i = 1; i < TG; ++i) { s.x += part[i].x; s.y += part[i].y; }
+            part[TG] = s;
+        }
+    }
+    __syncthreads();
+    const double2 r = part[TG];
+    __syncthreads();
+    return r;
+}
+
+// Plan of one bucket: T threads per CTA, G pairs per CTA (T / G threads per
+// pair).  G = 1 handles every length (L > 4096 by the radix-R split); G >= 2
+// keeps both spectra of each pair in shared memory, so G L <= 2048.
+template <int T, int G>
+constexpr int grp_lmax() { return G == 1 ? (1 << kMaxRaggedLogL) : BMAX / (2 * G); }
+
+template <int T, int G, typename ZT>
 __global__ void __launch_bounds__(T)
     ragged_kernel(const __grid_constant__ RaggedArgs a, const __grid_constant__ Tables tb)
 {
+    constexpr int TG = T / G;
+    constexpr int SW = TG >= 32 ? TG / 32 : 1;  // argmax slots per group
     extern __shared__ __align__(16) double2 smem[];
-    double2* X = smem;                       // [BMAX]
-    double2* part = smem + BMAX;             // [T + 1]
-    long long* sk = reinterpret_cast<long long*>(part + T + 1);  // [T/32]
-    int* si = reinterpret_cast<int*>(sk + T / 32);               // [T/32]
-    int* item = si + T / 32;                                     // [2]
+    double2* X = smem;                                          // [BMAX]
+    double2* part_all = smem + BMAX;                            // [G][TG + 1]
+    long long* sk_all = reinterpret_cast<long long*>(part_all + G * (TG + 1));  // [G][SW]
+    int* si_all = reinterpret_cast<int*>(sk_all + G * SW);                     // [G][SW]
+    int* item = si_all + G * SW;                                               // [1 + G]
+    const int g = threadIdx.x / TG, tl = threadIdx.x % TG;
+    double2* part = part_all + g * (TG + 1);
+    long long* sk = sk_all + g * SW;
+    int* si = si_all + g * SW;
+    int* badf = item + 1;
     const ZT* Z1 = static_cast<const ZT*>(a.z1);
     const ZT* Z2 = static_cast<const ZT*>(a.z2);
-    double2* Zs = a.slots + (int64_t)blockIdx.x * a.slot_elems;  // Z1_q parts [L]
-    double2* Fs = Zs + a.slot_elems / 2;                          // F_q parts [L]
-    int total = 0;
-    for (int b = 0; b < kBuckets; ++b) total += a.cnt->hist[b];
+    double2* Zs = a.slots + (int64_t)blockIdx.x * a.slot_elems;  // Z1_q parts [L] (G = 1)
+    double2* Fs = Zs + a.slot_elems / 2;                          // F_q parts [L] (G = 1)
+    const int b = a.bucket;
+    const int count = a.cnt->hist[b];
+    int start = 0;
+    for (int k = b + 1; k < kBuckets; ++k) start += a.cnt->hist[k];
+    const int L = 1 << b, logL = b;
+    const int logb = min(logL, LOG_BMAX);
+    const int B = 1 << logb, R = L >> logb;  // R > 1 only for G = 1
+    const double2* Wf = tb.tf[logb];
+    const double2* WL = tb.tw[logL];
 
     for (;;) {
-        if (threadIdx.x == 0) item[0] = atomicAdd(&a.cnt->head, 1);
+        if (threadIdx.x == 0) item[0] = atomicAdd(&a.cnt->bhead[b], G);
+        if (threadIdx.x < G) badf[threadIdx.x] = 0;
         __syncthreads();
-        const int it = item[0];
+        const int base = item[0];
         __syncthreads();
-        if (it >= total) break;
-        const int p = a.order[it];
-        const int64_t o = a.off[p];
-        const int n = (int)(a.off[p + 1] - o);
+        if (base >= count) break;
+        const bool valid = base + g < count;
+        const int p = valid ? a.order[start + base + g] : 0;
+        const int64_t o = valid ? a.off[p] : 0;
+        const int n = valid ? (int)(a.off[p + 1] - o) : 0;
         const ZT* z1 = Z1 + o;
         const ZT* z2 = Z2 + o;
-        int L = n;
-        if ((n & (n - 1)) != 0) L = 1 << (ilog2(2 * n - 1) + 1);
-        const int logL = ilog2(L);
-        const int logb = min(logL, LOG_BMAX);
-        const int B = 1 << logb, R = L >> logb;
-        const double2* Wf = tb.tf[logb];
-        const double2* WL = tb.tw[logL];
 
-        // non-finite inputs
+        // non-finite inputs: that pair is answered with NaNs and computed on
+        // zeros (its group still takes part in every barrier)
         bool nf = false;
-        for (int k = threadIdx.x; k < n; k += T) nf |= !finite2(ld_z(z1, k)) || !finite2(ld_z(z2, k));
-        const bool bad = __syncthreads_or(nf);
-        if (bad) {
-            if (threadIdx.x == 0) {
-                a.shift[p] = -1;
-                a.theta[p] = __longlong_as_double(0x7ff8000000000000LL);
-                a.energy[p] = __longlong_as_double(0x7ff8000000000000LL);
-                a.status[p] = FA_STATUS_NONFINITE;
-            }
-            continue;
-        }
-        // spectra of the padded curve 1, one DIF part at a time
-        for (int q = 0; q < R; ++q) {
-            load_dif<T, 0>(X, z1, n, L, B, R, q, WL);
-            __syncthreads();
-            fft_rt<T, BMAX>(X, logb, Wf);
-            for (int m = threadIdx.x; m < B; m += T) Zs[q * B + m] = X[m];
-            __syncthreads();
-        }
-        // per part: spectrum of curve 2, product, correlation transform
-        for (int q = 0; q < R; ++q) {
-            load_dif<T, 1>(X, z2, n, L, B, R, q, WL);
-            __syncthreads();
-            fft_rt<T, BMAX>(X, logb, Wf);
-            for (int m = threadIdx.x; m < B; m += T) X[m] = cmulc(Zs[q * B + m], X[m]);
-            __syncthreads();
-            fft_rt<T, BMAX>(X, logb, Wf);
-            if (q < R - 1)
-                for (int m = threadIdx.x; m < B; m += T) Fs[q * B + m] = X[m];
-            __syncthreads();
-        }
-        // L c(s) = sum_q W_L^{qs} F_q[s mod B] for s < n; F_{R-1} is still in X
+        for (int k = tl; k < n; k += TG) nf |= !finite2(ld_z(z1, k)) || !finite2(ld_z(z2, k));
+        if (nf) badf[g] = 1;
+        __syncthreads();
+        const bool bad = badf[g] != 0;
+        const int nn = bad ? 0 : n;  // the node count the transforms see
+
         long long key = -1;
         int idx = 0;
-        for (int s = threadIdx.x; s < n; s += T) {
-            const int sm = s & (B - 1);
-            double2 c = X[sm];
-            if (R > 1) {
-                c = cmul(c, __ldg(WL + (((R - 1) * s) & (L - 1))));
-                for (int q = 0; q < R - 1; ++q) {
-                    double2 f = Fs[q * B + sm];
-                    if (q > 0) f = cmul(f, __ldg(WL + ((q * s) & (L - 1))));
-                    c.x += f.x;
-                    c.y += f.y;
-                }
+        if constexpr (G == 1) {
+            // spectra of the padded curve 1, one DIF part at a time
+            for (int q = 0; q < R; ++q) {
+                load_dif<T, 0>(X, z1, nn, L, B, R, q, WL, tl);
+                __syncthreads();
+                fft_rt_g<T, BMAX>(X, logb, Wf, tl);
+                for (int m = tl; m < B; m += T) Zs[q * B + m] = X[m];
+                __syncthreads();
             }
-            const long long kq = __double_as_longlong(fma(c.x, c.x, c.y * c.y));
-            if (key_better(kq, s, key, idx)) { key = kq; idx = s; }
+            // per part: spectrum of curve 2, product, correlation transform
+            for (int q = 0; q < R; ++q) {
+                load_dif<T, 1>(X, z2, nn, L, B, R, q, WL, tl);
+                __syncthreads();
+                fft_rt_g<T, BMAX>(X, logb, Wf, tl);
+                for (int m = tl; m < B; m += T) X[m] = cmulc(Zs[q * B + m], X[m]);
+                __syncthreads();
+                fft_rt_g<T, BMAX>(X, logb, Wf, tl);
+                if (q < R - 1)
+                    for (int m = tl; m < B; m += T) Fs[q * B + m] = X[m];
+                __syncthreads();
+            }
+            // L c(s) = sum_q W_L^{qs} F_q[s mod B] for s < n; F_{R-1} is still in X
+            for (int s = tl; s < nn; s += T) {
+                const int sm = s & (B - 1);
+                double2 c = X[sm];
+                if (R > 1) {
+                    c = cmul(c, __ldg(WL + (((R - 1) * s) & (L - 1))));
+                    for (int q = 0; q < R - 1; ++q) {
+                        double2 f = Fs[q * B + sm];
+                        if (q > 0) f = cmul(f, __ldg(WL + ((q * s) & (L - 1))));
+                        c.x += f.x;
+                        c.y += f.y;
+                    }
+                }
+                const long long kq = __double_as_longlong(fma(c.x, c.x, c.y * c.y));
+                if (key_better(kq, s, key, idx)) { key = kq; idx = s; }
+            }
+        } else {
+            // both spectra of each pair in shared memory (L <= BMAX / (2G))
+            double2* Xg = X + (size_t)g * 2 * (BMAX / (2 * G));
+            double2* Yg = Xg + BMAX / (2 * G);
+            load_dif<TG, 0>(Xg, z1, nn, L, L, 1, 0, WL, tl);
+            load_dif<TG, 1>(Yg, z2, nn, L, L, 1, 0, WL, tl);
+            __syncthreads();
+            fft_rt_g<TG, BMAX / (2 * G)>(Xg, logb, Wf, tl);
+            fft_rt_g<TG, BMAX / (2 * G)>(Yg, logb, Wf, tl);
+            for (int m = tl; m < L; m += TG) Xg[m] = cmulc(Xg[m], Yg[m]);
+            __syncthreads();
+            fft_rt_g<TG, BMAX / (2 * G)>(Xg, logb, Wf, tl);
+            for (int s = tl; s < nn; s += TG) {
+                const double2 c = Xg[s];
+                const long long kq = __double_as_longlong(fma(c.x, c.x, c.y * c.y));
+                if (key_better(kq, s, key, idx)) { key = kq; idx = s; }
+            }
         }
-        cta_argmax<T>(key, idx, sk, si);
+        grp_argmax<TG>(key, idx, sk, si, tl);
         const int sbest = idx;
         // c(s*) by its O(n) sum, theta, energy by its definition
         double2 c = make_double2(0.0, 0.0);
-        for (int k = threadIdx.x; k < n; k += T) {
+        for (int k = tl; k < nn; k += TG) {
             const double2 u = ld_z(z1, k);
             int m = k + sbest;
-            if (m >= n) m -= n;
+            if (m >= nn) m -= nn;
             const double2 v = ld_z(z2, m);
             c.x = fma(u.x, v.x, fma(u.y, v.y, c.x));
             c.y = fma(u.y, v.x, fma(-u.x, v.y, c.y));
         }
-        c = cta_sum<T>(c, part);
+        c = grp_sum<TG>(c, part, tl);
         const double rr = sqrt(fma(c.x, c.x, c.y * c.y));
         const double2 rot = rr > 0.0 ? make_double2(c.x / rr, c.y / rr) : make_double2(1.0, 0.0);
         double e = 0.0;
-        for (int k = threadIdx.x; k < n; k += T) {
+        for (int k = tl; k < nn; k += TG) {
             const double2 u = ld_z(z1, k);
             int m = k + sbest;
-            if (m >= n) m -= n;
+            if (m >= nn) m -= nn;
             const double2 v = ld_z(z2, m);
             const double rx = fma(rot.x, v.x, -rot.y * v.y);
             const double ry = fma(rot.y, v.x, rot.x * v.y);
@@ -250,24 +334,55 @@ __global__ void __launch_bounds__(T)
             e = fma(dx, dx, e);
             e = fma(dy, dy, e);
         }
-        const double2 es = cta_sum<T>(make_double2(e, 0.0), part);
-        if (threadIdx.x == 0) {
-            a.shift[p] = sbest;
-            a.theta[p] = atan2(c.y, c.x);
-            a.energy[p] = es.x / (double)n;
-            a.status[p] = FA_STATUS_OK;
+        const double2 es = grp_sum<TG>(make_double2(e, 0.0), part, tl);
+        if (tl == 0 && valid) {
+            if (bad) {
+                a.shift[p] = -1;
+                a.theta[p] = __longlong_as_double(0x7ff8000000000000LL);
+                a.energy[p] = __longlong_as_double(0x7ff8000000000000LL);
+                a.status[p] = FA_STATUS_NONFINITE;
+            } else {
+                a.shift[p] = sbest;
+                a.theta[p] = atan2(c.y, c.x);
+                a.energy[p] = es.x / (double)n;
+                a.status[p] = FA_STATUS_OK;
+            }
         }
     }
 }
 
-template <int T>
-constexpr size_t ragged_smem() { return (size_t)BMAX * 16 + (T + 1) * 16 + (T / 32) * 12 + 16; }
-
-template <int T, typename ZT>
-int launch_t(const fa_handle* h, const RaggedArgs& a, const Tables& tb, int grid, cudaStream_t st)
+template <int T, int G>
+constexpr size_t ragged_smem()
 {
-    ragged_kernel<T, ZT><<<grid, T, ragged_smem<T>(), st>>>(a, tb);
-    return cuda_error(cudaGetLastError(), "ragged launch");
+    constexpr int TG = T / G, SW = TG >= 32 ? TG / 32 : 1;
+    return (size_t)BMAX * 16 + (size_t)G * (TG + 1) * 16 + (size_t)G * SW * 12 + 4 * (1 + G) + 16;
+}
+
+// the plans compiled in: (T, G)
+struct PlanDesc { int T, G; };
+constexpr PlanDesc kPlans[] = {{256, 1}, {512, 1}, {1024, 1}, {128, 2}, {256, 2}, {512, 2},
+                               {128, 4}, {256, 4}, {512, 4}, {256, 8}, {256, 16}};
+constexpr int kNPlans = sizeof(kPlans) / sizeof(kPlans[0]);
+
+template <int T, int G>
+const void* kernel_ptr(bool f64)
+{
+    return f64 ? (const void*)ragged_kernel<T, G, double2> : (const void*)ragged_kernel<T, G, float2>;
+}
+
+// f(kernel pointer, smem bytes) for plan i
+template <typename F>
+auto with_plan(int i, bool f64, F&& f)
+{
+    switch (i) {
+#define FA_PLAN(k, T_, G_) \
+    case k: return f(kernel_ptr<T_, G_>(f64), ragged_smem<T_, G_>(), T_);
+        FA_PLAN(0, 256, 1) FA_PLAN(1, 512, 1) FA_PLAN(2, 1024, 1) FA_PLAN(3, 128, 2)
+        FA_PLAN(4, 256, 2) FA_PLAN(5, 512, 2) FA_PLAN(6, 128, 4) FA_PLAN(7, 256, 4)
+        FA_PLAN(8, 512, 4) FA_PLAN(9, 256, 8) FA_PLAN(10, 256, 16)
+#undef FA_PLAN
+    }
+    return f(kernel_ptr<256, 1>(f64), ragged_smem<256, 1>(), 256);
 }
 
 // longest transform over all node counts n <= max_n: a non-power-of-two n just
@@ -281,73 +396,150 @@ int64_t lmax_for(int max_n)
 
 inline size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-}  // namespace
-
-int ragged_grid(const fa_handle* h, int T)
+int plan_grid(const fa_handle* h, int i)
 {
     int per_sm = 1;
-    cudaError_t e = cudaSuccess;
-    switch (T) {
-        case 1024: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ragged_kernel<1024, double2>, 1024, ragged_smem<1024>()); break;
-        case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ragged_kernel<512, double2>, 512, ragged_smem<512>()); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ragged_kernel<256, double2>, 256, ragged_smem<256>()); break;
-    }
+    const cudaError_t e = with_plan(i, true, [&](const void* k, size_t smem, int T) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, smem);
+    });
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     return per_sm * h->num_sms;
 }
 
+Tables make_tables(const fa_handle* h)
+{
+    Tables tb;
+    for (int i = 0; i <= LOG_BMAX; ++i) tb.tf[i] = (i >= kMinLogN) ? h->tf64[i] : nullptr;
+    for (int i = 0; i <= kMaxRaggedLogL; ++i) tb.tw[i] = (i >= kMinLogN) ? h->tw64[i] : nullptr;
+    return tb;
+}
+
+int launch_bucket(const fa_handle* h, RaggedArgs a, const Tables& tb, int bucket, int plan,
+                  bool f64, cudaStream_t st)
+{
+    a.bucket = bucket;
+    const int grid = plan_grid(h, plan);
+    const cudaError_t e = with_plan(plan, f64, [&](const void* k, size_t smem, int T) {
+        void* args[] = {(void*)&a, (void*)&tb};
+        return cudaLaunchKernel(k, dim3((unsigned)grid), dim3((unsigned)T), args, smem, st);
+    });
+    return cuda_error(e, "ragged launch");
+}
+
+}  // namespace
+
+int ragged_num_plans() { return kNPlans; }
+int ragged_plan_threads(int i) { return (i >= 0 && i < kNPlans) ? kPlans[i].T : 0; }
+int ragged_plan_group(int i) { return (i >= 0 && i < kNPlans) ? kPlans[i].G : 0; }
+
+// can plan i run transforms of length 2^bucket?
+bool ragged_plan_fits(int i, int bucket)
+{
+    if (i < 0 || i >= kNPlans) return false;
+    const int G = kPlans[i].G, L = 1 << bucket;
+    if (G == 1) return true;
+    return L <= BMAX / (2 * G) && kPlans[i].T / G <= L;
+}
+
+int ragged_default_plan(int bucket)
+{
+    const int L = 1 << bucket;
+    if (L <= 128) return 10;   // 16 pairs of 16 threads
+    if (L <= 256) return 9;    // 8 pairs of 32 threads
+    if (L <= 512) return 7;    // 4 pairs of 64 threads
+    if (L <= 1024) return 4;   // 2 pairs of 128 threads
+    return 0;                  // one pair of 256 threads
+}
+
 int ragged_set_attributes()
 {
-    const void* ks[] = {(const void*)ragged_kernel<1024, double2>, (const void*)ragged_kernel<1024, float2>,
-                        (const void*)ragged_kernel<256, double2>, (const void*)ragged_kernel<256, float2>,
-                        (const void*)ragged_kernel<512, double2>, (const void*)ragged_kernel<512, float2>};
-    const size_t sm[] = {ragged_smem<1024>(), ragged_smem<1024>(), ragged_smem<256>(),
-                         ragged_smem<256>(), ragged_smem<512>(), ragged_smem<512>()};
-    for (int i = 0; i < 6; ++i) {
-        cudaError_t e = cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[i]);
-        if (e != cudaSuccess) return cuda_error(e, "ragged: cudaFuncSetAttribute");
-    }
+    for (int i = 0; i < kNPlans; ++i)
+        for (int f = 0; f < 2; ++f) {
+            const cudaError_t e = with_plan(i, f == 0, [&](const void* k, size_t smem, int) {
+                return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            });
+            if (e != cudaSuccess) return cuda_error(e, "ragged: cudaFuncSetAttribute");
+        }
     return FA_OK;
 }
 
 size_t ragged_ws_bytes(const fa_handle* h, int64_t P, int max_n)
 {
-    const int grid = std::max(ragged_grid(h, 1024), std::max(ragged_grid(h, 256), ragged_grid(h, 512)));
+    int grid = 1;
+    for (int i = 0; i < kNPlans; ++i)
+        if (kPlans[i].G == 1) grid = std::max(grid, plan_grid(h, i));
     const int64_t L = lmax_for(max_n);
     return a256(kCounterBytes) + a256((size_t)P * sizeof(int)) +
            (size_t)grid * 2 * (size_t)L * sizeof(double2);
 }
 
-int launch_align_ragged(const fa_handle* h, const void* z1, const void* z2, const int64_t* off,
-                        int64_t P, int max_n, int ztype, int threads, int32_t* shift,
-                        double* theta, double* energy, int8_t* status, void* ws,
-                        cudaStream_t st)
+int ragged_max_bucket(int max_n)
 {
-    if (P == 0) return FA_OK;
+    int b = 2;
+    while ((1ll << b) < lmax_for(max_n)) ++b;
+    return b;
+}
+
+// counters, bucket histogram and the longest-first work list
+int ragged_prepare(const int64_t* off, int64_t P, int max_n, void* ws, int32_t* shift,
+                   double* theta, double* energy, int8_t* status, cudaStream_t st)
+{
     char* w = static_cast<char*>(ws);
     RaggedCounters* cnt = reinterpret_cast<RaggedCounters*>(w);
     int* order = reinterpret_cast<int*>(w + a256(kCounterBytes));
-    double2* slots = reinterpret_cast<double2*>(w + a256(kCounterBytes) + a256((size_t)P * sizeof(int)));
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(RaggedCounters), st);
     if (e != cudaSuccess) return cuda_error(e, "ragged: memset");
     const unsigned nb = (unsigned)((P + 255) / 256);
     ragged_keys_kernel<<<nb, 256, 0, st>>>(off, P, max_n, cnt, shift, theta, energy, status);
     ragged_order_kernel<<<nb, 256, 0, st>>>(off, P, max_n, cnt, order);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "ragged: keys/order launch");
+    return cuda_error(cudaGetLastError(), "ragged: keys/order launch");
+}
+
+// the bucket counts of the last ragged_prepare (device -> host, synchronises)
+int ragged_hist(void* ws, int* hist, cudaStream_t st)
+{
+    RaggedCounters c;
+    cudaError_t e = cudaMemcpyAsync(&c, ws, sizeof(RaggedCounters), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "ragged: histogram");
+    for (int b = 0; b < kBuckets; ++b) hist[b] = c.hist[b];
+    return FA_OK;
+}
+
+int ragged_run_bucket(const fa_handle* h, const void* z1, const void* z2, const int64_t* off,
+                      int64_t P, int max_n, int ztype, int bucket, int plan, int32_t* shift,
+                      double* theta, double* energy, int8_t* status, void* ws, bool reset,
+                      cudaStream_t st)
+{
+    char* w = static_cast<char*>(ws);
+    RaggedCounters* cnt = reinterpret_cast<RaggedCounters*>(w);
+    if (reset) {
+        const cudaError_t e = cudaMemsetAsync(&cnt->bhead[bucket], 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_error(e, "ragged: memset");
+    }
     RaggedArgs a;
-    a.z1 = z1; a.z2 = z2; a.off = off; a.P = P; a.max_n = max_n; a.cnt = cnt; a.order = order;
-    a.slots = slots; a.slot_elems = 2 * lmax_for(max_n);
+    a.z1 = z1; a.z2 = z2; a.off = off; a.P = P; a.max_n = max_n; a.cnt = cnt;
+    a.order = reinterpret_cast<int*>(w + a256(kCounterBytes));
+    a.slots = reinterpret_cast<double2*>(w + a256(kCounterBytes) + a256((size_t)P * sizeof(int)));
+    a.slot_elems = 2 * lmax_for(max_n);
     a.shift = shift; a.theta = theta; a.energy = energy; a.status = status;
-    Tables tb;
-    for (int i = 0; i <= LOG_BMAX; ++i) tb.tf[i] = (i >= kMinLogN) ? h->tf64[i] : nullptr;
-    for (int i = 0; i <= kMaxRaggedLogL; ++i) tb.tw[i] = (i >= kMinLogN) ? h->tw64[i] : nullptr;
-    const int T = (threads == 1024 || threads == 512) ? threads : 256;
-    const int grid = ragged_grid(h, T);
-    const bool f64 = ztype == FA_Z_F64;
-    if (T == 1024) return f64 ? launch_t<1024, double2>(h, a, tb, grid, st) : launch_t<1024, float2>(h, a, tb, grid, st);
-    if (T == 512) return f64 ? launch_t<512, double2>(h, a, tb, grid, st) : launch_t<512, float2>(h, a, tb, grid, st);
-    return f64 ? launch_t<256, double2>(h, a, tb, grid, st) : launch_t<256, float2>(h, a, tb, grid, st);
+    return launch_bucket(h, a, make_tables(h), bucket, plan, ztype == FA_Z_F64, st);
+}
+
+int launch_align_ragged(const fa_handle* h, const void* z1, const void* z2, const int64_t* off,
+                        int64_t P, int max_n, int ztype, int32_t* shift, double* theta,
+                        double* energy, int8_t* status, void* ws, cudaStream_t st)
+{
+    if (P == 0) return FA_OK;
+    int rc = ragged_prepare(off, P, max_n, ws, shift, theta, energy, status, st);
+    if (rc != FA_OK) return rc;
+    // longest transforms first (their launch's tail is covered by the next)
+    for (int b = ragged_max_bucket(max_n); b >= kMinLogN; --b) {
+        rc = ragged_run_bucket(h, z1, z2, off, P, max_n, ztype, b, h->ragged_plan[b], shift, theta,
+                               energy, status, ws, false, st);
+        if (rc != FA_OK) return rc;
+    }
+    return FA_OK;
 }
 
 }  // namespace fa

@@ -149,6 +149,7 @@ int fa_create(fa_handle** out, int device)
     fa_handle* h = new (std::nothrow) fa_handle();
     if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_create: out of host memory");
     h->device = device;
+    for (int b = 0; b < 16; ++b) h->ragged_plan[b] = ragged_default_plan(b);
     DeviceGuard g(device);
     if (g.rc != FA_OK) { delete h; return g.rc; }
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -310,8 +311,8 @@ int fa_align_pairs_ragged(fa_handle* h, const void* z1, const void* z2, const in
         int rc = ragged_check(h, z1, z2, offsets, P, max_n, ztype, shift, theta, energy, status,
                               workspace, workspace_bytes, &ws);
         if (rc != FA_OK || P == 0) return rc;
-        return launch_align_ragged(h, z1, z2, offsets, P, max_n, ztype, h->ragged_threads, shift,
-                                   theta, energy, status, ws, static_cast<cudaStream_t>(stream));
+        return launch_align_ragged(h, z1, z2, offsets, P, max_n, ztype, shift, theta, energy,
+                                   status, ws, static_cast<cudaStream_t>(stream));
     }
     return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged: null handle");
 }
@@ -330,39 +331,86 @@ int fa_align_pairs_ragged_autotune(fa_handle* h, const void* z1, const void* z2,
                           workspace, workspace_bytes, &ws);
     if (rc != FA_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int cand[3] = {256, 512, 1024};
-    float best_ms = -1.f;
-    int best = h->ragged_threads;
+    if (P == 0) {
+        if (chosen_threads) *chosen_threads = ragged_plan_threads(h->ragged_plan[ragged_max_bucket(max_n)]);
+        return FA_OK;
+    }
+    // which buckets the batch fills
+    rc = ragged_prepare(offsets, P, max_n, ws, shift, theta, energy, status, st);
+    int hist[16] = {};
+    if (rc == FA_OK) rc = ragged_hist(ws, hist, st);
+    if (rc != FA_OK) return rc;
     cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    for (int c = 0; c < 3 && P > 0; ++c) {
-        rc = launch_align_ragged(h, z1, z2, offsets, P, max_n, ztype, cand[c], shift, theta,
-                                 energy, status, ws, st);  // warm-up
-        if (rc != FA_OK) break;
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < 3 && rc == FA_OK; ++r)
-            rc = launch_align_ragged(h, z1, z2, offsets, P, max_n, ztype, cand[c], shift, theta,
-                                     energy, status, ws, st);
-        cudaEventRecord(e1, st);
-        cudaError_t e = cudaEventSynchronize(e1);
-        if (rc != FA_OK || e != cudaSuccess) { if (rc == FA_OK) rc = cuda_error(e, "autotune"); break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = cand[c]; }
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_error(e, "autotune: events");
+    int top = -1;
+    for (int b = ragged_max_bucket(max_n); b >= kMinLogN && rc == FA_OK; --b) {
+        h->ragged_plan_ms[b] = 0.f;
+        if (hist[b] == 0) continue;
+        if (top < 0) top = b;
+        // every compiled plan that fits this length: one warm-up, three timed runs
+        float best_ms = -1.f;
+        int best = h->ragged_plan[b];
+        for (int pl = 0; pl < ragged_num_plans() && rc == FA_OK; ++pl) {
+            if (!ragged_plan_fits(pl, b)) continue;
+            rc = ragged_run_bucket(h, z1, z2, offsets, P, max_n, ztype, b, pl, shift, theta, energy,
+                                   status, ws, true, st);
+            if (rc != FA_OK) break;
+            e = cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && rc == FA_OK && e == cudaSuccess; ++r)
+                rc = ragged_run_bucket(h, z1, z2, offsets, P, max_n, ztype, b, pl, shift, theta,
+                                       energy, status, ws, true, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (rc == FA_OK && e != cudaSuccess) rc = cuda_error(e, "autotune");
+            if (rc != FA_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 3.f;
+            if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = pl; }
+        }
+        h->ragged_plan[b] = best;
+        h->ragged_plan_ms[b] = best_ms > 0.f ? best_ms : 0.f;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != FA_OK) return rc;
-    // leave the outputs of the chosen configuration (sums run in a CTA-size
-    // dependent order, so other sizes can differ in the last bit)
-    if (P > 0) {
-        rc = launch_align_ragged(h, z1, z2, offsets, P, max_n, ztype, best, shift, theta, energy,
-                                 status, ws, st);
-        if (rc != FA_OK) return rc;
+    // leave the outputs of the chosen plans (sums run in a plan-dependent
+    // order, so other plans can differ in the last bit)
+    rc = launch_align_ragged(h, z1, z2, offsets, P, max_n, ztype, shift, theta, energy, status, ws, st);
+    if (rc != FA_OK) return rc;
+    if (chosen_threads) *chosen_threads = ragged_plan_threads(h->ragged_plan[top >= 0 ? top : ragged_max_bucket(max_n)]);
+    return FA_OK;
+}
+
+int fa_align_pairs_ragged_set_plan(fa_handle* h, int32_t bucket, int32_t threads,
+                                   int32_t pairs_per_cta)
+{
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged_set_plan: null handle");
+    if (bucket < kMinLogN || bucket > kMaxRaggedLogL)
+        return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged_set_plan: bucket outside [2, 14]");
+    for (int pl = 0; pl < ragged_num_plans(); ++pl)
+        if (ragged_plan_threads(pl) == threads && ragged_plan_group(pl) == pairs_per_cta) {
+            if (!ragged_plan_fits(pl, bucket))
+                return set_error(FA_ERR_UNSUPPORTED,
+                                 "fa_align_pairs_ragged_set_plan: plan does not fit this length");
+            h->ragged_plan[bucket] = pl;
+            h->ragged_plan_ms[bucket] = 0.f;
+            return FA_OK;
+        }
+    return set_error(FA_ERR_UNSUPPORTED, "fa_align_pairs_ragged_set_plan: no such compiled plan");
+}
+
+int fa_align_pairs_ragged_plan(fa_handle* h, int32_t* threads, int32_t* pairs_per_cta, float* ms)
+{
+    if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_align_pairs_ragged_plan: null handle");
+    for (int b = 0; b < 16; ++b) {
+        const int pl = h->ragged_plan[b];
+        if (threads) threads[b] = b >= kMinLogN && b <= kMaxRaggedLogL ? ragged_plan_threads(pl) : 0;
+        if (pairs_per_cta) pairs_per_cta[b] = b >= kMinLogN && b <= kMaxRaggedLogL ? ragged_plan_group(pl) : 0;
+        if (ms) ms[b] = h->ragged_plan_ms[b];
     }
-    h->ragged_threads = best;
-    if (chosen_threads) *chosen_threads = best;
     return FA_OK;
 }
 

@@ -7,15 +7,16 @@
 
 namespace fa {
 
-// In-place forward DFT of X[0, B), B = 2^logb in [4, BMAX], by all T threads
-// of the CTA (Stockham stages as in fft_stages.cuh with runtime sizes; each
-// thread holds its butterflies in registers between the two barriers).
+// In-place forward DFT of X[0, B), B = 2^logb in [4, BMAX], by a group of T
+// threads whose local index is tid (Stockham stages as in fft_stages.cuh with
+// runtime sizes; each thread holds its butterflies in registers between the
+// two barriers).  The barriers are CTA-wide: every group of the CTA calls it
+// at the same time with the same B.
 template <int T, int BMAX>
-__device__ void fft_rt(double2* X, int logb, const double2* __restrict__ Wf)
+__device__ void fft_rt_g(double2* X, int logb, const double2* __restrict__ Wf, int tid)
 {
     constexpr int MAX4 = BMAX / 4 / T > 0 ? BMAX / 4 / T : 1;  // radix-4 butterflies per thread
     const int B = 1 << logb, Q = B >> 2, H = B >> 1;
-    const int tid = threadIdx.x;
     double2 v[MAX4][4];  // one register block for both stage kinds
     int ns = 1;
     if (logb & 1) {
@@ -69,6 +70,13 @@ __device__ void fft_rt(double2* X, int logb, const double2* __restrict__ Wf)
         }
         __syncthreads();
     }
+}
+
+// the whole CTA (T threads) as one group
+template <int T, int BMAX>
+__device__ __forceinline__ void fft_rt(double2* X, int logb, const double2* __restrict__ Wf)
+{
+    fft_rt_g<T, BMAX>(X, logb, Wf, threadIdx.x);
 }
 
 template <int T>

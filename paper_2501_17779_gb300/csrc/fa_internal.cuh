@@ -20,7 +20,11 @@ struct fa_handle {
     // |cos| >= |sin| (e <= N/8 or e >= 3N/8), else W_N^e = m (rho + i); |rho| <= 1
     double2* tf64[13] = {};
     float4* tdf[13] = {};   // W_N[k] in double-float (re.h, re.l, im.h, im.l), FA_PREC_MIXED
-    int ragged_threads = 256;  // CTA size of the ragged persistent kernel (autotuned)
+    // fa_align_pairs_ragged: the plan (index into the compiled (CTA size, pairs
+    // per CTA) set) of each transform-length bucket log2 L, and the time per
+    // bucket of the last autotuning (ms, 0 when untuned)
+    int ragged_plan[16] = {};
+    float ragged_plan_ms[16] = {};
     // handle-owned scratch, used when the caller passes no workspace
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -127,13 +131,24 @@ int launch_align_all_tc(const fa_handle* h, const void* z, int64_t M, int logn, 
 int launch_align_all(const fa_handle* h, const void* z, int64_t M, int logn, int ztype, void* ws,
                      int8_t* status, int32_t* shift, double* theta, double* energy,
                      cudaStream_t st);
-int ragged_grid(const fa_handle* h, int threads);
 int ragged_set_attributes();
 size_t ragged_ws_bytes(const fa_handle* h, int64_t P, int max_n);
+int ragged_num_plans();
+int ragged_plan_threads(int plan);
+int ragged_plan_group(int plan);
+bool ragged_plan_fits(int plan, int bucket);
+int ragged_default_plan(int bucket);
+int ragged_max_bucket(int max_n);
+int ragged_prepare(const int64_t* off, int64_t P, int max_n, void* ws, int32_t* shift,
+                   double* theta, double* energy, int8_t* status, cudaStream_t st);
+int ragged_hist(void* ws, int* hist, cudaStream_t st);
+int ragged_run_bucket(const fa_handle* h, const void* z1, const void* z2, const int64_t* off,
+                      int64_t P, int max_n, int ztype, int bucket, int plan, int32_t* shift,
+                      double* theta, double* energy, int8_t* status, void* ws, bool reset,
+                      cudaStream_t st);
 int launch_align_ragged(const fa_handle* h, const void* z1, const void* z2, const int64_t* off,
-                        int64_t P, int max_n, int ztype, int threads, int32_t* shift,
-                        double* theta, double* energy, int8_t* status, void* ws,
-                        cudaStream_t st);
+                        int64_t P, int max_n, int ztype, int32_t* shift, double* theta,
+                        double* energy, int8_t* status, void* ws, cudaStream_t st);
 // counter: the kernel's 8-byte work counter, or nullptr for the one at the end
 // of ws; stage_curve0: the first curve's row in ws's complex128 staging area
 // (FA_STORE_FP32).  Launches that share one workspace concurrently (disjoint

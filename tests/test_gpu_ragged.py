@@ -92,9 +92,10 @@ def test_ragged_max_n_bound_and_complex64():
 
 
 def test_ragged_graph_capture_and_autotune():
-    """The whole call (memset + three launches) captured in a CUDA graph and
-    replayed gives the same result as a direct call; the autotuner picks one of
-    its CTA sizes and leaves a valid result."""
+    """The whole call (a memset, the bucketing launches and one launch per
+    transform-length bucket) captured in a CUDA graph and replayed gives the
+    same result as a direct call; the autotuner picks a plan per bucket and
+    leaves a valid result."""
     sizes = synth.log_uniform_sizes(9, 300, 64, 4096)
     rp = synth.ragged_aligned_pairs(25, sizes, min_harm=4, max_harm=16)
     z1, z2, offs = _dev(rp)
@@ -102,6 +103,10 @@ def test_ragged_graph_capture_and_autotune():
     ws = torch.empty(api.ragged_workspace_size(P, 4096), dtype=torch.uint8, device=DEV)
     ref = api.align_pairs_ragged(z1, z2, offs, max_n=4096, workspace=ws, autotune=True)
     torch.cuda.synchronize()
+    plan = api.ragged_plan()
+    tuned = {b: v for b, v in plan.items() if v[2] > 0}
+    print("autotuned plans (log2 L: threads, pairs per CTA, ms):", tuned)
+    assert tuned  # at least one bucket was timed
     ref = [x.clone() for x in ref]
     out = tuple(torch.empty_like(x) for x in ref)
     st = torch.cuda.Stream()
@@ -138,3 +143,56 @@ def test_ragged_large_batch_sampled():
     for p in idx:
         check_align(a1[o[p]:o[p + 1]][None], a2[o[p]:o[p + 1]][None], s[[p]], th[[p]], e[[p]],
                     st[[p]])
+
+
+PLANS = [(256, 1), (512, 1), (1024, 1), (128, 2), (256, 2), (512, 2), (128, 4), (256, 4),
+         (512, 4), (256, 8), (256, 16)]
+
+
+def test_ragged_every_plan_on_every_bucket_it_fits():
+    """Each compiled plan (CTA size, pairs per CTA), pinned on every transform
+    length it can run, against the FP64 oracle: buckets log2 L = 2..14 with
+    several pairs each (partly filled multi-pair CTAs included), powers of two
+    and padded lengths, one radix-R split length per R."""
+    sizes = [4, 5, 7, 9, 16, 17, 20, 33, 60, 64, 65, 100, 128, 129, 200, 256, 257, 300, 400,
+             512, 513, 700, 1000, 1024, 1025, 1500, 2048, 2049, 3000, 4096, 4097, 6000, 8192]
+    rp = synth.ragged_aligned_pairs(26, sizes, min_harm=2, max_harm=12)
+    z1, z2, offs = _dev(rp)
+    P, n = _split(rp)
+    orc = {}
+    for N in np.unique(n):
+        idx = np.nonzero(n == N)[0]
+        a = np.stack([rp.z1[rp.offsets[p]:rp.offsets[p + 1]] for p in idx])
+        b = np.stack([rp.z2[rp.offsets[p]:rp.offsets[p + 1]] for p in idx])
+        orc[N] = (idx, a, b, oracle.align_pairs(a, b))
+    L = np.array([m if m & (m - 1) == 0 else 1 << int(2 * m - 1).bit_length() for m in n])
+    buckets = sorted(set(int(np.log2(x)) for x in L))
+    try:
+        for T, G in PLANS:
+            used = []
+            for b in buckets:
+                try:
+                    api.set_ragged_plan(b, T, G)
+                    used.append(b)
+                except RuntimeError:
+                    api.set_ragged_plan(b, 256, 1)
+            s, th, e, st = [x.cpu().numpy() for x in api.align_pairs_ragged(z1, z2, offs,
+                                                                            max_n=8192)]
+            for N, (idx, a, b, o) in orc.items():
+                check_align(a, b, s[idx], th[idx], e[idx], st[idx], o)
+            print(f"plan ({T}, {G}) ran on buckets {used}")
+            assert used  # every plan fits some length of this batch
+    finally:
+        for b in range(2, 15):
+            api.set_ragged_plan(b, 256, 1)
+
+
+def test_ragged_plan_rejects_what_does_not_fit():
+    with pytest.raises(RuntimeError):
+        api.set_ragged_plan(12, 256, 4)   # 4 pairs of 4096 points exceed shared memory
+    with pytest.raises(RuntimeError):
+        api.set_ragged_plan(5, 256, 2)    # 128 threads per 32-point pair
+    with pytest.raises(RuntimeError):
+        api.set_ragged_plan(8, 384, 1)    # not compiled
+    plan = api.ragged_plan()
+    assert set(plan) == set(range(2, 15)) and all(t > 0 and g >= 1 for t, g, _ in plan.values())
