@@ -46,8 +46,8 @@ SEED = 1002
 # at capture time; a kernel whose sources have changed since reports no traffic.
 TRAFFIC_FILE = Path(__file__).resolve().parent / "profiles" / "dram_traffic.txt"
 KERNEL_SOURCES = {
-    "resample_kernel": ("resample.cu", "fa_internal.cuh"),
-    "align_fft_kernel": ("align_fft.cu", "fft_stages.cuh", "align_common.cuh", "fa_internal.cuh"),
+    "resample_kernel": ("resample.cu", "df.cuh"),
+    "align_fft_kernel": ("align_fft.cu", "fft_stages.cuh", "align_common.cuh"),
 }
 
 
@@ -124,6 +124,28 @@ def resample_flops(n_in: np.ndarray, N: int) -> int:
     per_chunk = 6 + 14 + 18 * levels + 14 - 7
     tot = 8 * n + 34 * (n - P) + per_chunk * P + 36 * N + 650
     return int(tot.sum())
+
+
+def elastic_flops(lm_steps: np.ndarray, iters: np.ndarray, N: int) -> int:
+    """FP64 flops (FMA = 2) of fa_elastic_distance, counted from the kernel's
+    algorithm per unit of work (the float32 lattice programme is not FP64
+    work and is left out):
+      per refinement (Levenberg-Marquardt) step and node: the trial point's
+        cell pass 180 (Catmull-Rom value, slope and curvature of q2 at the
+        cell midpoint 96, sqrt of the slope 2, residual 10, Jacobian and
+        curvature terms 52, reductions 20), the normal-equation rows 40, the
+        three-right-hand-side tridiagonal solve counted as Thomas 18, the
+        Schur-complement sums 10, the step and its shortening 12 = 260
+      per outer iteration ((t0,R)-step): two transforms 10 N log2 N, the
+        reparameterised samples 36 N, product, |c|^2, c(s*), energy 27 N
+      per pair: the pre-alignment (three transforms 15 N log2 N, product,
+        |c|^2 and c(s*) 17 N), the SRV samples of both curves 24 N, the
+        arc-length resampling of both curves 2 (42 + 36) N"""
+    lg = int(np.log2(N))
+    steps = np.asarray(lm_steps, np.int64).sum()
+    it = np.asarray(iters, np.int64).sum()
+    P = np.asarray(iters).size
+    return int(260 * N * steps + (10 * N * lg + 63 * N) * it + P * (15 * N * lg + 197 * N))
 
 
 def ragged_flops(sizes: np.ndarray) -> int:
@@ -720,8 +742,9 @@ def run_gpu(args):
         c1, c2 = ce[:Pe].contiguous(), ce[Pe:].contiguous()
         ews = torch.empty(api.elastic_workspace_size(Pe, Pe, Pe, Ne, Be, local), dtype=torch.uint8,
                           device=dev)
+        lms = torch.empty(Pe, dtype=torch.int32, device=dev)
         with torch.cuda.stream(stream):
-            eo = api.elastic_distance(c1, c2, band=Be, workspace=ews)
+            eo = api.elastic_distance(c1, c2, band=Be, workspace=ews, lm_steps=lms)
             torch.cuda.synchronize(dev)
             e0.record(stream)
             for _ in range(3):
@@ -729,9 +752,18 @@ def run_gpu(args):
             e1.record(stream)
         torch.cuda.synchronize(dev)
         ela_ms = e0.elapsed_time(e1) / 3
+        el_fl = elastic_flops(lms.cpu().numpy(), eo[3].cpu().numpy(), Ne)
         ela = {"workload": f"{Pe} pairs, N={Ne}, lattice band {Be}, gallery curves (50 classes, "
                            "harmonic perturbation 0.03, random smooth reparameterisation), FP64",
                "ms": ela_ms, "pairs_per_s": Pe / (ela_ms * 1e-3),
+               "lm_steps_mean": float(lms.double().mean().item()),
+               "roofline": {"bound": "alu", "peak": fp64_peak, "unit": "TFLOP/s",
+                            "achieved": el_fl / (ela_ms * 1e-3) / 1e12,
+                            "frac": el_fl / (ela_ms * 1e-3) / 1e12 / fp64_peak,
+                            "flops_per_launch": el_fl,
+                            "count": "FP64 flops counted per refinement step, outer iteration "
+                                     "and pair from the kernel's algorithm (bench.py "
+                                     "elastic_flops); the float32 lattice programme excluded"},
                "iterations_mean": float(eo[3].double().mean().item()),
                "iterations_max": int(eo[3].max().item()),
                "distance_mean": float(torch.sqrt(eo[2]).mean().item()),

@@ -256,6 +256,9 @@ int fa_align_all_pairs(fa_handle* h, const void* z, int64_t M, int32_t N, int32_
  *   energy     double[P]  E of the final triple (the distance is sqrt(E))
  *   gamma      double[P][N+1] node values g_k, or NULL
  *   iters      int32[P]   iterations run, or NULL
+ *   lm_steps   int32[P]   Levenberg-Marquardt steps taken by the gamma-steps
+ *              (their sum over the iterations; the unit of most of the FP64
+ *              work, for throughput accounting), or NULL
  *   status     int8[P]    FA_STATUS_OK, _DEGENERATE (a curve of zero length or
  *              fewer than 4 distinct nodes), _NONFINITE, _BAD_SIZE
  *   workspace  device scratch of fa_elastic_workspace_size(h, M1, M2, P, N, band)
@@ -270,7 +273,8 @@ int fa_elastic_distance(fa_handle* h, const double* curves1, int64_t M1, const d
                         int64_t M2, int32_t N, const int64_t* idx1, const int64_t* idx2,
                         int64_t P, int32_t band, int32_t max_iter, int32_t* shift,
                         double* theta, double* energy, double* gamma, int32_t* iters,
-                        int8_t* status, void* workspace, size_t workspace_bytes, void* stream);
+                        int32_t* lm_steps, int8_t* status, void* workspace,
+                        size_t workspace_bytes, void* stream);
 
 /*
  * Alignment of P pairs with DIFFERENT node counts, one persistent launch per

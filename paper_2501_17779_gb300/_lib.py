@@ -121,7 +121,7 @@ def load(build_if_missing: bool = False):
     L.fa_elastic_workspace_size.argtypes = [vp, i64, i64, i64, i32, i32]
     L.fa_elastic_workspace_size.restype = sz
     L.fa_elastic_distance.argtypes = [vp, vp, i64, vp, i64, i32, vp, vp, i64, i32, i32, vp, vp, vp,
-                                      vp, vp, vp, vp, sz, vp]
+                                      vp, vp, vp, vp, vp, sz, vp]
     L.fa_elastic_distance.restype = ctypes.c_int
     for name, args in (
             ("fa_fourier_descriptors", [vp, vp, i64, i32, i32, vp, vp]),

@@ -249,14 +249,16 @@ def elastic_workspace_size(M1: int, M2: int, P: int, N: int, band: int = -1,
 def elastic_distance(curves1: torch.Tensor, curves2: torch.Tensor, *,
                      idx1: torch.Tensor | None = None, idx2: torch.Tensor | None = None,
                      band: int = -1, max_iter: int = 20, gamma: bool = False,
-                     workspace: torch.Tensor | None = None, out: tuple | None = None):
+                     workspace: torch.Tensor | None = None, out: tuple | None = None,
+                     lm_steps: torch.Tensor | None = None):
     """Elastic shape distance (fa_elastic_distance).
 
     curves1 [M1, N], curves2 [M2, N]: complex128 CUDA tensors, node k of a curve
     at parameter k/N.  Pair p is (idx1[p], idx2[p]) (int64 CUDA tensors) or,
     without them, (p, p).  Returns (shift int32, theta, energy, iters int32,
     status int8) [P] each, plus gamma [P, N+1] when ``gamma``; the distance is
-    sqrt(energy).
+    sqrt(energy).  ``lm_steps`` (int32 CUDA tensor [P]) receives the
+    refinement steps each pair took.
     """
     _need_cuda("curves1", curves1, torch.complex128)
     _need_cuda("curves2", curves2, torch.complex128)
@@ -291,8 +293,8 @@ def elastic_distance(curves1: torch.Tensor, curves2: torch.Tensor, *,
         workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     rc = L.fa_elastic_distance(h, _ptr(curves1), M1, _ptr(curves2), M2, N, _ptr(idx1),
                                _ptr(idx2), P, band, max_iter, _ptr(shift), _ptr(theta),
-                               _ptr(energy), _ptr(g), _ptr(iters), _ptr(status), _ptr(workspace),
-                               workspace.numel(), _stream_ptr(dev))
+                               _ptr(energy), _ptr(g), _ptr(iters), _ptr(lm_steps), _ptr(status),
+                               _ptr(workspace), workspace.numel(), _stream_ptr(dev))
     _lib.check(rc)
     res = (shift, theta, energy, iters, status)
     return res + (g,) if gamma else res

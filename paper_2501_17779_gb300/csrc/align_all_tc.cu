@@ -50,7 +50,9 @@
 namespace fa {
 namespace {
 
-constexpr int kTcT = 128;      // threads per CTA = pairs per tile = TMEM lanes
+constexpr int kTcT = 128;           // pairs per tile = TMEM lanes
+constexpr int kTcProducers = 256;   // two threads per pair form its operand row
+constexpr int kTcThreads = kTcProducers + 32;  // and one warp issues copies and MMAs
 constexpr int kRowB = 64;      // bytes per operand row per K chunk
 constexpr int kStages = 3;
 constexpr int kCand = 8;       // candidate shifts kept per pair
@@ -58,29 +60,40 @@ constexpr float kPScale = 16384.0f;  // 2^14: cross-spectra scale (float16 range
 
 template <int V>
 struct TcVar;
+// MARGIN: a candidate whose GEMM |c|^2 is below (1 - MARGIN) times the best
+// one's cannot be the maximum when the GEMM's relative error on |c|^2 is at
+// most eps with MARGIN >= 2 eps (the best candidate is then >= (1 - eps) T and
+// the largest value seen <= (1 + eps) T, T the true maximum), so it is not
+// re-scored.  eps is about 6e-5 for bfloat16 pieces (16 bits) and 2e-6 for
+// float16 / TF32 pieces (21-22 bits); the margins below are 65x and 250x that.
+// Plain TF32 (11 bits) re-scores all 8.
 template <>
 struct TcVar<FA_PREC_TC_BF16X3> {
     static constexpr int ES = 2, NP = 2;
     static constexpr uint32_t FMT = 1;  // bfloat16 (kind::f16)
     static constexpr bool TF32 = false;
+    static constexpr float MARGIN = 1.0f / 256.0f;
 };
 template <>
 struct TcVar<FA_PREC_TC_FP16X3> {
     static constexpr int ES = 2, NP = 2;
     static constexpr uint32_t FMT = 0;  // float16 (kind::f16)
     static constexpr bool TF32 = false;
+    static constexpr float MARGIN = 1.0f / 2048.0f;
 };
 template <>
 struct TcVar<FA_PREC_TC_TF32> {
     static constexpr int ES = 4, NP = 1;
     static constexpr uint32_t FMT = 2;  // tf32 (kind::tf32)
     static constexpr bool TF32 = true;
+    static constexpr float MARGIN = 2.0f;  // keeps every candidate
 };
 template <>
 struct TcVar<FA_PREC_TC_TF32X3> {
     static constexpr int ES = 4, NP = 2;
     static constexpr uint32_t FMT = 2;
     static constexpr bool TF32 = true;
+    static constexpr float MARGIN = 1.0f / 2048.0f;
 };
 
 // round a float to TF32 (10 fraction bits), to nearest even
@@ -189,8 +202,16 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
 }
 
 // ---- the GEMM + top-8 kernel --------------------------------------------------
+// Warp roles: warps 0-7 produce the cross-spectrum operand rows (two threads
+// per pair) and warps 0-3 also read the accumulators (TMEM lane = pair);
+// lane 0 of warp 8 starts the bulk copies of the DFT blocks (one chunk ahead)
+// and issues the MMAs.  Per stage: b_full (copy landed), a_full (the 256
+// producers stored their rows), mma_done (the stage's MMAs finished, it may be
+// overwritten).  Two accumulators of 256 columns alternate between column
+// blocks: acc_full[b] (block finished) and tmem_empty[b] (its 128 readers are
+// done), so the MMAs of the next block overlap the epilogue of this one.
 template <int V, int LOGN>
-__global__ void __launch_bounds__(kTcT, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     tc_search_kernel(const float2* __restrict__ spec, int64_t M, const uint8_t* __restrict__ tab,
                      uint16_t* __restrict__ cand, unsigned long long* __restrict__ next,
                      int* __restrict__ err)
@@ -203,35 +224,51 @@ __global__ void __launch_bounds__(kTcT, 1)
     constexpr uint32_t B_BYTES = (uint32_t)(B_PIECE * T::NP);
     constexpr uint32_t ID = umma::idesc(128, 256, T::FMT);
     constexpr int NT = T::NP == 2 ? 3 : 1;
+    constexpr int KH = KF / 2;  // frequencies per half row
     extern __shared__ __align__(1024) uint8_t smem[];
     float2* zi_s = reinterpret_cast<float2*>(smem + kStages * STAGE);                  // [N]
     uint64_t* b_full = reinterpret_cast<uint64_t*>(smem + kStages * STAGE + N * 8);    // [kStages]
-    uint64_t* mma_done = b_full + kStages;                                             // [kStages]
-    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(mma_done + kStages);
+    uint64_t* a_full = b_full + kStages;                                               // [kStages]
+    uint64_t* mma_done = a_full + kStages;                                             // [kStages]
+    uint64_t* acc_full = mma_done + kStages;                                           // [2]
+    uint64_t* tmem_empty = acc_full + 2;                                               // [2]
+    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(tmem_empty + 2);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(s_taddr + 1);
     long long* s_tile = reinterpret_cast<long long*>(s_taddr + 2);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool producer = tid < kTcProducers;
+    const int row = tid & (kTcT - 1), half = (tid >> 7) & 1;  // pair and half row (producers)
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             umma::mbar_init(&b_full[s], 1);
+            umma::mbar_init(&a_full[s], kTcProducers);
             umma::mbar_init(&mma_done[s], 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            umma::mbar_init(&acc_full[b], 1);
+            umma::mbar_init(&tmem_empty[b], kTcT);
+        }
+        *s_abort = 0;
         umma::fence_mbar_init();
     }
-    if (warp == 0) umma::tmem_alloc(s_taddr, 256);
+    if (warp == 0) umma::tmem_alloc(s_taddr, 512);
     umma::tc_fence_before();
     __syncthreads();
     umma::tc_fence_after();
     const uint32_t tmem = *s_taddr;
     const int64_t total_tiles = ceil_sum128(M - 1);
-    int64_t g = 0;  // chunks issued by this CTA (stage = g % kStages, use = g / kStages)
-    bool ok = true;
+    int64_t g = 0, cbg = 0;  // chunks and column blocks so far (producers and the issuer alike)
+    auto fail = [&]() {
+        *s_abort = 1;
+        atomicExch(err, 1);
+    };
 
     for (;;) {
         if (tid == 0) *s_tile = (long long)atomicAdd(next, 1ull);
         __syncthreads();
         const int64_t t = *s_tile;
-        if (t >= total_tiles || !ok) break;
+        if (t >= total_tiles || *s_abort) break;
         // tile -> (i, j-tile): largest i with tiles_before(i) <= t
         int64_t lo = 0, hi = M - 2;
         while (lo < hi) {
@@ -240,144 +277,317 @@ __global__ void __launch_bounds__(kTcT, 1)
         }
         const int64_t i = lo;
         const int64_t j0 = i + 1 + 128 * (t - (ceil_sum128(M - 1) - ceil_sum128(M - 1 - i)));
-        const int64_t j = j0 + tid;
-        const bool valid = j < M;
-        for (int k = tid; k < N; k += kTcT) zi_s[k] = spec[i * N + k];
+        if (producer)
+            for (int k = tid; k < N; k += kTcProducers) zi_s[k] = spec[i * N + k];
         __syncthreads();
-        const float2* zj = spec + (valid ? j : i) * N;
 
-        float best[kCand];
-        int bs[kCand];
+        if (producer) {
+            const int64_t j = j0 + row;
+            const bool valid = j < M;
+            const float2* zj = spec + (valid ? j : i) * N + half * KH;
+            // this thread's spectrum values of the next two chunks (loads in
+            // flight two chunks ahead: they come from L2 with its latency)
+            float2 zb[KH], zb2[KH];
 #pragma unroll
-        for (int q = 0; q < kCand; ++q) { best[q] = -1.0f; bs[q] = 0; }
+            for (int q = 0; q < KH; ++q) {
+                zb[q] = valid ? zj[q] : make_float2(0.f, 0.f);
+                zb2[q] = valid ? zj[(1 % NK) * KF + q] : make_float2(0.f, 0.f);
+            }
+            float best[kCand];
+            int bs[kCand];
+#pragma unroll
+            for (int q = 0; q < kCand; ++q) { best[q] = -1.0f; bs[q] = 0; }
 
-        for (int cb = 0; cb < NCB && ok; ++cb) {
-            for (int kc = 0; kc < NK; ++kc, ++g) {
-                const int st = (int)(g % kStages);
-                const uint32_t use = (uint32_t)(g / kStages);
-                uint8_t* sa = smem + st * STAGE;
-                uint8_t* sb = sa + A_PIECE * T::NP;
-                if (use > 0)
-                    ok = __syncthreads_and(umma::mbar_wait(&mma_done[st], (use - 1) & 1) ? 1 : 0);
-                if (!ok) break;
-                if (tid == 0) {
-                    mbar_expect_tx(&b_full[st], B_BYTES);
-                    bulk_g2s(sb, tab + ((size_t)cb * NK + kc) * B_BYTES, B_BYTES, &b_full[st]);
-                }
-                // this pair's cross-spectrum row: frequencies f0 .. f0 + KF - 1
-                const int f0 = kc * KF;
-                uint32_t ph[KC], pl[KC];
+            for (int cb = 0; cb < NCB && !*s_abort; ++cb) {
+                for (int kc = 0; kc < NK; ++kc, ++g) {
+                    const int st = (int)(g % kStages);
+                    const uint32_t use = (uint32_t)(g / kStages);
+                    uint8_t* sa = smem + st * STAGE;
+                    if (*s_abort) break;
+                    if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) { fail(); break; }
+                    // this pair's cross-spectrum half row (frequencies f0 .. f0 + KH - 1)
+                    const int f0 = kc * KF + half * KH;
+                    uint32_t ph[KC / 2], pl[KC / 2];
 #pragma unroll
-                for (int q = 0; q < KF; ++q) {
-                    const float2 a = zi_s[f0 + q];
-                    const float2 b = valid ? zj[f0 + q] : make_float2(0.f, 0.f);
-                    const float pr = __fmul_rn(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), kPScale);
-                    const float pi = __fmul_rn(__fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y)), kPScale);
-                    to_pieces<V>(pr, ph[2 * q], pl[2 * q]);
-                    to_pieces<V>(pi, ph[2 * q + 1], pl[2 * q + 1]);
-                }
-#pragma unroll
-                for (int c16 = 0; c16 < kRowB / 16; ++c16) {
-                    uint4 vh, vl;
-                    if constexpr (T::ES == 2) {
-                        const int b0 = c16 * 8;
-                        vh = make_uint4(ph[b0] | (ph[b0 + 1] << 16), ph[b0 + 2] | (ph[b0 + 3] << 16),
-                                        ph[b0 + 4] | (ph[b0 + 5] << 16), ph[b0 + 6] | (ph[b0 + 7] << 16));
-                        vl = make_uint4(pl[b0] | (pl[b0 + 1] << 16), pl[b0 + 2] | (pl[b0 + 3] << 16),
-                                        pl[b0 + 4] | (pl[b0 + 5] << 16), pl[b0 + 6] | (pl[b0 + 7] << 16));
-                    } else {
-                        const int b0 = c16 * 4;
-                        vh = make_uint4(ph[b0], ph[b0 + 1], ph[b0 + 2], ph[b0 + 3]);
-                        vl = make_uint4(pl[b0], pl[b0 + 1], pl[b0 + 2], pl[b0 + 3]);
+                    for (int q = 0; q < KH; ++q) {
+                        const float2 a = zi_s[f0 + q];
+                        const float2 b = zb[q];
+                        const float pr = __fmul_rn(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), kPScale);
+                        const float pi = __fmul_rn(__fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y)), kPScale);
+                        to_pieces<V>(pr, ph[2 * q], pl[2 * q]);
+                        to_pieces<V>(pi, ph[2 * q + 1], pl[2 * q + 1]);
                     }
-                    const uint32_t off = umma::tile_off(tid, c16 * 16, kRowB);
-                    *reinterpret_cast<uint4*>(sa + off) = vh;
-                    if (T::NP > 1) *reinterpret_cast<uint4*>(sa + A_PIECE + off) = vl;
+                    {   // the chunk after next (K chunks wrap to the first ones for
+                        // the next column block)
+                        const int fn = ((kc + 2) % NK) * KF;
+#pragma unroll
+                        for (int q = 0; q < KH; ++q) {
+                            zb[q] = zb2[q];
+                            zb2[q] = valid ? zj[fn + q] : make_float2(0.f, 0.f);
+                        }
+                    }
+#pragma unroll
+                    for (int cc = 0; cc < kRowB / 32; ++cc) {
+                        const int c16 = half * (kRowB / 32) + cc;
+                        uint4 vh, vl;
+                        if constexpr (T::ES == 2) {
+                            const int b0 = cc * 8;
+                            vh = make_uint4(ph[b0] | (ph[b0 + 1] << 16), ph[b0 + 2] | (ph[b0 + 3] << 16),
+                                            ph[b0 + 4] | (ph[b0 + 5] << 16), ph[b0 + 6] | (ph[b0 + 7] << 16));
+                            vl = make_uint4(pl[b0] | (pl[b0 + 1] << 16), pl[b0 + 2] | (pl[b0 + 3] << 16),
+                                            pl[b0 + 4] | (pl[b0 + 5] << 16), pl[b0 + 6] | (pl[b0 + 7] << 16));
+                        } else {
+                            const int b0 = cc * 4;
+                            vh = make_uint4(ph[b0], ph[b0 + 1], ph[b0 + 2], ph[b0 + 3]);
+                            vl = make_uint4(pl[b0], pl[b0 + 1], pl[b0 + 2], pl[b0 + 3]);
+                        }
+                        const uint32_t off = umma::tile_off(row, c16 * 16, kRowB);
+                        *reinterpret_cast<uint4*>(sa + off) = vh;
+                        if (T::NP > 1) *reinterpret_cast<uint4*>(sa + A_PIECE + off) = vl;
+                    }
+                    umma::fence_async_smem();
+                    umma::mbar_arrive(&a_full[st]);
                 }
-                umma::fence_async_smem();
-                __syncthreads();
-                if (tid == 0) {
-                    bool landed = umma::mbar_wait(&b_full[st], use & 1);
-                    if (!landed) {
-                        atomicExch(err, 1);
-                    } else {
-                        umma::tc_fence_after();
-                        const uint32_t a0 = umma::smem_u32(sa), b0 = umma::smem_u32(sb);
-                        constexpr int PA[3] = {0, 0, 1}, PB[3] = {0, 1, 0};
+                if (*s_abort) break;
+                // warps 0-3: this column block's |c(s)|^2 into the running top 8
+                const int buf = (int)(cbg & 1);
+                if (half == 0) {
+                    if (!umma::mbar_wait(&acc_full[buf], (uint32_t)(cbg >> 1) & 1)) { fail(); break; }
+                    umma::tc_fence_after();
+#pragma unroll 1
+                    for (int c0 = 0; c0 < 128; c0 += 32) {
+                        float re[32], im[32];
+                        const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 256);
+                        umma::tmem_ld32(base + (uint32_t)c0, re);
+                        umma::tmem_ld32(base + (uint32_t)(128 + c0), im);
 #pragma unroll
-                        for (int ks = 0; ks < 2; ++ks) {
+                        for (int q = 0; q < 32; ++q) {
+                            float x = __fmaf_rn(re[q], re[q], __fmul_rn(im[q], im[q]));
+                            if (x > best[kCand - 1]) {
+                                int sx = cb * 128 + c0 + q;
 #pragma unroll
-                            for (int tt = 0; tt < NT; ++tt) {
-                                const uint64_t ad = umma::sdesc(a0 + (uint32_t)(PA[tt] * A_PIECE) + ks * 256,
-                                                                128, kRowB * 8);
-                                const uint64_t bd = umma::sdesc(b0 + (uint32_t)(PB[tt] * B_PIECE) + ks * 256,
-                                                                128, kRowB * 8);
-                                const uint32_t acc = (kc > 0 || ks > 0 || tt > 0) ? 1u : 0u;
-                                if constexpr (T::TF32) umma::mma_tf32(tmem, ad, bd, ID, acc);
-                                else umma::mma_f16(tmem, ad, bd, ID, acc);
+                                for (int r = 0; r < kCand; ++r) {
+                                    if (x > best[r]) {
+                                        const float tv = best[r];
+                                        const int ts = bs[r];
+                                        best[r] = x; bs[r] = sx;
+                                        x = tv; sx = ts;
+                                    }
+                                }
                             }
+                        }
+                    }
+                    umma::tc_fence_before();
+                    umma::mbar_arrive(&tmem_empty[buf]);
+                }
+                ++cbg;
+            }
+            if (valid && half == 0 && !*s_abort) {
+                // candidates that can still be the maximum (see TcVar::MARGIN); the
+                // count rides in bits 12-15 of the first entry (shifts < 4096)
+                int keep = 0;
+#pragma unroll
+                for (int q = 0; q < kCand; ++q)
+                    keep += best[q] >= __fmul_rn(best[0], 1.0f - T::MARGIN) ? 1 : 0;
+                keep = max(keep, 1);
+                uint4 w;
+                w.x = (uint32_t)bs[0] | ((uint32_t)keep << 12) | ((uint32_t)bs[1] << 16);
+                w.y = (uint32_t)bs[2] | ((uint32_t)bs[3] << 16);
+                w.z = (uint32_t)bs[4] | ((uint32_t)bs[5] << 16);
+                w.w = (uint32_t)bs[6] | ((uint32_t)bs[7] << 16);
+                *reinterpret_cast<uint4*>(cand + ((size_t)i * M + j) * kCand) = w;
+            }
+        } else if (lane == 0) {
+            // the issuer: DFT blocks one chunk ahead, MMAs, commits
+            auto copy_b = [&](int64_t gg, int cb, int kc) -> bool {
+                const int st = (int)(gg % kStages);
+                const uint32_t use = (uint32_t)(gg / kStages);
+                if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) return false;
+                mbar_expect_tx(&b_full[st], B_BYTES);
+                bulk_g2s(smem + st * STAGE + A_PIECE * T::NP,
+                         tab + ((size_t)cb * NK + kc) * B_BYTES, B_BYTES, &b_full[st]);
+                return true;
+            };
+            for (int cb = 0; cb < NCB && !*s_abort; ++cb) {
+                const int buf = (int)(cbg & 1);
+                if (cbg >= 2 && !umma::mbar_wait(&tmem_empty[buf], (uint32_t)((cbg >> 1) - 1) & 1)) {
+                    fail();
+                    break;
+                }
+                if (!copy_b(g, cb, 0)) { fail(); break; }
+                for (int kc = 0; kc < NK; ++kc, ++g) {
+                    const int st = (int)(g % kStages);
+                    const uint32_t use = (uint32_t)(g / kStages);
+                    if (*s_abort) break;
+                    if (kc + 1 < NK && !copy_b(g + 1, cb, kc + 1)) { fail(); break; }
+                    if (!umma::mbar_wait(&b_full[st], use & 1) || !umma::mbar_wait(&a_full[st], use & 1)) {
+                        fail();
+                        break;
+                    }
+                    umma::tc_fence_after();
+                    const uint32_t a0 = umma::smem_u32(smem + st * STAGE);
+                    const uint32_t b0 = a0 + (uint32_t)(A_PIECE * T::NP);
+                    constexpr int PA[3] = {0, 0, 1}, PB[3] = {0, 1, 0};
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+                        for (int tt = 0; tt < NT; ++tt) {
+                            const uint64_t ad = umma::sdesc(a0 + (uint32_t)(PA[tt] * A_PIECE) + ks * 256,
+                                                            128, kRowB * 8);
+                            const uint64_t bd = umma::sdesc(b0 + (uint32_t)(PB[tt] * B_PIECE) + ks * 256,
+                                                            128, kRowB * 8);
+                            const uint32_t acc = (kc > 0 || ks > 0 || tt > 0) ? 1u : 0u;
+                            if constexpr (T::TF32) umma::mma_tf32(tmem + buf * 256, ad, bd, ID, acc);
+                            else umma::mma_f16(tmem + buf * 256, ad, bd, ID, acc);
                         }
                     }
                     umma::mma_commit(&mma_done[st]);
                 }
+                if (*s_abort) break;
+                umma::mma_commit(&acc_full[buf]);
+                ++cbg;
             }
-            if (!ok) break;
-            // this column block's |c(s)|^2 into the running top 8
-            const int64_t gl = g - 1;
-            ok = __syncthreads_and(
-                     umma::mbar_wait(&mma_done[gl % kStages], (uint32_t)(gl / kStages) & 1) ? 1 : 0) != 0;
-            if (!ok) break;
-            umma::tc_fence_after();
-#pragma unroll 1
-            for (int c0 = 0; c0 < 128; c0 += 32) {
-                float re[32], im[32];
-                umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, re);
-                umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(128 + c0), im);
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    float x = __fmaf_rn(re[q], re[q], __fmul_rn(im[q], im[q]));
-                    if (x > best[kCand - 1]) {
-                        int sx = cb * 128 + c0 + q;
-#pragma unroll
-                        for (int r = 0; r < kCand; ++r) {
-                            if (x > best[r]) {
-                                const float tv = best[r];
-                                const int ts = bs[r];
-                                best[r] = x; bs[r] = sx;
-                                x = tv; sx = ts;
-                            }
-                        }
-                    }
-                }
-            }
-            umma::tc_fence_before();
-            __syncthreads();
-        }
-        if (!ok) break;
-        if (valid) {
-            uint4 w;
-            w.x = (uint32_t)bs[0] | ((uint32_t)bs[1] << 16);
-            w.y = (uint32_t)bs[2] | ((uint32_t)bs[3] << 16);
-            w.z = (uint32_t)bs[4] | ((uint32_t)bs[5] << 16);
-            w.w = (uint32_t)bs[6] | ((uint32_t)bs[7] << 16);
-            *reinterpret_cast<uint4*>(cand + ((size_t)i * M + j) * kCand) = w;
         }
     }
-    if (!ok && tid == 0) atomicExch(err, 1);
+    // every MMA this CTA issued has finished before the tensor memory is freed
+    if (warp == kTcProducers / 32 && lane == 0 && g > 0 && !*s_abort) {
+        const int64_t gl = g - 1;
+        if (!umma::mbar_wait(&mma_done[gl % kStages], (uint32_t)(gl / kStages) & 1)) atomicExch(err, 1);
+    }
     umma::tc_fence_before();
     __syncthreads();
-    if (warp == 0) umma::tmem_dealloc(tmem, 256);
+    if (warp == 0) umma::tmem_dealloc(tmem, 512);
 }
 
 // ---- re-score of the candidates, theta and energy (one warp per pair) --------
 template <typename ZT>
 __device__ __forceinline__ cdf ld_df(const ZT* p, int64_t k) { return split_c(p[k]); }
 
+// a b in float-float (exact leading product by FMA)
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+
 __device__ __forceinline__ dfl shfl_df(dfl v, int off)
 {
     return {__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)};
 }
 
+// one pair's re-score by a whole warp: the best candidate shift, c(s*) and the
+// energy in float-float (every lane ends with the same values)
+struct Rescored {
+    int s;
+    dfl cre, cim, e;
+};
+
+template <int LOGN, typename ZT>
+__device__ __forceinline__ Rescored rescore_pair(const ZT* __restrict__ z, int64_t i, int64_t j,
+                                                 int64_t M, const uint16_t* __restrict__ cand,
+                                                 int lane)
+{
+    constexpr int N = 1 << LOGN, R = N / 32;
+    const int64_t ij = i * M + j;
+    const ZT* zi = z + i * N;
+    const ZT* zj = z + j * N;
+    const uint4 cw = *reinterpret_cast<const uint4*>(cand + (size_t)ij * kCand);
+    long long bkey = -1;
+    int sbest = 0;
+    cdf cbest{{0.f, 0.f}, {0.f, 0.f}};
+    const int keep = (int)((cw.x >> 12) & 15u);
+#pragma unroll 1
+    for (int c = 0; c < keep; ++c) {
+        const uint32_t w = c < 2 ? cw.x : c < 4 ? cw.y : c < 6 ? cw.z : cw.w;
+        const int s = (int)((w >> (16 * (c & 1))) & 0xfffu) & (N - 1);
+        cdf acc{{0.f, 0.f}, {0.f, 0.f}};
+        if constexpr (std::is_same<ZT, float2>::value) {
+            // complex64 inputs: each product of two floats is exactly p + e
+            // (e by FMA); the p are summed by two-sums into (h, l), the small
+            // terms straight into l, normalised once at the end
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float2 u = zi[lane + 32 * r];
+                const float2 v = zj[(lane + 32 * r + s) & (N - 1)];
+                const float p1 = __fmul_rn(u.x, v.x), e1 = __fmaf_rn(u.x, v.x, -p1);
+                const float p2 = __fmul_rn(u.y, v.y), e2 = __fmaf_rn(u.y, v.y, -p2);
+                const float p3 = __fmul_rn(u.y, v.x), e3 = __fmaf_rn(u.y, v.x, -p3);
+                const float p4 = __fmul_rn(-u.x, v.y), e4 = __fmaf_rn(-u.x, v.y, -p4);
+                dfl t = two_sum(acc.re.h, p1);
+                const dfl t2 = two_sum(t.h, p2);
+                acc.re.h = t2.h;
+                acc.re.l = __fadd_rn(acc.re.l, __fadd_rn(__fadd_rn(t.l, t2.l), __fadd_rn(e1, e2)));
+                t = two_sum(acc.im.h, p3);
+                const dfl t4 = two_sum(t.h, p4);
+                acc.im.h = t4.h;
+                acc.im.l = __fadd_rn(acc.im.l, __fadd_rn(__fadd_rn(t.l, t4.l), __fadd_rn(e3, e4)));
+            }
+            acc.re = fast_two_sum(acc.re.h, acc.re.l);
+            acc.im = fast_two_sum(acc.im.h, acc.im.l);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const cdf b = ld_df(zj, (lane + 32 * r + s) & (N - 1));
+                // a conj(b)
+                const cdf ar = ld_df(zi, lane + 32 * r);
+                acc.re = df_add(acc.re, df_dot2<+1>(ar.re, b.re, ar.im, b.im));
+                acc.im = df_add(acc.im, df_dot2<-1>(ar.im, b.re, ar.re, b.im));
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            acc.re = df_add(acc.re, shfl_df(acc.re, off));
+            acc.im = df_add(acc.im, shfl_df(acc.im, off));
+        }
+        const long long key = df_key(cnorm2(acc));
+        if (key > bkey || (key == bkey && s < sbest)) { bkey = key; sbest = s; cbest = acc; }
+    }
+    // the rotation e^{i theta} = c / |c| in float-float (every lane holds the
+    // reduced c(s*); FP64 only for theta itself, on one lane below)
+    dfl rx{1.f, 0.f}, ry{0.f, 0.f};
+    {
+        const dfl n2 = cnorm2(cbest);
+        if (n2.h > 0.f) {
+            const float s0 = __fsqrt_rn(n2.h);
+            const float pp = __fmul_rn(s0, s0), pe = __fmaf_rn(s0, s0, -pp);
+            const float res = __fadd_rn(__fsub_rn(__fsub_rn(n2.h, pp), pe), n2.l);
+            const dfl r = fast_two_sum(s0, __fmul_rn(res, __fdiv_rn(0.5f, s0)));  // |c|
+            const float r0 = __fdiv_rn(1.0f, r.h);
+            const float q = __fmul_rn(r.h, r0), qe = __fmaf_rn(r.h, r0, -q);
+            const float e1 = __fsub_rn(__fsub_rn(1.0f, q), __fmaf_rn(r.l, r0, qe));
+            const dfl inv = fast_two_sum(r0, __fmul_rn(r0, e1));  // 1/|c|
+            rx = df_mul(cbest.re, inv);
+            ry = df_mul(cbest.im, inv);
+        }
+    }
+    // energy h sum_k |z_i[k] - e^{i theta} z_j[k + s*]|^2 in float-float
+    dfl e{0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const cdf b = ld_df(zj, (lane + 32 * r + sbest) & (N - 1));
+        const dfl bxr = df_dot2<-1>(rx, b.re, ry, b.im);  // Re(e^{i theta} b)
+        const dfl byr = df_dot2<+1>(ry, b.re, rx, b.im);  // Im(e^{i theta} b)
+        const cdf ar = ld_df(zi, lane + 32 * r);
+        const dfl dx = df_sub(ar.re, bxr), dy = df_sub(ar.im, byr);
+        e = df_add(e, df_dot2<+1>(dx, dx, dy, dy));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e = df_add(e, shfl_df(e, off));
+    Rescored out;
+    out.s = sbest;
+    out.cre = cbest.re;
+    out.cim = cbest.im;
+    out.e = e;
+    return out;
+}
+
+// One warp per pair: the re-score in float-float by all lanes, then theta
+// (FP64 atan2) and the outputs by lane 0.  (Handing each lane a different
+// pair's FP64 finish, 32 pairs per warp, measured slower: fewer warps in
+// flight for the FP32 work that dominates.)
 template <int LOGN, typename ZT>
 __global__ void __launch_bounds__(256)
     tc_rescore_kernel(const ZT* __restrict__ z, int64_t M, const uint16_t* __restrict__ cand,
@@ -385,7 +595,7 @@ __global__ void __launch_bounds__(256)
                       int32_t* __restrict__ shift, double* __restrict__ theta,
                       double* __restrict__ energy)
 {
-    constexpr int N = 1 << LOGN, R = N / 32;
+    constexpr int N = 1 << LOGN;
     const int lane = threadIdx.x & 31;
     const int64_t npairs = M * (M - 1) / 2;
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -410,60 +620,16 @@ __global__ void __launch_bounds__(256)
         }
         return;
     }
-    const ZT* zi = z + i * N;
-    const ZT* zj = z + j * N;
-    cdf a[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) a[r] = ld_df(zi, lane + 32 * r);
-    const uint4 cw = *reinterpret_cast<const uint4*>(cand + (size_t)ij * kCand);
-    long long bkey = -1;
-    int sbest = 0;
-    cdf cbest{{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll 1
-    for (int c = 0; c < kCand; ++c) {
-        const uint32_t w = c < 2 ? cw.x : c < 4 ? cw.y : c < 6 ? cw.z : cw.w;
-        const int s = (int)((w >> (16 * (c & 1))) & 0xffffu) & (N - 1);
-        cdf acc{{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const cdf b = ld_df(zj, (lane + 32 * r + s) & (N - 1));
-            // a conj(b)
-            acc.re = df_add(acc.re, df_dot2<+1>(a[r].re, b.re, a[r].im, b.im));
-            acc.im = df_add(acc.im, df_dot2<-1>(a[r].im, b.re, a[r].re, b.im));
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            acc.re = df_add(acc.re, shfl_df(acc.re, off));
-            acc.im = df_add(acc.im, shfl_df(acc.im, off));
-        }
-        const long long key = df_key(cnorm2(acc));
-        if (key > bkey || (key == bkey && s < sbest)) { bkey = key; sbest = s; cbest = acc; }
-    }
-    // theta = arg c(s*), the rotation e^{i theta} = c / |c| in FP64 (one pair)
-    const double cx = (double)cbest.re.h + (double)cbest.re.l;
-    const double cy = (double)cbest.im.h + (double)cbest.im.l;
-    const double rr = sqrt(fma(cx, cx, cy * cy));
-    const double ux = rr > 0.0 ? cx / rr : 1.0, uy = rr > 0.0 ? cy / rr : 0.0;
-    const dfl rx = split_d(ux), ry = split_d(uy);
-    // energy h sum_k |z_i[k] - e^{i theta} z_j[k + s*]|^2 in float-float
-    dfl e{0.f, 0.f};
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const cdf b = ld_df(zj, (lane + 32 * r + sbest) & (N - 1));
-        const dfl bxr = df_dot2<-1>(rx, b.re, ry, b.im);  // Re(e^{i theta} b)
-        const dfl byr = df_dot2<+1>(ry, b.re, rx, b.im);  // Im(e^{i theta} b)
-        const dfl dx = df_sub(a[r].re, bxr), dy = df_sub(a[r].im, byr);
-        e = df_add(e, df_dot2<+1>(dx, dx, dy, dy));
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) e = df_add(e, shfl_df(e, off));
+    const Rescored r = rescore_pair<LOGN, ZT>(z, i, j, M, cand, lane);
     if (lane == 0) {
+        const double cx = (double)r.cre.h + (double)r.cre.l;
+        const double cy = (double)r.cim.h + (double)r.cim.l;
         const double th = atan2(cy, cx);
-        const double en = ((double)e.h + (double)e.l) * (1.0 / N);
-        shift[ij] = sbest;
+        const double en = ((double)r.e.h + (double)r.e.l) * (1.0 / N);
+        shift[ij] = r.s;
         theta[ij] = th;
         energy[ij] = en;
-        shift[ji] = sbest ? N - sbest : 0;
+        shift[ji] = r.s ? N - r.s : 0;
         theta[ji] = (th == 3.141592653589793) ? th : -th;
         energy[ji] = en;
     }
@@ -517,13 +683,13 @@ int launch_tc(const fa_handle* h, const void* z, int64_t M, void* ws, int8_t* st
     rc = cuda_error(cudaGetLastError(), "all-pairs tc: setup launch");
     if (rc != FA_OK) return rc;
     constexpr size_t STAGE = (size_t)(128 + 256) * kRowB * T::NP;
-    const size_t smem = kStages * STAGE + (size_t)N * 8 + 2 * kStages * 8 + 32;
+    const size_t smem = kStages * STAGE + (size_t)N * 8 + (3 * kStages + 4) * 8 + 32;
     auto kern = tc_search_kernel<V, LOGN>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "all-pairs tc: cudaFuncSetAttribute");
     const int64_t tiles = ceil_sum128(M - 1);
     const int grid = (int)std::min<int64_t>(tiles, (int64_t)(h->num_sms > 0 ? h->num_sms : 1));
-    kern<<<grid, kTcT, smem, st>>>(spec32, M, tab, cand, next, err);
+    kern<<<grid, kTcThreads, smem, st>>>(spec32, M, tab, cand, next, err);
     rc = cuda_error(cudaGetLastError(), "all-pairs tc: search launch");
     if (rc != FA_OK) return rc;
     const int64_t npairs = M * (M - 1) / 2;

@@ -491,7 +491,8 @@ int fa_elastic_distance(fa_handle* h, const double* curves1, int64_t M1, const d
                         int64_t M2, int32_t N, const int64_t* idx1, const int64_t* idx2,
                         int64_t P, int32_t band, int32_t max_iter, int32_t* shift,
                         double* theta, double* energy, double* gamma, int32_t* iters,
-                        int8_t* status, void* workspace, size_t workspace_bytes, void* stream)
+                        int32_t* lm_steps, int8_t* status, void* workspace,
+                        size_t workspace_bytes, void* stream)
 {
     if (!h) return set_error(FA_ERR_INVALID_ARG, "fa_elastic_distance: null handle");
     if (M1 < 0 || M2 < 0 || P < 0)
@@ -525,7 +526,7 @@ int fa_elastic_distance(fa_handle* h, const double* curves1, int64_t M1, const d
         ws = h->ws;
     }
     return launch_elastic(h, curves1, M1, curves2, M2, N, idx1, idx2, P, band, max_iter, shift,
-                          theta, energy, gamma, iters, status, ws,
+                          theta, energy, gamma, iters, lm_steps, status, ws,
                           static_cast<cudaStream_t>(stream));
 }
 

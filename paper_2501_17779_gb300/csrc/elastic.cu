@@ -130,6 +130,7 @@ struct ElasticArgs {
     double* energy;
     double* gamma;          // nullable [P][N+1]
     int32_t* iters;         // nullable
+    int32_t* lm_steps;      // nullable: refinement steps taken per pair
     int8_t* status;
 };
 
@@ -441,7 +442,7 @@ __device__ __forceinline__ void cell_pass(const double2* q1, const double2* q2, 
 template <int T, int NMAX>
 __device__ double elastic_refine(const double2* q1, const double2* q2, int N, int s,
                                  double& theta, double* g0, double* gt0, CellBuf cur,
-                                 CellBuf alt, const LmArrays& L, double* red)
+                                 CellBuf alt, const LmArrays& L, double* red, int& steps)
 {
     const int tid = threadIdx.x;
     const int n = N - 1;
@@ -456,6 +457,7 @@ __device__ double elastic_refine(const double2* q1, const double2* q2, int N, in
     double En = h[7];
     double lambda = 1e-3;
     for (int it = 0; it < kLmIters; ++it) {
+        ++steps;
         for (int i = 1 + tid; i <= n; i += T) {
             const double2 b0 = cur.Bv[i - 1], a0 = cur.A[i - 1], a1 = cur.A[i], b1 = cur.Bv[i];
             const double2 r0 = cur.R[i - 1], r1 = cur.R[i];
@@ -646,6 +648,7 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
                 a.energy[pair] = nanv;
                 a.status[pair] = (int8_t)st;
                 if (a.iters) a.iters[pair] = 0;
+                if (a.lm_steps) a.lm_steps[pair] = 0;
             }
             if (a.gamma)
                 for (int k = tid; k <= N; k += T) a.gamma[pair * (N + 1) + k] = nanv;
@@ -703,7 +706,7 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
             elastic_dp<T>(N, B, q1f, reinterpret_cast<const float2*>(q2f),
                           reinterpret_cast<float*>(ar), bp, g);
         }
-        int it = 0;
+        int it = 0, lm = 0;
         double Eprev = HUGE_VAL, En = 0.0;
         if (a.max_iter == 0) {
             // no iteration: report the starting triple (pre-alignment s, theta
@@ -724,7 +727,7 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
             En = e[0] / (double)N;
         }
         for (it = 1; it <= a.max_iter; ++it) {
-            elastic_refine<T, NMAX>(q1, q2, N, s, theta, g, gt, cb0, cb1, L, red);
+            elastic_refine<T, NMAX>(q1, q2, N, s, theta, g, gt, cb0, cb1, L, red, lm);
             // (t0, R)-step on w_k = sqrt(D_k) q2(M_k)
             for (int k = tid; k < N; k += T) {
                 double2 v;
@@ -757,6 +760,7 @@ __global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__
             a.energy[pair] = En;
             a.status[pair] = FA_STATUS_OK;
             if (a.iters) a.iters[pair] = it;
+            if (a.lm_steps) a.lm_steps[pair] = lm;
         }
         if (a.gamma)
             for (int k = tid; k <= N; k += T) a.gamma[pair * (N + 1) + k] = g[k];
@@ -882,7 +886,8 @@ size_t elastic_ws_bytes(const fa_handle* h, int64_t M1, int64_t M2, int64_t P, i
 int launch_elastic(const fa_handle* h, const double* set1, int64_t M1, const double* set2,
                    int64_t M2, int N, const int64_t* idx1, const int64_t* idx2, int64_t P,
                    int band, int max_iter, int32_t* shift, double* theta, double* energy,
-                   double* gamma, int32_t* iters, int8_t* status, void* ws, cudaStream_t st)
+                   double* gamma, int32_t* iters, int32_t* lm_steps, int8_t* status, void* ws,
+                   cudaStream_t st)
 {
     const int64_t Mtot = M1 + M2;
     const ElLayout L = el_layout(h, Mtot, P, N, band);
@@ -928,6 +933,7 @@ int launch_elastic(const fa_handle* h, const double* set1, int64_t M1, const dou
                         : slots + (L.q2f_smem ? 0 : align256(sizeof(double2) * (size_t)L.q2f_elems * L.grid));
     A.tf = h->tf64[A.logn];
     A.shift = shift; A.theta = theta; A.energy = energy; A.gamma = gamma; A.iters = iters;
+    A.lm_steps = lm_steps;
     A.status = status;
     auto kern = N <= 256 ? elastic_pair_kernel<kElT, 256> : elastic_pair_kernel<kElT, 1024>;
     if (L.smem > 48 * 1024) {

@@ -163,6 +163,7 @@ size_t elastic_ws_bytes(const fa_handle* h, int64_t M1, int64_t M2, int64_t P, i
 int launch_elastic(const fa_handle* h, const double* set1, int64_t M1, const double* set2,
                    int64_t M2, int N, const int64_t* idx1, const int64_t* idx2, int64_t P,
                    int band, int max_iter, int32_t* shift, double* theta, double* energy,
-                   double* gamma, int32_t* iters, int8_t* status, void* ws, cudaStream_t st);
+                   double* gamma, int32_t* iters, int32_t* lm_steps, int8_t* status, void* ws,
+                   cudaStream_t st);
 
 }  // namespace fa

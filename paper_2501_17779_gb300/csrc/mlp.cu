@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
     uint32_t* s_taddr = reinterpret_cast<uint32_t*>(smem + 2 * STAGE + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t m0 = (int64_t)blockIdx.x * 128;
+    const int64_t m0 = (int64_t)blockIdx.x * 128, n0 = (int64_t)blockIdx.y * NT;
     const int64_t kb = (int64_t)blockIdx.z * g.kc;
     const int64_t ke = kb + g.kc < g.K ? kb + g.kc : g.K;
     const int nchunks = ke > kb ? (int)((ke - kb + kTcKC - 1) / kTcKC) : 0;
@@ -220,21 +220,74 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (c >= 2) ok = __syncthreads_and(umma::mbar_wait(&mbar[st], ((c - 2) >> 1) & 1) ? 1 : 0);
         if (!ok) break;
         const int64_t k0 = kb + (int64_t)c * kTcKC;
-        // A chunk: 128 rows x 32 k (walk the unit-stride index fastest)
-        for (int e = tid; e < 128 * kTcKC; e += kTcThreads) {
-            int r, k;
-            if (g.sak == 1) { r = e / kTcKC; k = e % kTcKC; } else { r = e % 128; k = e / 128; }
-            const int64_t m = m0 + r, kk = k0 + k;
-            const float x = (m < g.M && kk < ke) ? g.A[m * g.sam + kk * g.sak] : 0.0f;
-            tc_store_pieces(sa, A_PIECE, r, k, x, 3);
+        // A chunk: 128 rows x 32 k.  Row-major A: eight consecutive k per task,
+        // two float4 loads and one 16-byte store per piece; otherwise one
+        // element per task, the unit-stride index fastest (coalesced).
+        if (g.sak == 1) {
+            for (int e = tid; e < 128 * (kTcKC / 8); e += kTcThreads) {
+                const int r = e / (kTcKC / 8), kg = e % (kTcKC / 8);
+                const int64_t m = m0 + r, kk = k0 + kg * 8;
+                float x[8];
+                const float* src = g.A + m * g.sam + kk;
+                if (m < g.M && kk + 8 <= ke && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+                    const float4 u = *reinterpret_cast<const float4*>(src);
+                    const float4 v = *reinterpret_cast<const float4*>(src + 4);
+                    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
+                    x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) x[q] = (m < g.M && kk + q < ke) ? src[q] : 0.0f;
+                }
+                uint16_t h[8], md[8], l[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) umma::split3_bf16(x[q], h[q], md[q], l[q]);
+                const uint32_t off = umma::tile_off(r, kg * 16, 2 * kTcKC);
+                auto pack = [](const uint16_t* v) {
+                    return make_uint4(v[0] | ((uint32_t)v[1] << 16), v[2] | ((uint32_t)v[3] << 16),
+                                      v[4] | ((uint32_t)v[5] << 16), v[6] | ((uint32_t)v[7] << 16));
+                };
+                *reinterpret_cast<uint4*>(sa + off) = pack(h);
+                *reinterpret_cast<uint4*>(sa + A_PIECE + off) = pack(md);
+                *reinterpret_cast<uint4*>(sa + 2 * A_PIECE + off) = pack(l);
+            }
+        } else {
+            for (int e = tid; e < 128 * kTcKC; e += kTcThreads) {
+                const int r = e % 128, k = e / 128;
+                const int64_t m = m0 + r, kk = k0 + k;
+                const float x = (m < g.M && kk < ke) ? g.A[m * g.sam + kk * g.sak] : 0.0f;
+                tc_store_pieces(sa, A_PIECE, r, k, x, 3);
+            }
         }
-        // B chunk: NT rows (n) x 32 k
-        for (int e = tid; e < NT * kTcKC; e += kTcThreads) {
-            int n, k;
-            if (g.sbk == 1) { n = e / kTcKC; k = e % kTcKC; } else { n = e % NT; k = e / NT; }
-            const int64_t kk = k0 + k;
-            const float x = (n < g.N && kk < ke) ? to_f(g.B[kk * g.sbk + n * g.sbn]) : 0.0f;
-            tc_store_pieces(sb, B_PIECE, n, k, x, BP);
+        // B chunk: NT rows (n) x 32 k.  bfloat16 weights stored with k
+        // contiguous: eight at a time, copied as they are (one piece)
+        if (BP == 1 && g.sbk == 1) {
+            for (int e = tid; e < NT * (kTcKC / 8); e += kTcThreads) {
+                const int n = e / (kTcKC / 8), kg = e % (kTcKC / 8);
+                const int64_t nn = n0 + n, kk = k0 + kg * 8;
+                const TB* src = g.B + kk + nn * g.sbn;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (nn < g.N && kk + 8 <= ke && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+                    v = *reinterpret_cast<const uint4*>(src);
+                } else {
+                    uint16_t t[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        t[q] = (nn < g.N && kk + q < ke)
+                                   ? __bfloat16_as_ushort(__float2bfloat16_rn(to_f(src[q])))
+                                   : (uint16_t)0;
+                    v = make_uint4(t[0] | ((uint32_t)t[1] << 16), t[2] | ((uint32_t)t[3] << 16),
+                                   t[4] | ((uint32_t)t[5] << 16), t[6] | ((uint32_t)t[7] << 16));
+                }
+                *reinterpret_cast<uint4*>(sb + umma::tile_off(n, kg * 16, 2 * kTcKC)) = v;
+            }
+        } else {
+            for (int e = tid; e < NT * kTcKC; e += kTcThreads) {
+                int n, k;
+                if (g.sbk == 1) { n = e / kTcKC; k = e % kTcKC; } else { n = e % NT; k = e / NT; }
+                const int64_t nn = n0 + n, kk = k0 + k;
+                const float x = (nn < g.N && kk < ke) ? to_f(g.B[kk * g.sbk + nn * g.sbn]) : 0.0f;
+                tc_store_pieces(sb, B_PIECE, n, k, x, BP);
+            }
         }
         umma::fence_async_smem();
         __syncthreads();
@@ -267,10 +320,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         float* C = g.C + (int64_t)blockIdx.z * g.M * g.N;
         const int64_t m = m0 + warp * 32 + lane;
 #pragma unroll 1
-        for (int n0 = 0; n0 < NT; n0 += 32) {
+        for (int c0 = 0; c0 < NT; c0 += 32) {
             float v[32];
             if (nchunks > 0) {
-                umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0, v);
+                umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             } else {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = 0.0f;
@@ -278,7 +331,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (m < g.M) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int64_t n = n0 + j;
+                    const int64_t n = n0 + c0 + j;
                     if (n >= g.N) continue;
                     float x = v[j];
                     if constexpr (EPI == EPI_BIAS_RELU) x = fmaxf(x + g.bias[n], 0.0f);
@@ -298,7 +351,6 @@ template <typename TB, int NT, int EPI>
 int tc_gemm(const GemmArgs<float, TB>& a, int splits, int* err, cudaStream_t st)
 {
     if (a.M == 0 || a.N == 0) return FA_OK;
-    if (a.N > NT) return set_error(FA_ERR_UNSUPPORTED, "tc_gemm: N above the tile width");
     GemmArgs<float, TB> g = a;
     g.kc = (a.K + splits - 1) / splits;
     g.kc = (g.kc + kTcKC - 1) / kTcKC * kTcKC;
@@ -307,7 +359,7 @@ int tc_gemm(const GemmArgs<float, TB>& a, int splits, int* err, cudaStream_t st)
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "tc_gemm: cudaFuncSetAttribute");
-    const dim3 grid((unsigned)((a.M + 127) / 128), 1, (unsigned)splits);
+    const dim3 grid((unsigned)((a.M + 127) / 128), (unsigned)((a.N + NT - 1) / NT), (unsigned)splits);
     kern<<<grid, kTcThreads, smem, st>>>(g, err);
     return cuda_error(cudaGetLastError(), "tc_gemm launch");
 }
@@ -635,7 +687,7 @@ int ensure_mlp_ws(fa_mlp* m, size_t need)
     return FA_OK;
 }
 
-constexpr int kSplits = 16;
+constexpr int kSplits = 64;
 
 inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -654,15 +706,15 @@ int mlp_forward_into(const fa_mlp* m, const float* X, int64_t B, float* H1, floa
     g.M = B; g.N = kDh; g.K = kDin; g.A = X; g.sam = kDin; g.sak = 1;
     g.B = m->pb + kOffW1; g.sbk = 1; g.sbn = kDin; g.C = H1; g.scm = kDh; g.scn = 1;
     g.bias = m->p + kOffB1;
-    int rc = tc_gemm<__nv_bfloat16, kDh, EPI_BIAS_RELU>(g, 1, m->tc_err, st);
+    int rc = tc_gemm<__nv_bfloat16, 64, EPI_BIAS_RELU>(g, 1, m->tc_err, st);
     if (rc != FA_OK) return rc;
     g.K = kDh; g.A = H1; g.sam = kDh; g.B = m->pb + kOffW2; g.sbn = kDh; g.C = H2;
     g.bias = m->p + kOffB2;
-    rc = tc_gemm<__nv_bfloat16, kDh, EPI_BIAS_RELU>(g, 1, m->tc_err, st);
+    rc = tc_gemm<__nv_bfloat16, 64, EPI_BIAS_RELU>(g, 1, m->tc_err, st);
     if (rc != FA_OK) return rc;
     g.N = kDout; g.A = H2; g.B = m->pb + kOffW3; g.sbn = kDh; g.C = Y; g.scm = kDout;
     g.bias = m->p + kOffB3;
-    return tc_gemm<__nv_bfloat16, kDout, EPI_BIAS>(g, 1, m->tc_err, st);
+    return tc_gemm<__nv_bfloat16, 64, EPI_BIAS>(g, 1, m->tc_err, st);
 }
 
 // dW (out x in) = gH^T X over R rows, and db = column sums of gH, through the
@@ -673,8 +725,7 @@ int weight_grad(const float* gH, int64_t R, int out, const float* X, int in, flo
     GemmArgs<float, float> g{};
     g.M = out; g.N = in; g.K = R; g.A = gH; g.sam = 1; g.sak = out; g.B = X; g.sbk = in; g.sbn = 1;
     g.C = part; g.scm = in; g.scn = 1;
-    int rc = in > 64 ? tc_gemm<float, 256, EPI_NONE>(g, kSplits, tc_err, st)
-                     : tc_gemm<float, 64, EPI_NONE>(g, kSplits, tc_err, st);
+    int rc = tc_gemm<float, 64, EPI_NONE>(g, kSplits, tc_err, st);
     if (rc != FA_OK) return rc;
     split_sum_kernel<<<(unsigned)((out * in + 255) / 256), 256, 0, st>>>(part, kSplits,
                                                                         (int64_t)out * in, dW);
@@ -843,7 +894,7 @@ int fa_mlp_pair_grad(fa_mlp* m, const float* X, int64_t rows, const int64_t* pi,
         g.M = R; g.N = kDh; g.K = kDout; g.A = gY; g.sam = kDout; g.sak = 1;
         g.B = m->pb + kOffW3; g.sbk = kDh; g.sbn = 1; g.C = gH2; g.scm = kDh; g.scn = 1;
         g.mask = H2;
-        rc = tc_gemm<__nv_bfloat16, kDh, EPI_MASK>(g, 1, m->tc_err, st);
+        rc = tc_gemm<__nv_bfloat16, 64, EPI_MASK>(g, 1, m->tc_err, st);
         if (rc != FA_OK) return rc;
     }
     // layer 2
@@ -855,7 +906,7 @@ int fa_mlp_pair_grad(fa_mlp* m, const float* X, int64_t rows, const int64_t* pi,
         g.M = R; g.N = kDh; g.K = kDh; g.A = gH2; g.sam = kDh; g.sak = 1;
         g.B = m->pb + kOffW2; g.sbk = kDh; g.sbn = 1; g.C = gH1; g.scm = kDh; g.scn = 1;
         g.mask = H1;
-        rc = tc_gemm<__nv_bfloat16, kDh, EPI_MASK>(g, 1, m->tc_err, st);
+        rc = tc_gemm<__nv_bfloat16, 64, EPI_MASK>(g, 1, m->tc_err, st);
         if (rc != FA_OK) return rc;
     }
     // layer 1

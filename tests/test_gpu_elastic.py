@@ -38,20 +38,30 @@ def _gpu(b1, b2, band=-1, max_iter=20, **kw):
     return dict(shift=s, theta=th, energy=e, iters=it, status=st, gamma=g)
 
 
-def _compare(r, o, label=""):
+def _compare(r, o, label="", end_to_end=True):
+    """Kernel against oracle.  End to end (each side takes its own
+    pre-alignment and lattice path) a pair may end at another local optimum
+    when the two starting points differ -- a near-tie of the pre-alignment's
+    correlation peak flipped by rounding, or a float32 path sum: at most
+    DISAGREE_FRAC of the pairs (at least one) may do so; every other pair
+    meets the FP64 bounds.  From a common start (end_to_end=False) every pair
+    must meet them."""
     ok = o["status"] == 0
     np.testing.assert_array_equal(r["status"], o["status"])
     dE = np.abs(r["energy"][ok] - o["energy"][ok])
-    same_s = r["shift"][ok] == o["shift"][ok]
-    print(f"{label} max|dE|={dE.max():.3g} shift agree {same_s.mean():.4f}")
-    assert (dE <= E_ABS).all(), dE.max()
+    agree = dE <= E_ABS
+    allowed = max(1, int(DISAGREE_FRAC * agree.size)) if end_to_end else 0
+    print(f"{label} max|dE|={dE.max():.3g}; {(~agree).sum()} of {agree.size} pairs elsewhere "
+          f"(allowed {allowed})")
+    assert (~agree).sum() <= allowed, dE.max()
+    same_s = (r["shift"][ok] == o["shift"][ok]) & agree
     # where the shift agrees, theta and gamma describe the same optimum
     dth = np.abs(np.angle(np.exp(1j * (r["theta"][ok] - o["theta"][ok]))))[same_s]
     dg = np.abs(r["gamma"][ok] - o["gamma"][ok]).max(axis=1)[same_s]
     print(f"{label} max|dtheta|={dth.max() if dth.size else 0:.3g} max|dg|={dg.max() if dg.size else 0:.3g}")
     assert (dth <= TH_ABS).all() and (dg <= G_ABS).all()
-    # a different shift is a tie of the energy (checked above); allow 5 % or one pair
-    assert (~same_s).sum() <= max(1, int(0.05 * same_s.size))
+    # a different shift at an agreeing energy is a tie; allow 5 % or one pair
+    assert (agree & ~(r["shift"][ok] == o["shift"][ok])).sum() <= max(1, int(0.05 * agree.size))
 
 
 # --- the three-part parity of the elastic kernel -----------------------------
@@ -60,10 +70,11 @@ def _compare(r, o, label=""):
 #     (t0,R)-steps reproduce the kernel's result at the FP64 bounds above;
 # (c) end to end against the oracle's own pipeline (its FP64 DP included),
 #     with at most DISAGREE_FRAC of the pairs (at least one) allowed to end
-#     elsewhere because the two programmes started from different paths.
-#     Emulated on the CPU (the float32 path sums against the FP64 ones on
-#     1,276 pairs of these sets and a 256-node gallery) no pair ended
-#     elsewhere.
+#     elsewhere because the two sides started from different points: the
+#     float32 path sums, or a near-tie of the pre-alignment's correlation peak
+#     that rounding flips (seen once: N = 32, one iteration).  Emulated on the
+#     CPU (the float32 path sums against the FP64 ones on 1,276 pairs of these
+#     sets and a 256-node gallery) no pair ended elsewhere.
 DISAGREE_FRAC = 0.02
 STEPS = [(1, 1), (1, 2), (2, 1), (1, 3), (3, 1), (2, 3), (3, 2)]
 
@@ -155,7 +166,7 @@ def test_elastic_alternation_from_the_kernels_start_matches_oracle(N, band):
     r0 = _gpu(b1, b2, band=band, max_iter=0)
     r = _gpu(b1, b2, band=band, max_iter=20)
     o = oracle.elastic_from_start(b1, b2, r0["shift"], r0["theta"], r0["gamma"], max_iter=20)
-    _compare(r, o, f"from kernel start N={N} band={band}")
+    _compare(r, o, f"from kernel start N={N} band={band}", end_to_end=False)
 
 
 def test_elastic_gallery_end_to_end_disagreement_rate():
@@ -289,3 +300,21 @@ def test_elastic_graph_capture_matches_direct_call():
     torch.cuda.synchronize()
     for a, b in zip(ref, out):
         torch.testing.assert_close(a, b, rtol=0, atol=0)
+
+
+def test_elastic_reports_refinement_steps():
+    """lm_steps counts the Levenberg-Marquardt steps of each pair's gamma-steps:
+    at least one and at most 64 per iteration, none for a pair that fails."""
+    N, P = 64, 10
+    b1 = np.stack([_curve(6000 + p, N) for p in range(P)])
+    b2 = np.stack([_curve(7000 + p, N) for p in range(P)])
+    b2[3, 4] = np.nan
+    t1 = torch.from_numpy(b1).to(DEV)
+    t2 = torch.from_numpy(b2).to(DEV)
+    lm = torch.full((P,), -1, dtype=torch.int32, device=DEV)
+    s, th, e, it, st = api.elastic_distance(t1, t2, lm_steps=lm)
+    torch.cuda.synchronize()
+    lm, it, st = lm.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+    assert st[3] == 2 and lm[3] == 0
+    ok = st == 0
+    assert (lm[ok] >= it[ok]).all() and (lm[ok] <= 64 * it[ok]).all()
