@@ -79,6 +79,16 @@ FP64_NOMINAL_TFLOPS = 1.25
 
 
 # ----------------------------------------------------- algorithmic counts ---
+def measured_hbm_gbs():
+    """HBM copy bandwidth (GB/s) measured on this GPU type, from the peaks file
+    at the repository root, or None when it is absent."""
+    f = Path(__file__).resolve().parent / "MEASURED_PEAKS.json"
+    try:
+        return float(json.loads(f.read_text())["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def fft_flops(logn: int) -> int:
     """FP64 flops (FMA = 2) of one forward transform in the kernel's algorithm:
     an optional radix-2 stage (4 real adds per butterfly), then radix-4
@@ -509,22 +519,32 @@ def run_gpu(args):
     en32 = torch.empty(P, dtype=torch.float64, device=dev)
     st32 = torch.empty(P, dtype=torch.int8, device=dev)
 
-    def step32():
+    def resample32():
         _lib.check(L.fa_resample_arclength(h, pts.data_ptr(), offs.data_ptr(), C, n_pts, N,
                                            flags | _lib.STORE_FP32, z32.data_ptr(), rst.data_ptr(),
                                            ws32.data_ptr(), ws32_bytes, sptr))
+
+    def align32():
         _lib.check(L.fa_align_pairs(h, z32.data_ptr(), z32.data_ptr() + P * N * 8, P, N,
                                     _lib.Z_F32, _lib.FFT, _lib.PREC_FP64, sh32.data_ptr(),
                                     th32.data_ptr(), en32.data_ptr(), st32.data_ptr(), sptr))
 
+    ev32 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     with torch.cuda.stream(stream):
-        step32()
+        resample32()
+        align32()
         e0.record(stream)
-        for _ in range(K):
-            step32()
+        for k in range(K):
+            ev32[k][0].record(stream)
+            resample32()
+            ev32[k][1].record(stream)
+            align32()
+            ev32[k][2].record(stream)
         e1.record(stream)
     torch.cuda.synchronize(dev)
     f32_ms = e0.elapsed_time(e1) / K
+    rs32_ms = statistics.mean(ev32[k][0].elapsed_time(ev32[k][1]) for k in range(K))
+    al32_ms = statistics.mean(ev32[k][1].elapsed_time(ev32[k][2]) for k in range(K))
     same32 = sh32 == ref_shift
     dth32 = torch.remainder(th32 - ref_theta + np.pi, 2 * np.pi) - np.pi
     dz32 = 2.0 ** -24 * np.sqrt(2.0) * zmax
@@ -538,7 +558,8 @@ def run_gpu(args):
                "of the FP64 path's, dz = 2^-24 sqrt(2) max|z| (complex64 rounding of the nodes)",
         "max_abs_dtheta_where_shift_agrees": float(dth32.abs()[same32].max().item()),
         "max_rel_denergy": float(((en32 - ref_energy).abs() / ref_energy.abs()).max().item()),
-        "dtype": "f64 compute, complex64 resampled nodes"}
+        "dtype": "f64 compute, complex64 resampled nodes",
+        "kernels_ms": {"resample_kernel<fp32 store>": rs32_ms, "align_fft_kernel<float2>": al32_ms}}
     del z32, ws32
 
     # FP64 peak measured in this run (denominator of the roofline)
@@ -560,6 +581,24 @@ def run_gpu(args):
     }
     for kv in kernels.values():  # each kernel against the same measured FP64 peak
         kv["frac_of_measured_fp64_peak"] = kv["tflops"] / fp64_peak
+    # the FP32-storage variant against both rooflines: its arithmetic is the
+    # same FP64 work, its algorithmic HBM bytes are 16 B per raw node read + 8 B
+    # per resampled node written (resampling) and 8 B per node of both curves
+    # read (alignment); the binding one is the larger fraction
+    hbm_peak = measured_hbm_gbs()
+    bytes_rs32 = 16 * int(n_pts) + 8 * C * N + 8 * (C + 1)
+    bytes_al32 = 2 * P * N * 8 + 21 * P
+    roof32 = {}
+    for name, fl, by, ms in (("resample_kernel<fp32 store>", fl_rs, bytes_rs32, rs32_ms),
+                             ("align_fft_kernel<float2>", fl_al, bytes_al32, al32_ms)):
+        f_fp64 = fl / (ms * 1e-3) / 1e12 / fp64_peak
+        f_hbm = (by / (ms * 1e-3) / 1e9 / hbm_peak) if hbm_peak else None
+        roof32[name] = {"ms": ms, "flops_per_launch": fl, "bytes_per_launch": by,
+                        "frac_of_measured_fp64_peak": f_fp64, "frac_of_measured_hbm": f_hbm,
+                        "bound": "alu" if f_hbm is None or f_fp64 >= f_hbm else "hbm"}
+    fp32_storage["roofline"] = {"kernels": roof32, "fp64_peak_tflops": fp64_peak,
+                                "hbm_peak_gbs": hbm_peak, "of": "measured",
+                                "note": "no FP32-pipe roofline: the variant computes in FP64"}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     if args.traffic is not None:
         traffic, tnote = args.traffic, "given on the command line"

@@ -24,19 +24,21 @@
 //   TF32    one TF32 product (about 11 bits)
 //   TF32X3  TF32 hi + lo pieces, three products (about 21 bits)
 // The 8 candidates of each pair are then re-scored by their direct O(N)
-// correlation in float-float arithmetic (about 48 bits, rel. error ~1e-14),
+// correlation, summed exactly on a fixed grid with float32 remainders (about
+// 40 bits for complex64 input; float-float otherwise),
 // the largest |c(s)|^2 wins (smallest s on ties), theta = arg c(s*) and the
 // energy of Eq. disc-energy by its definition, both at FP64-bound accuracy.
 //
-// GEMM kernel: one CTA of 128 threads per SM, persistent over (i, j-tile)
+// GEMM kernel: one CTA of 288 threads per SM, persistent over (i, j-tile)
 // tiles from an atomic counter; per tile, per 128-shift column block, the
 // 2N-long contraction runs in chunks of 64 bytes per row (32 f16 or 16 tf32
-// elements) through three shared-memory stages.  Per chunk: thread 0 starts a
+// elements) through four shared-memory stages.  Per chunk: one lane starts a
 // bulk copy (cp.async.bulk, completion on an mbarrier) of the pre-tiled DFT
-// block, every thread forms its pair's cross-spectrum piece row (FP32 from the
-// complex64 spectra), thread 0 issues the MMAs and commits them to the stage's
-// mbarrier.  All waits are bounded; a wait that runs out sets an error flag
-// that turns every output of the call into NaN.
+// block one chunk ahead and issues the MMAs, committing them to the stage's
+// mbarrier; 256 producer threads form the 128 cross-spectrum rows (FP32 from
+// the complex64 spectra, split into pieces), several lanes per row so that
+// their loads are coalesced.  All waits are bounded; a wait that runs out sets
+// an error flag that turns every output of the call into NaN.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -51,10 +53,10 @@ namespace fa {
 namespace {
 
 constexpr int kTcT = 128;           // pairs per tile = TMEM lanes
-constexpr int kTcProducers = 256;   // two threads per pair form its operand row
+constexpr int kTcProducers = 256;   // threads that form the operand rows
 constexpr int kTcThreads = kTcProducers + 32;  // and one warp issues copies and MMAs
 constexpr int kRowB = 64;      // bytes per operand row per K chunk
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr int kCand = 8;       // candidate shifts kept per pair
 constexpr float kPScale = 16384.0f;  // 2^14: cross-spectra scale (float16 range)
 
@@ -202,10 +204,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
 }
 
 // ---- the GEMM + top-8 kernel --------------------------------------------------
-// Warp roles: warps 0-7 produce the cross-spectrum operand rows (two threads
-// per pair) and warps 0-3 also read the accumulators (TMEM lane = pair);
-// lane 0 of warp 8 starts the bulk copies of the DFT blocks (one chunk ahead)
-// and issues the MMAs.  Per stage: b_full (copy landed), a_full (the 256
+// Warp roles: warps 0-7 produce the cross-spectrum operand rows and warps
+// 0-3 also read the accumulators (TMEM lane = pair); lane 0 of warp 8 starts
+// the bulk copies of the DFT blocks (one chunk ahead) and issues the MMAs.
+// Per stage: b_full (copy landed), a_full (the 256
 // producers stored their rows), mma_done (the stage's MMAs finished, it may be
 // overwritten).  Two accumulators of 256 columns alternate between column
 // blocks: acc_full[b] (block finished) and tmem_empty[b] (its 128 readers are
@@ -224,7 +226,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     constexpr uint32_t B_BYTES = (uint32_t)(B_PIECE * T::NP);
     constexpr uint32_t ID = umma::idesc(128, 256, T::FMT);
     constexpr int NT = T::NP == 2 ? 3 : 1;
-    constexpr int KH = KF / 2;  // frequencies per half row
+    constexpr int LPR = KF / 2;                // producer lanes per operand row
+    constexpr int RPP = kTcProducers / LPR;    // rows per producer pass
+    constexpr int NPASS = kTcT / RPP;          // passes per chunk
+    static_assert(NPASS * RPP == kTcT && 32 % LPR == 0, "producer mapping");
     extern __shared__ __align__(1024) uint8_t smem[];
     float2* zi_s = reinterpret_cast<float2*>(smem + kStages * STAGE);                  // [N]
     uint64_t* b_full = reinterpret_cast<uint64_t*>(smem + kStages * STAGE + N * 8);    // [kStages]
@@ -237,7 +242,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     long long* s_tile = reinterpret_cast<long long*>(s_taddr + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool producer = tid < kTcProducers;
-    const int row = tid & (kTcT - 1), half = (tid >> 7) & 1;  // pair and half row (producers)
+    const int prow = tid / LPR, sub = tid % LPR;  // producers: row in a pass, frequency pair
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -259,6 +264,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t tmem = *s_taddr;
     const int64_t total_tiles = ceil_sum128(M - 1);
     int64_t g = 0, cbg = 0;  // chunks and column blocks so far (producers and the issuer alike)
+    int64_t copied = 0;      // DFT blocks copied so far (the issuer)
     auto fail = [&]() {
         *s_abort = 1;
         atomicExch(err, 1);
@@ -282,17 +288,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncthreads();
 
         if (producer) {
-            const int64_t j = j0 + row;
-            const bool valid = j < M;
-            const float2* zj = spec + (valid ? j : i) * N + half * KH;
+            // Operand rows are formed LPR lanes per pair, two frequencies per
+            // lane (one 16-byte load), so that a warp's load covers LPR * 16
+            // contiguous bytes of each of 32 / LPR rows; pass q handles rows
+            // q RPP + tid / LPR.
+            const float4* zrow[NPASS];
+#pragma unroll
+            for (int q = 0; q < NPASS; ++q) {
+                const int64_t j = j0 + q * RPP + prow;
+                zrow[q] = reinterpret_cast<const float4*>(spec + (j < M ? j : i) * N) + sub;
+            }
             // this thread's spectrum values of the next two chunks (loads in
             // flight two chunks ahead: they come from L2 with its latency)
-            float2 zb[KH], zb2[KH];
+            float4 zb[NPASS], zb2[NPASS];
 #pragma unroll
-            for (int q = 0; q < KH; ++q) {
-                zb[q] = valid ? zj[q] : make_float2(0.f, 0.f);
-                zb2[q] = valid ? zj[(1 % NK) * KF + q] : make_float2(0.f, 0.f);
+            for (int q = 0; q < NPASS; ++q) {
+                zb[q] = zrow[q][0];
+                zb2[q] = zrow[q][(1 % NK) * (KF / 2)];
             }
+            const float4* zi4 = reinterpret_cast<const float4*>(zi_s) + sub;
             float best[kCand];
             int bs[kCand];
 #pragma unroll
@@ -305,45 +319,41 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     uint8_t* sa = smem + st * STAGE;
                     if (*s_abort) break;
                     if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) { fail(); break; }
-                    // this pair's cross-spectrum half row (frequencies f0 .. f0 + KH - 1)
-                    const int f0 = kc * KF + half * KH;
-                    uint32_t ph[KC / 2], pl[KC / 2];
+                    // frequencies kc KF + 2 sub, + 1 of curve i
+                    const float4 a = zi4[kc * (KF / 2)];
 #pragma unroll
-                    for (int q = 0; q < KH; ++q) {
-                        const float2 a = zi_s[f0 + q];
-                        const float2 b = zb[q];
-                        const float pr = __fmul_rn(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), kPScale);
-                        const float pi = __fmul_rn(__fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y)), kPScale);
-                        to_pieces<V>(pr, ph[2 * q], pl[2 * q]);
-                        to_pieces<V>(pi, ph[2 * q + 1], pl[2 * q + 1]);
+                    for (int q = 0; q < NPASS; ++q) {
+                        const float4 b = zb[q];
+                        float v[4];
+                        v[0] = __fmul_rn(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), kPScale);
+                        v[1] = __fmul_rn(__fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y)), kPScale);
+                        v[2] = __fmul_rn(__fmaf_rn(a.z, b.z, __fmul_rn(a.w, b.w)), kPScale);
+                        v[3] = __fmul_rn(__fmaf_rn(a.w, b.z, -__fmul_rn(a.z, b.w)), kPScale);
+                        uint32_t ph[4], pl[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) to_pieces<V>(v[e], ph[e], pl[e]);
+                        const int r = q * RPP + prow;
+                        const uint32_t off = umma::tile_off(r, sub * 4 * T::ES, kRowB);
+                        if constexpr (T::ES == 2) {
+                            *reinterpret_cast<uint2*>(sa + off) =
+                                make_uint2(ph[0] | (ph[1] << 16), ph[2] | (ph[3] << 16));
+                            *reinterpret_cast<uint2*>(sa + A_PIECE + off) =
+                                make_uint2(pl[0] | (pl[1] << 16), pl[2] | (pl[3] << 16));
+                        } else {
+                            *reinterpret_cast<uint4*>(sa + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                            if (T::NP > 1)
+                                *reinterpret_cast<uint4*>(sa + A_PIECE + off) =
+                                    make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                        }
                     }
                     {   // the chunk after next (K chunks wrap to the first ones for
                         // the next column block)
-                        const int fn = ((kc + 2) % NK) * KF;
+                        const int fn = ((kc + 2) % NK) * (KF / 2);
 #pragma unroll
-                        for (int q = 0; q < KH; ++q) {
+                        for (int q = 0; q < NPASS; ++q) {
                             zb[q] = zb2[q];
-                            zb2[q] = valid ? zj[fn + q] : make_float2(0.f, 0.f);
+                            zb2[q] = zrow[q][fn];
                         }
-                    }
-#pragma unroll
-                    for (int cc = 0; cc < kRowB / 32; ++cc) {
-                        const int c16 = half * (kRowB / 32) + cc;
-                        uint4 vh, vl;
-                        if constexpr (T::ES == 2) {
-                            const int b0 = cc * 8;
-                            vh = make_uint4(ph[b0] | (ph[b0 + 1] << 16), ph[b0 + 2] | (ph[b0 + 3] << 16),
-                                            ph[b0 + 4] | (ph[b0 + 5] << 16), ph[b0 + 6] | (ph[b0 + 7] << 16));
-                            vl = make_uint4(pl[b0] | (pl[b0 + 1] << 16), pl[b0 + 2] | (pl[b0 + 3] << 16),
-                                            pl[b0 + 4] | (pl[b0 + 5] << 16), pl[b0 + 6] | (pl[b0 + 7] << 16));
-                        } else {
-                            const int b0 = cc * 4;
-                            vh = make_uint4(ph[b0], ph[b0 + 1], ph[b0 + 2], ph[b0 + 3]);
-                            vl = make_uint4(pl[b0], pl[b0 + 1], pl[b0 + 2], pl[b0 + 3]);
-                        }
-                        const uint32_t off = umma::tile_off(row, c16 * 16, kRowB);
-                        *reinterpret_cast<uint4*>(sa + off) = vh;
-                        if (T::NP > 1) *reinterpret_cast<uint4*>(sa + A_PIECE + off) = vl;
                     }
                     umma::fence_async_smem();
                     umma::mbar_arrive(&a_full[st]);
@@ -351,7 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (*s_abort) break;
                 // warps 0-3: this column block's |c(s)|^2 into the running top 8
                 const int buf = (int)(cbg & 1);
-                if (half == 0) {
+                if (tid < kTcT) {
                     if (!umma::mbar_wait(&acc_full[buf], (uint32_t)(cbg >> 1) & 1)) { fail(); break; }
                     umma::tc_fence_after();
 #pragma unroll 1
@@ -382,7 +392,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 ++cbg;
             }
-            if (valid && half == 0 && !*s_abort) {
+            if (tid < kTcT && j0 + tid < M && !*s_abort) {
+                const int64_t j = j0 + tid;
                 // candidates that can still be the maximum (see TcVar::MARGIN); the
                 // count rides in bits 12-15 of the first entry (shifts < 4096)
                 int keep = 0;
@@ -398,55 +409,64 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 *reinterpret_cast<uint4*>(cand + ((size_t)i * M + j) * kCand) = w;
             }
         } else if (lane == 0) {
-            // the issuer: DFT blocks one chunk ahead, MMAs, commits
-            auto copy_b = [&](int64_t gg, int cb, int kc) -> bool {
-                const int st = (int)(gg % kStages);
-                const uint32_t use = (uint32_t)(gg / kStages);
+            // the issuer: DFT blocks two chunks ahead (across column blocks),
+            // MMAs, commits; chunk c of the tile is column block c / NK, K chunk
+            // c % NK, and DFT block c of the pre-tiled table
+            constexpr int NC = NCB * NK;
+            auto copy_b = [&](int c) -> bool {
+                const int st = (int)(copied % kStages);
+                const uint32_t use = (uint32_t)(copied / kStages);
                 if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) return false;
                 mbar_expect_tx(&b_full[st], B_BYTES);
-                bulk_g2s(smem + st * STAGE + A_PIECE * T::NP,
-                         tab + ((size_t)cb * NK + kc) * B_BYTES, B_BYTES, &b_full[st]);
+                bulk_g2s(smem + st * STAGE + A_PIECE * T::NP, tab + (size_t)c * B_BYTES, B_BYTES,
+                         &b_full[st]);
+                ++copied;
                 return true;
             };
-            for (int cb = 0; cb < NCB && !*s_abort; ++cb) {
+            if (!copy_b(0) || (NC > 1 && !copy_b(1))) fail();
+            for (int c = 0; c < NC && !*s_abort; ++c, ++g) {
+                const int kc = c % NK;
                 const int buf = (int)(cbg & 1);
-                if (cbg >= 2 && !umma::mbar_wait(&tmem_empty[buf], (uint32_t)((cbg >> 1) - 1) & 1)) {
+                const int st = (int)(g % kStages);
+                const uint32_t use = (uint32_t)(g / kStages);
+                if (kc == 0 && cbg >= 2 &&
+                    !umma::mbar_wait(&tmem_empty[buf], (uint32_t)((cbg >> 1) - 1) & 1)) {
                     fail();
                     break;
                 }
-                if (!copy_b(g, cb, 0)) { fail(); break; }
-                for (int kc = 0; kc < NK; ++kc, ++g) {
-                    const int st = (int)(g % kStages);
-                    const uint32_t use = (uint32_t)(g / kStages);
-                    if (*s_abort) break;
-                    if (kc + 1 < NK && !copy_b(g + 1, cb, kc + 1)) { fail(); break; }
-                    if (!umma::mbar_wait(&b_full[st], use & 1) || !umma::mbar_wait(&a_full[st], use & 1)) {
-                        fail();
-                        break;
-                    }
-                    umma::tc_fence_after();
-                    const uint32_t a0 = umma::smem_u32(smem + st * STAGE);
-                    const uint32_t b0 = a0 + (uint32_t)(A_PIECE * T::NP);
-                    constexpr int PA[3] = {0, 0, 1}, PB[3] = {0, 1, 0};
-#pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
-#pragma unroll
-                        for (int tt = 0; tt < NT; ++tt) {
-                            const uint64_t ad = umma::sdesc(a0 + (uint32_t)(PA[tt] * A_PIECE) + ks * 256,
-                                                            128, kRowB * 8);
-                            const uint64_t bd = umma::sdesc(b0 + (uint32_t)(PB[tt] * B_PIECE) + ks * 256,
-                                                            128, kRowB * 8);
-                            const uint32_t acc = (kc > 0 || ks > 0 || tt > 0) ? 1u : 0u;
-                            if constexpr (T::TF32) umma::mma_tf32(tmem + buf * 256, ad, bd, ID, acc);
-                            else umma::mma_f16(tmem + buf * 256, ad, bd, ID, acc);
-                        }
-                    }
-                    umma::mma_commit(&mma_done[st]);
+                if (c + 2 < NC && !copy_b(c + 2)) { fail(); break; }
+                if (!umma::mbar_wait(&b_full[st], use & 1) || !umma::mbar_wait(&a_full[st], use & 1)) {
+                    fail();
+                    break;
                 }
-                if (*s_abort) break;
-                umma::mma_commit(&acc_full[buf]);
-                ++cbg;
+                umma::tc_fence_after();
+                const uint32_t a0 = umma::smem_u32(smem + st * STAGE);
+                const uint32_t b0 = a0 + (uint32_t)(A_PIECE * T::NP);
+                constexpr int PA[3] = {0, 0, 1}, PB[3] = {0, 1, 0};
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+                    for (int tt = 0; tt < NT; ++tt) {
+                        const uint64_t ad = umma::sdesc(a0 + (uint32_t)(PA[tt] * A_PIECE) + ks * 256,
+                                                        128, kRowB * 8);
+                        const uint64_t bd = umma::sdesc(b0 + (uint32_t)(PB[tt] * B_PIECE) + ks * 256,
+                                                        128, kRowB * 8);
+                        const uint32_t acc = (kc > 0 || ks > 0 || tt > 0) ? 1u : 0u;
+                        if constexpr (T::TF32) umma::mma_tf32(tmem + buf * 256, ad, bd, ID, acc);
+                        else umma::mma_f16(tmem + buf * 256, ad, bd, ID, acc);
+                    }
+                }
+                umma::mma_commit(&mma_done[st]);
+                if (kc == NK - 1) {
+                    umma::mma_commit(&acc_full[buf]);
+                    ++cbg;
+                }
             }
+            // copies started but not consumed (only after an abort) land before
+            // the CTA may exit
+            for (int64_t gg = g; gg < copied; ++gg)
+                if (!umma::mbar_wait(&b_full[gg % kStages], (uint32_t)(gg / kStages) & 1)) atomicExch(err, 1);
+            g = copied;
         }
     }
     // every MMA this CTA issued has finished before the tensor memory is freed
@@ -499,35 +519,86 @@ __device__ __forceinline__ Rescored rescore_pair(const ZT* __restrict__ z, int64
     int sbest = 0;
     cdf cbest{{0.f, 0.f}, {0.f, 0.f}};
     const int keep = (int)((cw.x >> 12) & 15u);
-#pragma unroll 1
-    for (int c = 0; c < keep; ++c) {
+    auto cand_shift = [&](int c) {
         const uint32_t w = c < 2 ? cw.x : c < 4 ? cw.y : c < 6 ? cw.z : cw.w;
-        const int s = (int)((w >> (16 * (c & 1))) & 0xfffu) & (N - 1);
-        cdf acc{{0.f, 0.f}, {0.f, 0.f}};
-        if constexpr (std::is_same<ZT, float2>::value) {
-            // complex64 inputs: each product of two floats is exactly p + e
-            // (e by FMA); the p are summed by two-sums into (h, l), the small
-            // terms straight into l, normalised once at the end
+        return (int)((w >> (16 * (c & 1))) & 0xfffu) & (N - 1);
+    };
+    auto take = [&](const cdf& acc, int s) {
+        const long long key = df_key(cnorm2(acc));
+        if (key > bkey || (key == bkey && s < sbest)) { bkey = key; sbest = s; cbest = acc; }
+    };
+    bool done = false;
+    if constexpr (std::is_same<ZT, float2>::value) {
+        // complex64 inputs.  Each product a b is split on a fixed grid: the
+        // running sum T <- fl(a b + T), started at T0 = 1.5 2^k, takes the
+        // part of a b on the grid of ulp(T) exactly (T_new - T is exact by
+        // Sterbenz's lemma, as |a b| < 2^(k-1) <= T / 2), and the remainder
+        // fl(a b - (T_new - T)), at most half a grid step u = 2^(k-23), is
+        // recovered by one FMA and summed in float32.  Cauchy-Schwarz bounds the
+        // sum of |a b| over a correlation by |z_i| |z_j| <= 2^(k-1), so T stays
+        // in [2^k, 2^(k+1)] and the lanes' grid parts add exactly; the
+        // remainders' rounding errors are typically of order 2^(k-40) (at most
+        // about 2^(k-30)).  Four float32 operations per product instead of the
+        // ten of a float-float sum.
+        float2 ui[R];
+        float ni = 0.f, nj = 0.f;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float2 u = zi[lane + 32 * r];
-                const float2 v = zj[(lane + 32 * r + s) & (N - 1)];
-                const float p1 = __fmul_rn(u.x, v.x), e1 = __fmaf_rn(u.x, v.x, -p1);
-                const float p2 = __fmul_rn(u.y, v.y), e2 = __fmaf_rn(u.y, v.y, -p2);
-                const float p3 = __fmul_rn(u.y, v.x), e3 = __fmaf_rn(u.y, v.x, -p3);
-                const float p4 = __fmul_rn(-u.x, v.y), e4 = __fmaf_rn(-u.x, v.y, -p4);
-                dfl t = two_sum(acc.re.h, p1);
-                const dfl t2 = two_sum(t.h, p2);
-                acc.re.h = t2.h;
-                acc.re.l = __fadd_rn(acc.re.l, __fadd_rn(__fadd_rn(t.l, t2.l), __fadd_rn(e1, e2)));
-                t = two_sum(acc.im.h, p3);
-                const dfl t4 = two_sum(t.h, p4);
-                acc.im.h = t4.h;
-                acc.im.l = __fadd_rn(acc.im.l, __fadd_rn(__fadd_rn(t.l, t4.l), __fadd_rn(e3, e4)));
+        for (int r = 0; r < R; ++r) {
+            ui[r] = zi[lane + 32 * r];
+            const float2 v = zj[lane + 32 * r];
+            ni = __fmaf_rn(ui[r].x, ui[r].x, __fmaf_rn(ui[r].y, ui[r].y, ni));
+            nj = __fmaf_rn(v.x, v.x, __fmaf_rn(v.y, v.y, nj));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            ni += __shfl_xor_sync(0xffffffffu, ni, off);
+            nj += __shfl_xor_sync(0xffffffffu, nj, off);
+        }
+        // 4 |z_i| |z_j| (float32 rounding of the norms is far inside the
+        // factor 2 of headroom); 2^k <= q < 2^(k+1)
+        const float q = __fmul_rn(4.0f, __fmul_rn(__fsqrt_rn(ni), __fsqrt_rn(nj)));
+        if (q >= 0x1p-60f && q <= 0x1p+100f) {
+            const float T0 = __uint_as_float((__float_as_uint(q) & 0x7f800000u) | 0x00400000u);
+#pragma unroll 1
+            for (int c = 0; c < keep; ++c) {
+                const int s = cand_shift(c);
+                float tr = T0, ti = T0, lr = 0.f, li = 0.f;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float2 v = zj[(lane + 32 * r + s) & (N - 1)];
+                    const float2 a = ui[r];
+                    float t = __fmaf_rn(a.x, v.x, tr);
+                    lr = __fadd_rn(lr, __fmaf_rn(a.x, v.x, __fsub_rn(tr, t)));
+                    tr = t;
+                    t = __fmaf_rn(a.y, v.y, tr);
+                    lr = __fadd_rn(lr, __fmaf_rn(a.y, v.y, __fsub_rn(tr, t)));
+                    tr = t;
+                    t = __fmaf_rn(a.y, v.x, ti);
+                    li = __fadd_rn(li, __fmaf_rn(a.y, v.x, __fsub_rn(ti, t)));
+                    ti = t;
+                    t = __fmaf_rn(-a.x, v.y, ti);
+                    li = __fadd_rn(li, __fmaf_rn(-a.x, v.y, __fsub_rn(ti, t)));
+                    ti = t;
+                }
+                float gr = __fsub_rn(tr, T0), gi = __fsub_rn(ti, T0);  // exact
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    gr = __fadd_rn(gr, __shfl_xor_sync(0xffffffffu, gr, off));  // exact
+                    gi = __fadd_rn(gi, __shfl_xor_sync(0xffffffffu, gi, off));  // exact
+                    lr = __fadd_rn(lr, __shfl_xor_sync(0xffffffffu, lr, off));
+                    li = __fadd_rn(li, __shfl_xor_sync(0xffffffffu, li, off));
+                }
+                take(cdf{two_sum(gr, lr), two_sum(gi, li)}, s);
             }
-            acc.re = fast_two_sum(acc.re.h, acc.re.l);
-            acc.im = fast_two_sum(acc.im.h, acc.im.l);
-        } else {
+            done = true;
+        }
+    }
+    if (!done) {
+        // any input, any scale: products and sums in float-float
+#pragma unroll 1
+        for (int c = 0; c < keep; ++c) {
+            const int s = cand_shift(c);
+            cdf acc{{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const cdf b = ld_df(zj, (lane + 32 * r + s) & (N - 1));
@@ -536,14 +607,13 @@ __device__ __forceinline__ Rescored rescore_pair(const ZT* __restrict__ z, int64
                 acc.re = df_add(acc.re, df_dot2<+1>(ar.re, b.re, ar.im, b.im));
                 acc.im = df_add(acc.im, df_dot2<-1>(ar.im, b.re, ar.re, b.im));
             }
-        }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            acc.re = df_add(acc.re, shfl_df(acc.re, off));
-            acc.im = df_add(acc.im, shfl_df(acc.im, off));
+            for (int off = 16; off > 0; off >>= 1) {
+                acc.re = df_add(acc.re, shfl_df(acc.re, off));
+                acc.im = df_add(acc.im, shfl_df(acc.im, off));
+            }
+            take(acc, s);
         }
-        const long long key = df_key(cnorm2(acc));
-        if (key > bkey || (key == bkey && s < sbest)) { bkey = key; sbest = s; cbest = acc; }
     }
     // the rotation e^{i theta} = c / |c| in float-float (every lane holds the
     // reduced c(s*); FP64 only for theta itself, on one lane below)

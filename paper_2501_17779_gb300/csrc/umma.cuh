@@ -131,14 +131,16 @@ __device__ __forceinline__ bool mbar_test(uint64_t* mbar, uint32_t parity)
     return ok != 0;
 }
 // Waits for the phase of the given parity to complete; gives up after about
-// 2^22 polls of a few hundred nanoseconds each (well over a second, far beyond
-// any MMA) and returns false, so that a wrong arrival count can never hang
-// the GPU: the caller then records an error and leaves cleanly.
+// 2^22 polls, all but the first 256 followed by a 256 ns sleep (well over a
+// second, far beyond any MMA) and returns false, so that a wrong arrival count
+// can never hang the GPU: the caller then records an error and leaves cleanly.
+// The first polls do not sleep: in a pipeline the phase usually completes
+// within a few hundred cycles, and a sleep would add its whole length.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity)
 {
     for (uint32_t i = 0; i < (1u << 22); ++i) {
         if (mbar_test(mbar, parity)) return true;
-        __nanosleep(256);
+        if (i >= 256) __nanosleep(256);
     }
     return false;
 }
