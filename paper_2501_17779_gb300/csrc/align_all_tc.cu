@@ -29,16 +29,19 @@
 // the largest |c(s)|^2 wins (smallest s on ties), theta = arg c(s*) and the
 // energy of Eq. disc-energy by its definition, both at FP64-bound accuracy.
 //
-// GEMM kernel: one CTA of 288 threads per SM, persistent over (i, j-tile)
+// GEMM kernel: one CTA of 448 threads per SM, persistent over (i, j-tile)
 // tiles from an atomic counter; per tile, per 128-shift column block, the
 // 2N-long contraction runs in chunks of 64 bytes per row (32 f16 or 16 tf32
-// elements) through four shared-memory stages.  Per chunk: one lane starts a
-// bulk copy (cp.async.bulk, completion on an mbarrier) of the pre-tiled DFT
-// block one chunk ahead and issues the MMAs, committing them to the stage's
-// mbarrier; 256 producer threads form the 128 cross-spectrum rows (FP32 from
-// the complex64 spectra, split into pieces), several lanes per row so that
-// their loads are coalesced.  All waits are bounded; a wait that runs out sets
-// an error flag that turns every output of the call into NaN.
+// elements) through four shared-memory stages.  Warps 0-7 form the 128
+// cross-spectrum rows of each chunk (FP32 from the complex64 spectra, split
+// into pieces, several lanes per row so that their loads are coalesced); one
+// lane of warp 12 issues the MMAs, one lane of warp 13 bulk-copies
+// (cp.async.bulk, completion on an mbarrier) the pre-tiled DFT blocks as far
+// ahead as the stages allow; warps 8-11 read the
+// finished accumulators and keep each pair's best 8 shifts, while the MMAs of
+// the next column block run into the other accumulator.  All waits are
+// bounded; a wait that runs out sets an error flag that turns every output of
+// the call into NaN.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -53,8 +56,11 @@ namespace fa {
 namespace {
 
 constexpr int kTcT = 128;           // pairs per tile = TMEM lanes
-constexpr int kTcProducers = 256;   // threads that form the operand rows
-constexpr int kTcThreads = kTcProducers + 32;  // and one warp issues copies and MMAs
+constexpr int kTcProducers = 256;   // warps 0-7 form the operand rows
+constexpr int kEpiWarp0 = kTcProducers / 32;   // warps 8-11 read the accumulators
+constexpr int kIssuerWarp = kEpiWarp0 + 4;      // warp 12 issues the MMAs
+constexpr int kCopyWarp = kIssuerWarp + 1;      // warp 13 copies the DFT blocks
+constexpr int kTcThreads = 32 * (kCopyWarp + 1);
 constexpr int kRowB = 64;      // bytes per operand row per K chunk
 constexpr int kStages = 4;
 constexpr int kCand = 8;       // candidate shifts kept per pair
@@ -123,6 +129,28 @@ __device__ __forceinline__ void to_pieces(float x, uint32_t& hi, uint32_t& lo)
         const __half h = __float2half_rn(x);
         hi = __half_as_ushort(h);
         lo = __half_as_ushort(__float2half_rn(__fsub_rn(x, __half2float(h))));
+    }
+}
+
+// x0, x1 as two packed 16-bit pieces each (hi = x0 | x1 << 16 rounded, lo the
+// rounded remainders), for the variants with 16-bit operands
+template <int V>
+__device__ __forceinline__ void to_pieces2(float x0, float x1, uint32_t& hi, uint32_t& lo)
+{
+    using T = TcVar<V>;
+    static_assert(!T::TF32, "16-bit variants only");
+    if constexpr (T::FMT == 1) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(__fsub_rn(x0, hf.x), __fsub_rn(x1, hf.y));
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(x0, x1);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(__fsub_rn(x0, hf.x), __fsub_rn(x1, hf.y));
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
     }
 }
 
@@ -204,14 +232,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
 }
 
 // ---- the GEMM + top-8 kernel --------------------------------------------------
-// Warp roles: warps 0-7 produce the cross-spectrum operand rows and warps
-// 0-3 also read the accumulators (TMEM lane = pair); lane 0 of warp 8 starts
-// the bulk copies of the DFT blocks (one chunk ahead) and issues the MMAs.
-// Per stage: b_full (copy landed), a_full (the 256
-// producers stored their rows), mma_done (the stage's MMAs finished, it may be
-// overwritten).  Two accumulators of 256 columns alternate between column
-// blocks: acc_full[b] (block finished) and tmem_empty[b] (its 128 readers are
-// done), so the MMAs of the next block overlap the epilogue of this one.
+// Warp roles: warps 0-7 produce the cross-spectrum operand rows, warps 8-11
+// read the accumulators (TMEM lane = pair), lane 0 of warp 12 issues the MMAs
+// and lane 0 of warp 13 copies the DFT blocks.  Per stage: b_full (copy landed), a_full (the
+// 256 producers stored their rows), mma_done (the stage's MMAs finished, it
+// may be overwritten).  Two accumulators of 256 columns alternate between
+// column blocks: acc_full[b] (block finished) and tmem_empty[b] (its 128
+// readers are done).
 template <int V, int LOGN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_search_kernel(const float2* __restrict__ spec, int64_t M, const uint8_t* __restrict__ tab,
@@ -241,7 +268,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_taddr + 1);
     long long* s_tile = reinterpret_cast<long long*>(s_taddr + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool producer = tid < kTcProducers;
     const int prow = tid / LPR, sub = tid % LPR;  // producers: row in a pass, frequency pair
 
     if (tid == 0) {
@@ -263,8 +289,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     umma::tc_fence_after();
     const uint32_t tmem = *s_taddr;
     const int64_t total_tiles = ceil_sum128(M - 1);
-    int64_t g = 0, cbg = 0;  // chunks and column blocks so far (producers and the issuer alike)
-    int64_t copied = 0;      // DFT blocks copied so far (the issuer)
+    int64_t g = 0, cbg = 0;  // chunks (producers, issuer) and column blocks (epilogue, issuer) so far
+    int64_t copied = 0;      // DFT blocks copied so far (the copier)
     auto fail = [&]() {
         *s_abort = 1;
         atomicExch(err, 1);
@@ -283,11 +309,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         const int64_t i = lo;
         const int64_t j0 = i + 1 + 128 * (t - (ceil_sum128(M - 1) - ceil_sum128(M - 1 - i)));
-        if (producer)
-            for (int k = tid; k < N; k += kTcProducers) zi_s[k] = spec[i * N + k];
+        if (warp < kEpiWarp0)
+            for (int k = tid; k < N; k += kTcProducers) {
+                // curve i's spectrum times the cross-spectrum scale (a power of
+                // two: the products below round exactly as if scaled after)
+                const float2 v = spec[i * N + k];
+                zi_s[k] = make_float2(v.x * kPScale, v.y * kPScale);
+            }
         __syncthreads();
 
-        if (producer) {
+        if (warp < kEpiWarp0) {
+            // ---- producers ----
             // Operand rows are formed LPR lanes per pair, two frequencies per
             // lane (one 16-byte load), so that a warp's load covers LPR * 16
             // contiguous bytes of each of 32 / LPR rows; pass q handles rows
@@ -298,8 +330,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int64_t j = j0 + q * RPP + prow;
                 zrow[q] = reinterpret_cast<const float4*>(spec + (j < M ? j : i) * N) + sub;
             }
-            // this thread's spectrum values of the next two chunks (loads in
-            // flight two chunks ahead: they come from L2 with its latency)
+            // this thread's spectrum values of the next two chunks
             float4 zb[NPASS], zb2[NPASS];
 #pragma unroll
             for (int q = 0; q < NPASS; ++q) {
@@ -307,93 +338,114 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 zb2[q] = zrow[q][(1 % NK) * (KF / 2)];
             }
             const float4* zi4 = reinterpret_cast<const float4*>(zi_s) + sub;
+            // this thread's byte offsets in an operand stage, one per pass
+            uint32_t soff[NPASS];
+#pragma unroll
+            for (int q = 0; q < NPASS; ++q) soff[q] = umma::tile_off(q * RPP + prow, sub * 4 * T::ES, kRowB);
+            // One K chunk: wait for its stage, form and store this thread's
+            // operand pieces from zbuf, signal, then load the chunk two ahead
+            // into zbuf (K chunks wrap to the first ones for the next column
+            // block).  The loads come after the proxy fence, which would
+            // otherwise wait for them.
+            auto produce = [&](int kc, float4 (&zbuf)[NPASS]) -> bool {
+                const int st = (int)(g % kStages);
+                const uint32_t use = (uint32_t)(g / kStages);
+                uint8_t* sa = smem + st * STAGE;
+                if (*s_abort) return false;
+                if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) { fail(); return false; }
+                // frequencies kc KF + 2 sub, + 1 of curve i (pre-scaled)
+                const float4 a = zi4[kc * (KF / 2)];
+#pragma unroll
+                for (int q = 0; q < NPASS; ++q) {
+                    const float4 b = zbuf[q];
+                    const float v0 = __fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y));
+                    const float v1 = __fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y));
+                    const float v2 = __fmaf_rn(a.z, b.z, __fmul_rn(a.w, b.w));
+                    const float v3 = __fmaf_rn(a.w, b.z, -__fmul_rn(a.z, b.w));
+                    if constexpr (T::ES == 2) {
+                        uint32_t h01, l01, h23, l23;
+                        to_pieces2<V>(v0, v1, h01, l01);
+                        to_pieces2<V>(v2, v3, h23, l23);
+                        *reinterpret_cast<uint2*>(sa + soff[q]) = make_uint2(h01, h23);
+                        *reinterpret_cast<uint2*>(sa + A_PIECE + soff[q]) = make_uint2(l01, l23);
+                    } else {
+                        uint32_t ph[4], pl[4];
+                        to_pieces<V>(v0, ph[0], pl[0]);
+                        to_pieces<V>(v1, ph[1], pl[1]);
+                        to_pieces<V>(v2, ph[2], pl[2]);
+                        to_pieces<V>(v3, ph[3], pl[3]);
+                        *reinterpret_cast<uint4*>(sa + soff[q]) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                        if (T::NP > 1)
+                            *reinterpret_cast<uint4*>(sa + A_PIECE + soff[q]) =
+                                make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                    }
+                }
+                umma::fence_async_smem();
+                umma::mbar_arrive(&a_full[st]);
+                const int fn = ((kc + 2) % NK) * (KF / 2);
+#pragma unroll
+                for (int q = 0; q < NPASS; ++q) zbuf[q] = zrow[q][fn];
+                ++g;
+                return true;
+            };
+            // two chunks per trip: the buffers trade roles without copies
+            bool ok = true;
+            for (int cb = 0; cb < NCB && ok; ++cb)
+                for (int kc = 0; kc < NK && ok; kc += 2) ok = produce(kc, zb) && produce(kc + 1, zb2);
+        } else if (warp < kIssuerWarp) {
+            // ---- epilogue: TMEM lane = pair row ----
+            const int row = (warp - kEpiWarp0) * 32 + lane;
             float best[kCand];
             int bs[kCand];
 #pragma unroll
             for (int q = 0; q < kCand; ++q) { best[q] = -1.0f; bs[q] = 0; }
-
-            for (int cb = 0; cb < NCB && !*s_abort; ++cb) {
-                for (int kc = 0; kc < NK; ++kc, ++g) {
-                    const int st = (int)(g % kStages);
-                    const uint32_t use = (uint32_t)(g / kStages);
-                    uint8_t* sa = smem + st * STAGE;
-                    if (*s_abort) break;
-                    if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) { fail(); break; }
-                    // frequencies kc KF + 2 sub, + 1 of curve i
-                    const float4 a = zi4[kc * (KF / 2)];
-#pragma unroll
-                    for (int q = 0; q < NPASS; ++q) {
-                        const float4 b = zb[q];
-                        float v[4];
-                        v[0] = __fmul_rn(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), kPScale);
-                        v[1] = __fmul_rn(__fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y)), kPScale);
-                        v[2] = __fmul_rn(__fmaf_rn(a.z, b.z, __fmul_rn(a.w, b.w)), kPScale);
-                        v[3] = __fmul_rn(__fmaf_rn(a.w, b.z, -__fmul_rn(a.z, b.w)), kPScale);
-                        uint32_t ph[4], pl[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) to_pieces<V>(v[e], ph[e], pl[e]);
-                        const int r = q * RPP + prow;
-                        const uint32_t off = umma::tile_off(r, sub * 4 * T::ES, kRowB);
-                        if constexpr (T::ES == 2) {
-                            *reinterpret_cast<uint2*>(sa + off) =
-                                make_uint2(ph[0] | (ph[1] << 16), ph[2] | (ph[3] << 16));
-                            *reinterpret_cast<uint2*>(sa + A_PIECE + off) =
-                                make_uint2(pl[0] | (pl[1] << 16), pl[2] | (pl[3] << 16));
-                        } else {
-                            *reinterpret_cast<uint4*>(sa + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                            if (T::NP > 1)
-                                *reinterpret_cast<uint4*>(sa + A_PIECE + off) =
-                                    make_uint4(pl[0], pl[1], pl[2], pl[3]);
-                        }
-                    }
-                    {   // the chunk after next (K chunks wrap to the first ones for
-                        // the next column block)
-                        const int fn = ((kc + 2) % NK) * (KF / 2);
-#pragma unroll
-                        for (int q = 0; q < NPASS; ++q) {
-                            zb[q] = zb2[q];
-                            zb2[q] = zrow[q][fn];
-                        }
-                    }
-                    umma::fence_async_smem();
-                    umma::mbar_arrive(&a_full[st]);
-                }
-                if (*s_abort) break;
-                // warps 0-3: this column block's |c(s)|^2 into the running top 8
+            // a value below (1 - MARGIN) times the largest seen so far can never
+            // be among the candidates kept at the end (the largest only grows),
+            // so it is not inserted; the kept set is the same as without the
+            // test, and the insertions (a serial chain) become rare
+            float top = -1.0f;
+            bool ok = true;
+            for (int cb = 0; cb < NCB && ok; ++cb) {
                 const int buf = (int)(cbg & 1);
-                if (tid < kTcT) {
-                    if (!umma::mbar_wait(&acc_full[buf], (uint32_t)(cbg >> 1) & 1)) { fail(); break; }
-                    umma::tc_fence_after();
+                if (!umma::mbar_wait(&acc_full[buf], (uint32_t)(cbg >> 1) & 1)) { fail(); ok = false; break; }
+                umma::tc_fence_after();
 #pragma unroll 1
-                    for (int c0 = 0; c0 < 128; c0 += 32) {
-                        float re[32], im[32];
-                        const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 256);
-                        umma::tmem_ld32(base + (uint32_t)c0, re);
-                        umma::tmem_ld32(base + (uint32_t)(128 + c0), im);
+                for (int c0 = 0; c0 < 128; c0 += 32) {
+                    float re[32], im[32];
+                    const uint32_t base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
+                    umma::tmem_ld32(base + (uint32_t)c0, re);
+                    umma::tmem_ld32(base + (uint32_t)(128 + c0), im);
+                    float m = top;
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            float x = __fmaf_rn(re[q], re[q], __fmul_rn(im[q], im[q]));
-                            if (x > best[kCand - 1]) {
-                                int sx = cb * 128 + c0 + q;
+                    for (int q = 0; q < 32; ++q) {
+                        re[q] = __fmaf_rn(re[q], re[q], __fmul_rn(im[q], im[q]));
+                        m = fmaxf(m, re[q]);
+                    }
+                    top = m;
+                    const float thr = fmaxf(best[kCand - 1], __fmul_rn(top, 1.0f - T::MARGIN));
 #pragma unroll
-                                for (int r = 0; r < kCand; ++r) {
-                                    if (x > best[r]) {
-                                        const float tv = best[r];
-                                        const int ts = bs[r];
-                                        best[r] = x; bs[r] = sx;
-                                        x = tv; sx = ts;
-                                    }
+                    for (int q = 0; q < 32; ++q) {
+                        float x = re[q];
+                        if (x > best[kCand - 1] && x >= thr) {
+                            int sx = cb * 128 + c0 + q;
+#pragma unroll
+                            for (int r = 0; r < kCand; ++r) {
+                                if (x > best[r]) {
+                                    const float tv = best[r];
+                                    const int ts = bs[r];
+                                    best[r] = x; bs[r] = sx;
+                                    x = tv; sx = ts;
                                 }
                             }
                         }
                     }
-                    umma::tc_fence_before();
-                    umma::mbar_arrive(&tmem_empty[buf]);
                 }
+                umma::tc_fence_before();
+                umma::mbar_arrive(&tmem_empty[buf]);
                 ++cbg;
             }
-            if (tid < kTcT && j0 + tid < M && !*s_abort) {
-                const int64_t j = j0 + tid;
+            if (ok && j0 + row < M && !*s_abort) {
+                const int64_t j = j0 + row;
                 // candidates that can still be the maximum (see TcVar::MARGIN); the
                 // count rides in bits 12-15 of the first entry (shifts < 4096)
                 int keep = 0;
@@ -408,22 +460,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 w.w = (uint32_t)bs[6] | ((uint32_t)bs[7] << 16);
                 *reinterpret_cast<uint4*>(cand + ((size_t)i * M + j) * kCand) = w;
             }
-        } else if (lane == 0) {
-            // the issuer: DFT blocks two chunks ahead (across column blocks),
-            // MMAs, commits; chunk c of the tile is column block c / NK, K chunk
-            // c % NK, and DFT block c of the pre-tiled table
+        } else if (warp == kIssuerWarp && lane == 0) {
+            // ---- the MMA issuer: chunk c as soon as its operands are in.
+            // Chunk c of the tile is column block c / NK, K chunk c % NK.
             constexpr int NC = NCB * NK;
-            auto copy_b = [&](int c) -> bool {
-                const int st = (int)(copied % kStages);
-                const uint32_t use = (uint32_t)(copied / kStages);
-                if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) return false;
-                mbar_expect_tx(&b_full[st], B_BYTES);
-                bulk_g2s(smem + st * STAGE + A_PIECE * T::NP, tab + (size_t)c * B_BYTES, B_BYTES,
-                         &b_full[st]);
-                ++copied;
-                return true;
-            };
-            if (!copy_b(0) || (NC > 1 && !copy_b(1))) fail();
             for (int c = 0; c < NC && !*s_abort; ++c, ++g) {
                 const int kc = c % NK;
                 const int buf = (int)(cbg & 1);
@@ -434,7 +474,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     fail();
                     break;
                 }
-                if (c + 2 < NC && !copy_b(c + 2)) { fail(); break; }
                 if (!umma::mbar_wait(&b_full[st], use & 1) || !umma::mbar_wait(&a_full[st], use & 1)) {
                     fail();
                     break;
@@ -462,15 +501,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     ++cbg;
                 }
             }
-            // copies started but not consumed (only after an abort) land before
-            // the CTA may exit
-            for (int64_t gg = g; gg < copied; ++gg)
-                if (!umma::mbar_wait(&b_full[gg % kStages], (uint32_t)(gg / kStages) & 1)) atomicExch(err, 1);
-            g = copied;
+        } else if (warp == kCopyWarp && lane == 0) {
+            // ---- the DFT-block copier: block c (= chunk c of the tile) into
+            // the stage of chunk c as soon as the MMAs of chunk c - kStages are
+            // done with it, so copies run up to kStages chunks ahead
+            constexpr int NC = NCB * NK;
+            for (int c = 0; c < NC && !*s_abort; ++c, ++g) {
+                const int st = (int)(g % kStages);
+                const uint32_t use = (uint32_t)(g / kStages);
+                if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) { fail(); break; }
+                mbar_expect_tx(&b_full[st], B_BYTES);
+                bulk_g2s(smem + st * STAGE + A_PIECE * T::NP, tab + (size_t)c * B_BYTES, B_BYTES,
+                         &b_full[st]);
+                ++copied;
+            }
         }
     }
+    // copies started and never consumed (only after an abort) land before
+    // the CTA may exit: the copier waits for its own copies
+    if (warp == kCopyWarp && lane == 0) {
+        const int64_t first = copied > kStages ? copied - kStages : 0;
+        for (int64_t gg = first; gg < copied; ++gg)
+            if (!umma::mbar_wait(&b_full[gg % kStages], (uint32_t)(gg / kStages) & 1)) atomicExch(err, 1);
+    }
     // every MMA this CTA issued has finished before the tensor memory is freed
-    if (warp == kTcProducers / 32 && lane == 0 && g > 0 && !*s_abort) {
+    if (warp == kIssuerWarp && lane == 0 && g > 0 && !*s_abort) {
         const int64_t gl = g - 1;
         if (!umma::mbar_wait(&mma_done[gl % kStages], (uint32_t)(gl / kStages) & 1)) atomicExch(err, 1);
     }
