@@ -538,16 +538,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 template <typename ZT>
 __device__ __forceinline__ cdf ld_df(const ZT* p, int64_t k) { return split_c(p[k]); }
 
-// a b in float-float (exact leading product by FMA)
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
-{
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
-    return fast_two_sum(p, e);
-}
-
 __device__ __forceinline__ dfl shfl_df(dfl v, int off)
 {
     return {__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)};

@@ -62,6 +62,29 @@ __device__ __forceinline__ dfl df_dot2(dfl a, dfl b, dfl c, dfl d)
     return fast_two_sum(s.h, err);
 }
 
+// a b (the leading product split exactly by FMA; about 2^-47 relative)
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+
+// 1/x for x != 0: the FP32 reciprocal of the leading part and one Newton step
+// r0 + r0 (1 - x r0), its residual formed by FMA (1 - x.h r0 is exact to
+// 2^-48, x r0 being within 2^-23 of 1); about 2^-46 relative
+__device__ __forceinline__ dfl df_rcp(dfl x)
+{
+    const float r0 = __frcp_rn(x.h);
+    const float e = __fmaf_rn(-x.l, r0, __fmaf_rn(-x.h, r0, 1.0f));
+    return fast_two_sum(r0, __fmul_rn(r0, e));
+}
+
+__device__ __forceinline__ dfl df_neg(dfl x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ dfl df_twice(dfl x) { return {__fmul_rn(2.0f, x.h), __fmul_rn(2.0f, x.l)}; }
+
 // complex double-float, stored in shared memory as float4 (re.h, re.l, im.h, im.l)
 struct cdf {
     dfl re, im;

@@ -194,6 +194,46 @@ __device__ __forceinline__ double twice_pos(double x)
     return __longlong_as_double((long long)r);
 }
 
+// ---- the spline solve in float-float, in units scaled by 2^k ~ 1/L --------
+// v 2^k as a double-float, from the bits (split_d with the exponent moved by
+// k): exact to 2^-47 relative; magnitudes that land below 2^-126 give 0 (only
+// a chord vector's near-zero component can), and the caller keeps every
+// scaled magnitude below 2^120.
+__device__ __forceinline__ dfl split_scaled(double v, int k)
+{
+    const long long b = __double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const int fe = e - 1023 + 127 + k;  // float exponent field of v 2^k
+    if (e == 0 || fe <= 0) return {0.f, 0.f};
+    const unsigned sign = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7fffff));
+    if (fe < 53) return {hi, 0.f};
+    const int m = (int)(b & 0x1fffffff);
+    const float lo = __fmul_rn(__int2float_rn(m), __uint_as_float((unsigned)(fe - 52) << 23));
+    return {hi, sign ? -lo : lo};
+}
+// f 2^k as a double, from the bits (zero and subnormal floats give 0; the
+// caller keeps |k| < 800, so the exponent stays in range)
+__device__ __forceinline__ double widen_scaled(float f, int k)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned ef = (u >> 23) & 0xff;
+    if (ef == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(ef - 127 + 1023 + k) << 52) |
+                                            ((unsigned long long)(u & 0x7fffff) << 29)));
+}
+// (x.h + x.l) 2^k in FP64: one FP64 instruction
+__device__ __forceinline__ double to_d(dfl x, int k) { return widen_scaled(x.h, k) + widen_scaled(x.l, k); }
+// unit chord direction (p_{l+1} - p_l) / d_l from the chord vector and 1/d_l,
+// each scaled by 2^k and 2^-k, multiplied in float-float
+__device__ __forceinline__ cdf tau_df(double2 cv, double ih, int k)
+{
+    const dfl s = split_scaled(ih, -k);
+    return {df_mul(split_scaled(cv.x, k), s), df_mul(split_scaled(cv.y, k), s)};
+}
+__device__ __forceinline__ cdf cscale(cdf a, dfl s) { return {df_mul(a.re, s), df_mul(a.im, s)}; }
+
 __device__ __forceinline__ double2 d2(double x, double y) { return make_double2(x, y); }
 __device__ __forceinline__ double2 add2(double2 a, double2 b) { return d2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 sub2(double2 a, double2 b) { return d2(a.x - b.x, a.y - b.y); }
@@ -286,7 +326,8 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     // d = q * rsqrt(q) and 1/d = rsqrt(q) from one reciprocal square root
     // (q = |p_{l+1} - p_l|^2 >= 0, so its bit pattern tests > 0 as an integer)
     bool zero = false, nf = false;
-    unsigned emax = 0;  // largest biased exponent of a coordinate
+    unsigned emax = 0;      // largest biased exponent of a coordinate
+    unsigned dmin = 2047u;  // smallest biased exponent of a chord length
     for (int l = lane; l < n; l += 32) {
         const double2 pl = __ldg(p + l);
         const double2 pn = __ldg(p + ((l + 1 == n) ? 0 : l + 1));
@@ -298,7 +339,9 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         const bool pos = __double_as_longlong(q) > 0;
         const double rs = rsqrt_nr(q);
         zero |= !pos;
-        D[l] = pos ? q * rs : 0.0;
+        const double dl = pos ? q * rs : 0.0;
+        dmin = min(dmin, (unsigned)(__double_as_longlong(dl) >> 52) & 0x7ffu);
+        D[l] = dl;
         IH[l] = rs;
         CV[l] = d2(dx, dy);
     }
@@ -326,6 +369,18 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     const double base = incl - csum;  // arc length before node s_j
     __syncwarp();
 
+    // The spline solve (steps B-D) runs in float-float, in units scaled by
+    // 2^ks (2^-ks <= L < 2^(1-ks)): scaled chords are in (2^-100, 2), their
+    // reciprocals below 2^100, every quantity of the solve in float range.
+    // Curves whose chords span more than 2^100 below L, or whose perimeter
+    // is beyond 2^+-800, solve in FP64.  The solve needs ~1e-8 relative on M
+    // (M enters the outputs through terms of order d^2 |M|, a 1e-4..1e-6 part
+    // of the curve for these samplings); float-float gives ~1e-13.
+    const int eLb = (int)((__double_as_longlong(L) >> 52) & 0x7ff);  // biased exponent of L
+    const int dminw = (int)__reduce_min_sync(0xffffffffu, dmin);
+    const bool dfsolve = eLb > 1023 - 800 && eLb < 1023 + 800 && eLb - dminw < 100;
+    const int ks = 1023 - eLb;
+
     // ---- B: forward sweep over the interior ---------------------------------
     // The system is solved for M' = M / (6 L^2) (right-hand sides tau_l -
     // tau_{l-1}); the evaluation uses h^2 M' = h^2 M / (6 L^2).  The first
@@ -343,7 +398,9 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     double gL = 0, kL = 0;
     double2 yF = d2(0, 0);
     double gF = 0, kF = 0;
-    if (act) {
+    cdf yLd{{0.f, 0.f}, {0.f, 0.f}};  // the float-float solve's last interior values
+    dfl gLd{0.f, 0.f}, kLd{0.f, 0.f};
+    if (act && !dfsolve) {
         const double* __restrict__ Dr = D;
         const double* __restrict__ IHr = IH;
         const double2* __restrict__ CVr = CV;
@@ -393,6 +450,61 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         Ae = hprev;
         Ce = h;
         Be = twice_pos(hprev + Ce);
+    } else if (act) {
+        // the same sweep in float-float (scaled units; FP64 only for the arc
+        // lengths S and the conversions of the interface data below)
+        const double* __restrict__ Dr = D;
+        const double* __restrict__ IHr = IH;
+        const double2* __restrict__ CVr = CV;
+        double* __restrict__ Ur = U;
+        float4* __restrict__ F0r = reinterpret_cast<float4*>(F0);
+        float4* __restrict__ F1r = reinterpret_cast<float4*>(F1);
+        const int lp = (sj == 0) ? n - 1 : sj - 1;
+        dfl hprev = split_scaled(Dr[lp], ks);
+        cdf tprev = tau_df(CVr[lp], IHr[lp], ks);
+        double S = base;
+        dfl cp{0.f, 0.f}, gp{-1.f, 0.f}, pi{1.f, 0.f}, gFd{0.f, 0.f};
+        cdf yp{{0.f, 0.f}, {0.f, 0.f}}, yFd{{0.f, 0.f}, {0.f, 0.f}};
+        double h64 = Dr[sj], ih64 = IHr[sj];
+        double2 cv = CVr[sj];
+        for (int i = sj; i < ej; ++i) {
+            const double hn64 = Dr[i + 1], ihn64 = IHr[i + 1];  // i + 1 <= ej < n
+            const double2 cvn = CVr[i + 1];
+            Ur[i] = S;
+            S += h64;
+            const dfl h = split_scaled(h64, ks);
+            const cdf tau = tau_df(cv, ih64, ks);
+            const cdf R = csub(tau, tprev);
+            const dfl den = df_sub(df_twice(df_add(hprev, h)), df_mul(hprev, cp));
+            const dfl r = df_rcp(den);
+            const dfl ncp = df_mul(h, r);
+            const cdf nyp{df_mul(df_sub(R.re, df_mul(hprev, yp.re)), r),
+                          df_mul(df_sub(R.im, df_mul(hprev, yp.im)), r)};
+            const dfl ngp = df_neg(df_mul(df_mul(hprev, gp), r));
+            F0r[i] = make_float4(ncp.h, ncp.l, ngp.h, ngp.l);
+            F1r[i] = st4(nyp);
+            yFd = cadd(yFd, cscale(nyp, pi));
+            gFd = df_add(gFd, df_mul(pi, ngp));
+            pi = df_neg(df_mul(pi, ncp));
+            cp = ncp; gp = ngp; yp = nyp;
+            hprev = h; tprev = tau;
+            h64 = hn64; ih64 = ihn64; cv = cvn;
+        }
+        yLd = yp; gLd = gp; kLd = cp;
+        Ur[ej] = S;
+        const cdf Red = csub(tau_df(cv, ih64, ks), tprev);
+        const dfl Ced = split_scaled(h64, ks);
+        // the interface data in FP64 for the reduced system (scaled units)
+        Ae = to_d(hprev, 0);
+        Ce = to_d(Ced, 0);
+        Be = to_d(df_twice(df_add(hprev, Ced)), 0);
+        Re = d2(to_d(Red.re, 0), to_d(Red.im, 0));
+        yL = d2(to_d(yp.re, 0), to_d(yp.im, 0));
+        gL = to_d(gp, 0);
+        kL = to_d(cp, 0);
+        yF = d2(to_d(yFd.re, 0), to_d(yFd.im, 0));
+        gF = to_d(gFd, 0);
+        kF = -to_d(pi, 0);
     }
 
     // reduced cyclic system over the P interfaces:
@@ -436,7 +548,25 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     const double2 Iprev = shfl_d2(I, prv, P);
 
     // ---- D: second backward sweep writes M ----------------------------------
-    if (act) {
+    if (act && dfsolve) {
+        // float-float, scaled units; M' = M_scaled 2^ks stored in FP64
+        const double sc = __longlong_as_double((long long)(1023 + ks) << 52);  // 2^ks
+        M[ej] = scl2(I, sc);
+        const cdf Id = split_c(I), Ipd = split_c(Iprev);
+        cdf Mi{df_sub(df_sub(yLd.re, df_mul(Ipd.re, gLd)), df_mul(Id.re, kLd)),
+               df_sub(df_sub(yLd.im, df_mul(Ipd.im, gLd)), df_mul(Id.im, kLd))};
+        M[ej - 1] = d2(to_d(Mi.re, ks), to_d(Mi.im, ks));
+        const float4* __restrict__ F0r = reinterpret_cast<const float4*>(F0);
+        const float4* __restrict__ F1r = reinterpret_cast<const float4*>(F1);
+        for (int i = ej - 2; i >= sj; --i) {
+            const float4 f0 = F0r[i];
+            const cdf y = ld4(F1r[i]);
+            const dfl c{f0.x, f0.y}, g{f0.z, f0.w};
+            Mi = {df_sub(df_sub(y.re, df_mul(c, Mi.re)), df_mul(g, Ipd.re)),
+                  df_sub(df_sub(y.im, df_mul(c, Mi.im)), df_mul(g, Ipd.im))};
+            M[i] = d2(to_d(Mi.re, ks), to_d(Mi.im, ks));
+        }
+    } else if (act) {
         M[ej] = I;
         double2 Mi = d2(yL.x - Iprev.x * gL - I.x * kL, yL.y - Iprev.y * gL - I.y * kL);
         M[ej - 1] = Mi;

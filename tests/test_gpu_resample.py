@@ -124,6 +124,27 @@ def test_resample_extreme_scales(scale):
     assert np.abs(z - zo).max() <= TOL
 
 
+def test_resample_fp64_fallback_for_chords_spanning_2_to_the_100():
+    """A curve whose first chord is about 1e-35 of its perimeter takes the
+    kernel's FP64 spline solve instead of the float-float one (scaled chords
+    must stay above 2^-100); both paths meet the same bound against the
+    oracle, here in one batch.  The curve is moved so that node 0 is the
+    origin, which makes a chord that short representable, and node 1 is put
+    next to it (as the first chord its knot interval u_1 - u_0 = d_0 / L stays
+    nonzero in FP64)."""
+    pts, offs = synth.raw_curves(45, C=8, n_min=200, n_max=600)
+    pts = pts.copy()
+    for c in (1, 5):
+        a, b = offs[c], offs[c + 1]
+        pts[a:b] -= pts[a]
+        pts[a + 1] = 1e-35 + 1e-35j
+    z, st = _gpu_resample(pts, offs, 512)
+    zo, sto = oracle.resample(pts, offs, 512)
+    np.testing.assert_array_equal(st, sto)
+    assert (st == 0).all()
+    assert np.abs(z - zo).max() <= TOL
+
+
 def test_resample_fp32_storage():
     pts, offs = synth.raw_curves(8, C=32, n_min=500, n_max=2000)
     z, st = _gpu_resample(pts, offs, 1024, fp32=True)
