@@ -573,8 +573,17 @@ __device__ int rigid_fft(double2* X, const double2* Acopy, const double2* Bspec,
 
 // NMAX: the largest N this instantiation handles (sizes the per-thread
 // register blocks of the transforms and of the reduction solver)
+// Resident pair CTAs per SM the kernel is compiled for: at N <= 256 four (its
+// registers capped at 128, with some spills; the Catmull-Rom table and the
+// back-pointers then live in the workspace), which measured 5.7 % faster than
+// two CTAs of 246 registers with everything in shared memory (18.75 against
+// 19.88 ms on 4,096 gallery pairs, identical energies); larger N are bound by
+// shared memory to two.
+template <int NMAX>
+constexpr int el_min_blocks() { return NMAX <= 256 ? 4 : 1; }
+
 template <int T, int NMAX>
-__global__ void __launch_bounds__(T) elastic_pair_kernel(const __grid_constant__ ElasticArgs a)
+__global__ void __launch_bounds__(T, el_min_blocks<NMAX>()) elastic_pair_kernel(const __grid_constant__ ElasticArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N, tid = threadIdx.x;
@@ -840,7 +849,8 @@ struct ElLayout {
     int64_t q2f_elems, bp_bytes;
 };
 
-constexpr size_t kSmemBudget = 112 * 1024;  // two pair CTAs per SM
+// shared memory per pair CTA: four CTAs per SM at N <= 256, two above
+inline size_t el_smem_budget(int N) { return N <= 256 ? (size_t)56 * 1024 : (size_t)112 * 1024; }
 
 ElLayout el_layout(const fa_handle* h, int64_t Mtot, int64_t P, int N, int band)
 {
@@ -853,12 +863,20 @@ ElLayout el_layout(const fa_handle* h, int64_t Mtot, int64_t P, int N, int band)
                    (kElT / 32 + 2) * 8 * sizeof(double) + (kElT / 32) * (sizeof(long long) + sizeof(int)) +
                    4 * sizeof(int) + 16;
     size_t sm = fixed;
-    L.q2f_smem = sm + L.q2f_elems * sizeof(double2) <= kSmemBudget;
+    const size_t budget = el_smem_budget(N);
+    L.q2f_smem = sm + L.q2f_elems * sizeof(double2) <= budget;
     if (L.q2f_smem) sm += L.q2f_elems * sizeof(double2);
-    L.bp_smem = sm + (size_t)L.bp_bytes <= kSmemBudget;
+    L.bp_smem = sm + (size_t)L.bp_bytes <= budget;
     if (L.bp_smem) sm += (size_t)L.bp_bytes;
     L.smem = sm;
-    const int per_sm = sm <= kSmemBudget ? (sm <= 72 * 1024 ? 3 : 2) : 1;
+    int per_sm = 1;
+    {
+        const void* k = N <= 256 ? (const void*)elastic_pair_kernel<kElT, 256>
+                                 : (const void*)elastic_pair_kernel<kElT, 1024>;
+        if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kElT, sm) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
     L.grid = (int)std::max<int64_t>(1, std::min<int64_t>(P, (int64_t)h->num_sms * per_sm));
     size_t o = 0;
     L.off_offsets = o; o = align256(o + sizeof(int64_t) * (size_t)(Mtot + 1));
