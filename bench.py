@@ -757,7 +757,9 @@ def run_gpu(args):
             sel = nz[np.log2(Lz).astype(int) == bkt]
             flb = ragged_flops(sel)
             per_bucket[f"L=2^{bkt}"] = {
-                "pairs": int(sel.size), "threads": t_, "pairs_per_cta": g_, "ms": ms_,
+                "pairs": int(sel.size), "threads": t_,
+                "pairs_per_cta": g_ if g_ > 0 else None,
+                "ctas_per_pair": -g_ if g_ < 0 else 1, "ms": ms_,
                 "frac_of_fp64_peak": (flb / (ms_ * 1e-3) / 1e12 / fp64_peak) if ms_ > 0 else None}
         rag = {"workload": f"{Pr} pairs, n log-uniform in [64, 8192] (multiples of 16), 4..32 "
                            "harmonics, FP64, one persistent launch per transform-length bucket",

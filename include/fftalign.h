@@ -315,8 +315,9 @@ int fa_align_pairs_ragged(fa_handle* h, const void* z1, const void* z2, const in
 /*
  * Autotuner of fa_align_pairs_ragged: for every transform-length bucket the
  * caller's batch fills, runs that bucket's pairs with each compiled plan that
- * fits the length (CTA sizes 128..1024 threads, 1..16 pairs per CTA), one
- * warm-up and three timed runs each, and keeps the fastest plan per bucket in
+ * fits the length (CTA sizes 128..1024 threads, 1..16 pairs per CTA, and for
+ * L = 8192 and 16384 also one pair per thread-block cluster of L/4096 CTAs),
+ * one warm-up and three timed runs each, and keeps the fastest plan per bucket in
  * the handle for later calls (fa_align_pairs_ragged_plan reports them).
  * *chosen_threads receives the CTA size chosen for the longest bucket
  * present.  Same arguments and outputs as fa_align_pairs_ragged (the outputs
@@ -331,16 +332,21 @@ int fa_align_pairs_ragged_autotune(fa_handle* h, const void* z1, const void* z2,
                                    void* stream, int32_t* chosen_threads);
 
 /* The handle's plan for fa_align_pairs_ragged, per bucket b = log2 L in
- * [0, 16): threads[b] (CTA size), pairs_per_cta[b], and ms[b], the time of
+ * [0, 16): threads[b] (CTA size), pairs_per_cta[b] (-R for one pair per
+ * cluster of R CTAs), and ms[b], the time of
  * that bucket's launch measured by the last autotuning (0 when not tuned);
  * entries outside the supported lengths are 0.  Any pointer may be NULL
  * (HOST arrays of 16 entries). */
 int fa_align_pairs_ragged_plan(fa_handle* h, int32_t* threads, int32_t* pairs_per_cta, float* ms);
 /* Sets the handle's plan for bucket log2 L = bucket (in [2, 14]): one of the
  * compiled (threads, pairs_per_cta) combinations -- (256|512|1024, 1),
- * (128|256|512, 2), (128|256|512, 4), (256, 8), (256, 16) -- that fits the
- * length (pairs_per_cta >= 2 needs pairs_per_cta L <= 2048 and at most L
- * threads per pair); FA_ERR_UNSUPPORTED otherwise. */
+ * (128|256|512, 2), (128|256|512, 4), (256, 8), (256, 16), and the cluster
+ * plans (256|512, -2) for L = 8192 and (256|512, -4) for L = 16384, in which
+ * the R CTAs of a thread-block cluster share one pair (each transforms one of
+ * the R decimation-in-frequency parts in its shared memory and the
+ * recombination reads the others' parts through distributed shared memory)
+ * -- that fits the length (pairs_per_cta >= 2 needs pairs_per_cta L <= 2048
+ * and at most L threads per pair); FA_ERR_UNSUPPORTED otherwise. */
 int fa_align_pairs_ragged_set_plan(fa_handle* h, int32_t bucket, int32_t threads,
                                    int32_t pairs_per_cta);
 

@@ -219,7 +219,8 @@ def align_pairs_ragged(z1: torch.Tensor, z2: torch.Tensor, offsets: torch.Tensor
 def ragged_plan(device: int | None = None) -> dict:
     """The handle's per-bucket plan for align_pairs_ragged (fa_align_pairs_ragged_plan):
     {log2 L: (CTA size, pairs per CTA, ms of the last autotuning)} for the
-    supported transform lengths."""
+    supported transform lengths; pairs per CTA is -R for a plan in which a
+    thread-block cluster of R CTAs shares one pair (L = 8192, 16384)."""
     L = _lib.load()
     t = (ctypes.c_int32 * 16)()
     g = (ctypes.c_int32 * 16)()

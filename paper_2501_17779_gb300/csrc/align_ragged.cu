@@ -24,6 +24,8 @@
 // a memset on the caller's stream, so the sequence can be captured in a CUDA
 // graph.  The CTA size (256, 512 or 1024 threads) is the tunable, chosen by
 // fa_align_pairs_ragged_autotune from timed runs on the caller's batch.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "fa_internal.cuh"
@@ -351,6 +353,183 @@ __global__ void __launch_bounds__(T)
     }
 }
 
+// ---- one pair per thread-block cluster (L = R BMAX, R = 2 or 4) -------------
+// CTA q of the cluster computes DIF part q of both spectra and F_q =
+// DFT_B(Z1_q conj Z2_q), all in its own shared memory (no global slots); the
+// recombination L c(s) = sum_q W_L^{qs} F_q[s mod B] reads the other CTAs' F_q
+// through distributed shared memory, each CTA taking a 1/R share of the
+// shifts; the argmax, c(s*) and the energy are reduced over the cluster in
+// rank order.  Every CTA of a cluster takes the same branches and reaches every
+// cluster barrier (the pair index is read from rank 0 and the non-finite test
+// is repeated by every rank on the whole curves).
+struct ClusterShared {
+    long long key;  // this rank's best |c|^2 key
+    double2 c;      // this rank's share of c(s*)
+    double e;       // this rank's share of the energy sum
+    int idx;        // shift of key
+    int item;       // the pair's position in the bucket (rank 0)
+    int bad;
+};
+
+template <int T>
+constexpr size_t ragged_cluster_smem()
+{
+    return (size_t)2 * BMAX * 16 + (size_t)(T + 1) * 16 + (size_t)(T / 32) * 12 + 16 +
+           sizeof(ClusterShared);
+}
+
+template <int T, int R, typename ZT>
+__global__ void __launch_bounds__(T, 1)
+    ragged_cluster_kernel(const __grid_constant__ RaggedArgs a, const __grid_constant__ Tables tb)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank();
+    extern __shared__ __align__(16) double2 smem[];
+    double2* Z = smem;                  // [BMAX] curve 1's part q, then its spectrum
+    double2* X = Z + BMAX;              // [BMAX] curve 2's part q, the product, then F_q
+    double2* part = X + BMAX;           // [T + 1] CTA sums
+    long long* sk = reinterpret_cast<long long*>(part + T + 1);  // [T / 32]
+    int* si = reinterpret_cast<int*>(sk + T / 32);               // [T / 32]
+    ClusterShared* sh = reinterpret_cast<ClusterShared*>(
+        (reinterpret_cast<uintptr_t>(si + T / 32) + 15) & ~uintptr_t(15));
+    const int tid = threadIdx.x;
+    const ZT* Z1 = static_cast<const ZT*>(a.z1);
+    const ZT* Z2 = static_cast<const ZT*>(a.z2);
+    const int b = a.bucket;
+    const int count = a.cnt->hist[b];
+    int start = 0;
+    for (int k = b + 1; k < kBuckets; ++k) start += a.cnt->hist[k];
+    const int L = 1 << b;
+    constexpr int B = BMAX;
+    const double2* Wf = tb.tf[LOG_BMAX];
+    const double2* WL = tb.tw[b];
+    const double2* F[R];
+    ClusterShared* shr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        F[r] = cluster.map_shared_rank(X, r);
+        shr[r] = cluster.map_shared_rank(sh, r);
+    }
+
+    for (;;) {
+        if (q == 0 && tid == 0) sh->item = atomicAdd(&a.cnt->bhead[b], 1);
+        cluster.sync();
+        const int item = shr[0]->item;
+        cluster.sync();  // every rank has read rank 0's value before it changes
+        if (item >= count) break;
+        const int p = a.order[start + item];
+        const int64_t o = a.off[p];
+        const int n = (int)(a.off[p + 1] - o);
+        const ZT* z1 = Z1 + o;
+        const ZT* z2 = Z2 + o;
+        if (tid == 0) sh->bad = 0;
+        __syncthreads();
+        bool nf = false;
+        for (int k = tid; k < n; k += T) nf |= !finite2(ld_z(z1, k)) || !finite2(ld_z(z2, k));
+        if (nf) sh->bad = 1;
+        __syncthreads();
+        const bool bad = sh->bad != 0;
+        const int nn = bad ? 0 : n;
+
+        // part q of both spectra, the product, F_q
+        load_dif<T, 0>(Z, z1, nn, L, B, R, q, WL, tid);
+        __syncthreads();
+        fft_rt<T, BMAX>(Z, LOG_BMAX, Wf);
+        load_dif<T, 1>(X, z2, nn, L, B, R, q, WL, tid);
+        __syncthreads();
+        fft_rt<T, BMAX>(X, LOG_BMAX, Wf);
+        for (int m = tid; m < B; m += T) X[m] = cmulc(Z[m], X[m]);
+        __syncthreads();
+        fft_rt<T, BMAX>(X, LOG_BMAX, Wf);
+        cluster.sync();  // every F_q is complete
+
+        // this rank's shifts: L c(s) = sum_r W_L^{rs} F_r[s mod B]
+        const int share = (nn + R - 1) / R;
+        const int s0 = q * share, s1 = min(nn, s0 + share);
+        long long key = -1;
+        int idx = 0;
+        for (int s = s0 + tid; s < s1; s += T) {
+            const int sm = s & (B - 1);
+            double2 c = F[0][sm];
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const double2 f = cmul(F[r][sm], __ldg(WL + ((r * s) & (L - 1))));
+                c.x += f.x;
+                c.y += f.y;
+            }
+            const long long kq = __double_as_longlong(fma(c.x, c.x, c.y * c.y));
+            if (key_better(kq, s, key, idx)) { key = kq; idx = s; }
+        }
+        cta_argmax<T>(key, idx, sk, si);
+        if (tid == 0) { sh->key = key; sh->idx = idx; }
+        cluster.sync();
+        long long bk = -1;
+        int sbest = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long kr = shr[r]->key;
+            const int ir = shr[r]->idx;
+            if (key_better(kr, ir, bk, sbest)) { bk = kr; sbest = ir; }
+        }
+
+        // c(s*) and the energy by their definitions, k split over the ranks
+        const int k0 = s0, k1 = s1;
+        double2 c = make_double2(0.0, 0.0);
+        for (int k = k0 + tid; k < k1; k += T) {
+            const double2 u = ld_z(z1, k);
+            int m = k + sbest;
+            if (m >= nn) m -= nn;
+            const double2 v = ld_z(z2, m);
+            c.x = fma(u.x, v.x, fma(u.y, v.y, c.x));
+            c.y = fma(u.y, v.x, fma(-u.x, v.y, c.y));
+        }
+        c = cta_sum<T>(c, part);
+        if (tid == 0) sh->c = c;
+        cluster.sync();
+        double2 cs = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const double2 cr = shr[r]->c;
+            cs.x += cr.x;
+            cs.y += cr.y;
+        }
+        const double rr = sqrt(fma(cs.x, cs.x, cs.y * cs.y));
+        const double2 rot = rr > 0.0 ? make_double2(cs.x / rr, cs.y / rr) : make_double2(1.0, 0.0);
+        double e = 0.0;
+        for (int k = k0 + tid; k < k1; k += T) {
+            const double2 u = ld_z(z1, k);
+            int m = k + sbest;
+            if (m >= nn) m -= nn;
+            const double2 v = ld_z(z2, m);
+            const double rx = fma(rot.x, v.x, -rot.y * v.y);
+            const double ry = fma(rot.y, v.x, rot.x * v.y);
+            const double dx = u.x - rx, dy = u.y - ry;
+            e = fma(dx, dx, e);
+            e = fma(dy, dy, e);
+        }
+        const double2 es = cta_sum<T>(make_double2(e, 0.0), part);
+        if (tid == 0) sh->e = es.x;
+        cluster.sync();
+        if (q == 0 && tid == 0) {
+            if (bad) {
+                a.shift[p] = -1;
+                a.theta[p] = __longlong_as_double(0x7ff8000000000000LL);
+                a.energy[p] = __longlong_as_double(0x7ff8000000000000LL);
+                a.status[p] = FA_STATUS_NONFINITE;
+            } else {
+                double et = 0.0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) et += shr[r]->e;
+                a.shift[p] = sbest;
+                a.theta[p] = atan2(cs.y, cs.x);
+                a.energy[p] = et / (double)n;
+                a.status[p] = FA_STATUS_OK;
+            }
+        }
+    }
+}
+
 template <int T, int G>
 constexpr size_t ragged_smem()
 {
@@ -358,16 +537,27 @@ constexpr size_t ragged_smem()
     return (size_t)BMAX * 16 + (size_t)G * (TG + 1) * 16 + (size_t)G * SW * 12 + 4 * (1 + G) + 16;
 }
 
-// the plans compiled in: (T, G)
+// the plans compiled in: (T, G); G = -R for one pair per cluster of R CTAs
 struct PlanDesc { int T, G; };
 constexpr PlanDesc kPlans[] = {{256, 1}, {512, 1}, {1024, 1}, {128, 2}, {256, 2}, {512, 2},
-                               {128, 4}, {256, 4}, {512, 4}, {256, 8}, {256, 16}};
+                               {128, 4}, {256, 4}, {512, 4}, {256, 8}, {256, 16},
+                               {256, -2}, {512, -2}, {256, -4}, {512, -4}};
 constexpr int kNPlans = sizeof(kPlans) / sizeof(kPlans[0]);
 
 template <int T, int G>
 const void* kernel_ptr(bool f64)
 {
-    return f64 ? (const void*)ragged_kernel<T, G, double2> : (const void*)ragged_kernel<T, G, float2>;
+    if constexpr (G < 0)
+        return f64 ? (const void*)ragged_cluster_kernel<T, -G, double2>
+                   : (const void*)ragged_cluster_kernel<T, -G, float2>;
+    else
+        return f64 ? (const void*)ragged_kernel<T, G, double2> : (const void*)ragged_kernel<T, G, float2>;
+}
+template <int T, int G>
+constexpr size_t plan_smem()
+{
+    if constexpr (G < 0) return ragged_cluster_smem<T>();
+    else return ragged_smem<T, G>();
 }
 
 // f(kernel pointer, smem bytes) for plan i
@@ -376,10 +566,11 @@ auto with_plan(int i, bool f64, F&& f)
 {
     switch (i) {
 #define FA_PLAN(k, T_, G_) \
-    case k: return f(kernel_ptr<T_, G_>(f64), ragged_smem<T_, G_>(), T_);
+    case k: return f(kernel_ptr<T_, G_>(f64), plan_smem<T_, G_>(), T_);
         FA_PLAN(0, 256, 1) FA_PLAN(1, 512, 1) FA_PLAN(2, 1024, 1) FA_PLAN(3, 128, 2)
         FA_PLAN(4, 256, 2) FA_PLAN(5, 512, 2) FA_PLAN(6, 128, 4) FA_PLAN(7, 256, 4)
         FA_PLAN(8, 512, 4) FA_PLAN(9, 256, 8) FA_PLAN(10, 256, 16)
+        FA_PLAN(11, 256, -2) FA_PLAN(12, 512, -2) FA_PLAN(13, 256, -4) FA_PLAN(14, 512, -4)
 #undef FA_PLAN
     }
     return f(kernel_ptr<256, 1>(f64), ragged_smem<256, 1>(), 256);
@@ -396,8 +587,37 @@ int64_t lmax_for(int max_n)
 
 inline size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// launch configuration of a cluster plan (grid filled in by the caller)
+cudaLaunchConfig_t cluster_config(int T, size_t smem, int R, cudaStream_t st, cudaLaunchAttribute* attr)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3((unsigned)T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr->id = cudaLaunchAttributeClusterDimension;
+    attr->val.clusterDim.x = (unsigned)R;
+    attr->val.clusterDim.y = 1;
+    attr->val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
 int plan_grid(const fa_handle* h, int i)
 {
+    if (kPlans[i].G < 0) {
+        // clusters that can be resident at once, R CTAs each
+        const int R = -kPlans[i].G;
+        int nc = 0;
+        const cudaError_t e = with_plan(i, true, [&](const void* k, size_t smem, int T) {
+            cudaLaunchAttribute attr;
+            cudaLaunchConfig_t cfg = cluster_config(T, smem, R, nullptr, &attr);
+            cfg.gridDim = dim3((unsigned)(R * (h->num_sms > 0 ? h->num_sms : 1)));
+            return cudaOccupancyMaxActiveClusters(&nc, k, &cfg);
+        });
+        if (e != cudaSuccess || nc < 1) nc = 1;
+        return nc * R;
+    }
     int per_sm = 1;
     const cudaError_t e = with_plan(i, true, [&](const void* k, size_t smem, int T) {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, smem);
@@ -419,9 +639,14 @@ int launch_bucket(const fa_handle* h, RaggedArgs a, const Tables& tb, int bucket
 {
     a.bucket = bucket;
     const int grid = plan_grid(h, plan);
+    const int R = kPlans[plan].G < 0 ? -kPlans[plan].G : 1;
     const cudaError_t e = with_plan(plan, f64, [&](const void* k, size_t smem, int T) {
         void* args[] = {(void*)&a, (void*)&tb};
-        return cudaLaunchKernel(k, dim3((unsigned)grid), dim3((unsigned)T), args, smem, st);
+        if (R == 1) return cudaLaunchKernel(k, dim3((unsigned)grid), dim3((unsigned)T), args, smem, st);
+        cudaLaunchAttribute attr;
+        cudaLaunchConfig_t cfg = cluster_config(T, smem, R, st, &attr);
+        cfg.gridDim = dim3((unsigned)grid);
+        return cudaLaunchKernelExC(&cfg, k, args);
     });
     return cuda_error(e, "ragged launch");
 }
@@ -438,6 +663,7 @@ bool ragged_plan_fits(int i, int bucket)
     if (i < 0 || i >= kNPlans) return false;
     const int G = kPlans[i].G, L = 1 << bucket;
     if (G == 1) return true;
+    if (G < 0) return L == -G * BMAX;  // a cluster of R CTAs: exactly R parts of BMAX
     return L <= BMAX / (2 * G) && kPlans[i].T / G <= L;
 }
 

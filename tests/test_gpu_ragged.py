@@ -145,13 +145,14 @@ def test_ragged_large_batch_sampled():
                     st[[p]])
 
 
+# (CTA size, pairs per CTA); -R: one pair per cluster of R CTAs (L = R 4096)
 PLANS = [(256, 1), (512, 1), (1024, 1), (128, 2), (256, 2), (512, 2), (128, 4), (256, 4),
-         (512, 4), (256, 8), (256, 16)]
+         (512, 4), (256, 8), (256, 16), (256, -2), (512, -2), (256, -4), (512, -4)]
 
 
 def test_ragged_every_plan_on_every_bucket_it_fits():
-    """Each compiled plan (CTA size, pairs per CTA), pinned on every transform
-    length it can run, against the FP64 oracle: buckets log2 L = 2..14 with
+    """Each compiled plan (CTA size, pairs per CTA, or a cluster of CTAs per
+    pair), pinned on every transform length it can run, against the FP64 oracle: buckets log2 L = 2..14 with
     several pairs each (partly filled multi-pair CTAs included), powers of two
     and padded lengths, one radix-R split length per R."""
     sizes = [4, 5, 7, 9, 16, 17, 20, 33, 60, 64, 65, 100, 128, 129, 200, 256, 257, 300, 400,
@@ -194,5 +195,10 @@ def test_ragged_plan_rejects_what_does_not_fit():
         api.set_ragged_plan(5, 256, 2)    # 128 threads per 32-point pair
     with pytest.raises(RuntimeError):
         api.set_ragged_plan(8, 384, 1)    # not compiled
+    with pytest.raises(RuntimeError):
+        api.set_ragged_plan(13, 512, -4)  # a cluster of 4 needs L = 16384
+    with pytest.raises(RuntimeError):
+        api.set_ragged_plan(12, 256, -2)  # 4096 points fit one CTA
     plan = api.ragged_plan()
-    assert set(plan) == set(range(2, 15)) and all(t > 0 and g >= 1 for t, g, _ in plan.values())
+    assert set(plan) == set(range(2, 15))
+    assert all(t > 0 and (g >= 1 or g in (-2, -4)) for t, g, _ in plan.values())
