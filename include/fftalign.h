@@ -392,9 +392,9 @@ int fa_align_curves_host(fa_handle* h, const double* pts, const int64_t* offsets
  *
  * Scratch: a fixed device array of FA_NOALLOC_SCRATCH_BYTES (64 MiB) that
  * every GPU which loads the library holds until the process exits.  A batch
- * needs fa_resample_workspace_size(C, n_pts, N_out, flags) bytes of it (72
+ * needs fa_resample_workspace_size(C, n_pts, N_out, flags) bytes of it (48
  * bytes per input node, plus 16 bytes per output node with FA_STORE_FP32:
- * about 930,000 input nodes per call); larger batches are rejected with
+ * about 1.39 million input nodes per call); larger batches are rejected with
  * FA_ERR_UNSUPPORTED and a message giving both sizes.  Nothing is allocated
  * or freed; each call resets one 8-byte work counter inside the array with a
  * memset on `stream`.

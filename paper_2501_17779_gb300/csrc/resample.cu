@@ -24,11 +24,14 @@
 //   D. a backward sweep writes M for every node.
 //   E. the spline is evaluated at t_k = k/N_out (each lane a contiguous block
 //      of outputs; interval search by integer compares on the knots; the
-//      chord vectors p_{l+1} - p_l of step A are kept for B and E; the
 //      closed-polygon perimeter of the outputs is summed in the same loop),
 //      then the outputs are centred at their mean and divided by it.
-// Per-node intermediates live in a caller- or handle-provided workspace
-// (global memory, L1/L2 resident while a warp works on its curve).
+// Per-node intermediates (arc lengths, chord lengths, the forward sweep's
+// records, M: 48 B per node) live in a caller- or handle-provided workspace
+// (global memory, L1/L2 resident while a warp works on its curve).  The chord
+// vectors and reciprocal chord lengths are recomputed where B and E need them
+// (two FP64 subtractions from the input, one Newton reciprocal) instead of
+// being stored: the workspace's latency, not the FP64 pipe, bounds the kernel.
 #include <algorithm>
 
 #include "df.cuh"
@@ -50,8 +53,6 @@ constexpr int kWarps = 4;  // curves per CTA
 struct Ws {
     double* U;     // cumulative arc length S_l = L u_l [n_pts]
     double* D;     // chord lengths d_l                 [n_pts]
-    double* IH;    // 1/d_l                             [n_pts]
-    double2* CV;   // chord vectors p_{l+1} - p_l       [n_pts]
     double2* F0;   // forward sweep (c'_l, g'_l)        [n_pts]
     double2* F1;   // forward sweep y'_l (x, y)         [n_pts]
     double2* M;    // spline second derivatives M_l     [n_pts] (stored over F1)
@@ -225,12 +226,12 @@ __device__ __forceinline__ double widen_scaled(float f, int k)
 }
 // (x.h + x.l) 2^k in FP64: one FP64 instruction
 __device__ __forceinline__ double to_d(dfl x, int k) { return widen_scaled(x.h, k) + widen_scaled(x.l, k); }
-// unit chord direction (p_{l+1} - p_l) / d_l from the chord vector and 1/d_l,
-// each scaled by 2^k and 2^-k, multiplied in float-float
-__device__ __forceinline__ cdf tau_df(double2 cv, double ih, int k)
+// unit chord direction (p_{l+1} - p_l) / d_l from the chord vector scaled by
+// 2^k and its scaled length h = d_l 2^k (1/h by a float-float Newton step)
+__device__ __forceinline__ cdf tau_dfh(double2 cv, dfl h, int k)
 {
-    const dfl s = split_scaled(ih, -k);
-    return {df_mul(split_scaled(cv.x, k), s), df_mul(split_scaled(cv.y, k), s)};
+    const dfl r = df_rcp(h);
+    return {df_mul(split_scaled(cv.x, k), r), df_mul(split_scaled(cv.y, k), r)};
 }
 __device__ __forceinline__ cdf cscale(cdf a, dfl s) { return {df_mul(a.re, s), df_mul(a.im, s)}; }
 
@@ -238,6 +239,14 @@ __device__ __forceinline__ double2 d2(double x, double y) { return make_double2(
 __device__ __forceinline__ double2 add2(double2 a, double2 b) { return d2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 sub2(double2 a, double2 b) { return d2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 scl2(double2 a, double s) { return d2(a.x * s, a.y * s); }
+// chord vector p_{l+1} - p_l of a closed curve of n nodes (the same FP64
+// subtraction as the chord pass, so the same bits); recomputed from the input
+// where it is needed instead of being kept in the workspace
+__device__ __forceinline__ double2 chord_vec(const double2* __restrict__ p, int l, int n)
+{
+    const double2 a = __ldg(p + l), b = __ldg(p + (l + 1 == n ? 0 : l + 1));
+    return d2(b.x - a.x, b.y - a.y);
+}
 
 __device__ __forceinline__ double shfl_d(double v, int src, int width)
 {
@@ -316,8 +325,6 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
 
     double* U = ws.U + o;
     double* D = ws.D + o;
-    double* IH = ws.IH + o;
-    double2* CV = ws.CV + o;
     double2* F0 = ws.F0 + o;
     double2* F1 = ws.F1 + o;
     double2* M = ws.M + o;
@@ -342,8 +349,6 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         const double dl = pos ? q * rs : 0.0;
         dmin = min(dmin, (unsigned)(__double_as_longlong(dl) >> 52) & 0x7ffu);
         D[l] = dl;
-        IH[l] = rs;
-        CV[l] = d2(dx, dy);
     }
     if (__any_sync(0xffffffffu, nf)) {
         fill_nan<F32OUT>(zout, zbase, Nout, lane);
@@ -402,24 +407,22 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     dfl gLd{0.f, 0.f}, kLd{0.f, 0.f};
     if (act && !dfsolve) {
         const double* __restrict__ Dr = D;
-        const double* __restrict__ IHr = IH;
-        const double2* __restrict__ CVr = CV;
         double* __restrict__ Ur = U;
         double2* __restrict__ F0r = F0;
         double2* __restrict__ F1r = F1;
         const int lp = (sj == 0) ? n - 1 : sj - 1;
         double hprev = Dr[lp];
-        double2 tprev = scl2(CVr[lp], IHr[lp]);
+        double2 tprev = scl2(chord_vec(p, lp, n), rcp_nr(Dr[lp]));
         double S = base;
         double cp = 0, gp = -1.0;
         double2 yp = d2(0, 0);
         double pi = 1.0;
         // operands of the next row, loaded one row ahead
-        double h = Dr[sj], ih = IHr[sj];
-        double2 cv = CVr[sj];
+        double h = Dr[sj], ih = rcp_nr(h);
+        double2 cv = chord_vec(p, sj, n);
         for (int i = sj; i < ej; ++i) {
-            const double hn = Dr[i + 1], ihn = IHr[i + 1];  // i + 1 <= ej < n
-            const double2 cvn = CVr[i + 1];
+            const double hn = Dr[i + 1], ihn = rcp_nr(hn);  // i + 1 <= ej < n
+            const double2 cvn = chord_vec(p, i + 1, n);
             Ur[i] = S;
             S += h;
             const double2 tau = scl2(cv, ih);
@@ -454,26 +457,24 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         // the same sweep in float-float (scaled units; FP64 only for the arc
         // lengths S and the conversions of the interface data below)
         const double* __restrict__ Dr = D;
-        const double* __restrict__ IHr = IH;
-        const double2* __restrict__ CVr = CV;
         double* __restrict__ Ur = U;
         float4* __restrict__ F0r = reinterpret_cast<float4*>(F0);
         float4* __restrict__ F1r = reinterpret_cast<float4*>(F1);
         const int lp = (sj == 0) ? n - 1 : sj - 1;
         dfl hprev = split_scaled(Dr[lp], ks);
-        cdf tprev = tau_df(CVr[lp], IHr[lp], ks);
+        cdf tprev = tau_dfh(chord_vec(p, lp, n), hprev, ks);
         double S = base;
         dfl cp{0.f, 0.f}, gp{-1.f, 0.f}, pi{1.f, 0.f}, gFd{0.f, 0.f};
         cdf yp{{0.f, 0.f}, {0.f, 0.f}}, yFd{{0.f, 0.f}, {0.f, 0.f}};
-        double h64 = Dr[sj], ih64 = IHr[sj];
-        double2 cv = CVr[sj];
+        double h64 = Dr[sj];
+        double2 cv = chord_vec(p, sj, n);
         for (int i = sj; i < ej; ++i) {
-            const double hn64 = Dr[i + 1], ihn64 = IHr[i + 1];  // i + 1 <= ej < n
-            const double2 cvn = CVr[i + 1];
+            const double hn64 = Dr[i + 1];  // i + 1 <= ej < n
+            const double2 cvn = chord_vec(p, i + 1, n);
             Ur[i] = S;
             S += h64;
             const dfl h = split_scaled(h64, ks);
-            const cdf tau = tau_df(cv, ih64, ks);
+            const cdf tau = tau_dfh(cv, h, ks);
             const cdf R = csub(tau, tprev);
             const dfl den = df_sub(df_twice(df_add(hprev, h)), df_mul(hprev, cp));
             const dfl r = df_rcp(den);
@@ -488,12 +489,12 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             pi = df_neg(df_mul(pi, ncp));
             cp = ncp; gp = ngp; yp = nyp;
             hprev = h; tprev = tau;
-            h64 = hn64; ih64 = ihn64; cv = cvn;
+            h64 = hn64; cv = cvn;
         }
         yLd = yp; gLd = gp; kLd = cp;
         Ur[ej] = S;
-        const cdf Red = csub(tau_df(cv, ih64, ks), tprev);
         const dfl Ced = split_scaled(h64, ks);
+        const cdf Red = csub(tau_dfh(cv, Ced, ks), tprev);
         // the interface data in FP64 for the reduced system (scaled units)
         Ae = to_d(hprev, 0);
         Ce = to_d(Ced, 0);
@@ -621,11 +622,12 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             const long long sb = __double_as_longlong(st);
             while (l + 1 < n && __double_as_longlong(U[l + 1]) <= sb) ++l;
             const int ln = (l + 1 == n) ? 0 : l + 1;
-            const double2 pl = __ldg(p + l), cv = CV[l];  // cv = p_{l+1} - p_l
+            const double2 pl = __ldg(p + l), pn = __ldg(p + ln);
+            const double2 cv = d2(pn.x - pl.x, pn.y - pl.y);  // p_{l+1} - p_l
             const double2 Ml = M[l], Mn = M[ln];
             const double d = D[l];
             const double u = st - U[l];  // arc length into the interval
-            const double b = u * IH[l];  // (t - u_l) / h_l
+            const double b = u * rcp_nr(d);  // (t - u_l) / h_l
             // cubic weights a(a^2 - 1) h6 and b(b^2 - 1) h6 (a = 1 - b, h6 =
             // h^2 M / 6 / M' = d^2 with M' = M / (6 L^2)) from
             // w = b(b - 1) h6 = -ab h6 = u (u - d): the second is w(1 + b), the
@@ -736,7 +738,7 @@ size_t resample_ws_bytes(int64_t C, int64_t n_pts, int N_out, int flags)
     constexpr int64_t kMax = (int64_t)1 << 40;
     if (C > kMax || n_pts > kMax || N_out > (1 << 20)) return SIZE_MAX;
     const size_t np = (size_t)(n_pts > 0 ? n_pts : 0);
-    size_t b = 3 * align256(np * sizeof(double)) + 3 * align256(np * sizeof(double2));
+    size_t b = 2 * align256(np * sizeof(double)) + 2 * align256(np * sizeof(double2));
     const size_t c = (size_t)(C > 0 ? C : 0);
     if (flags & FA_STORE_FP32) b += align256(c * (size_t)N_out * sizeof(double2));
     return b + 256;  // the work counter
@@ -752,8 +754,6 @@ int launch_resample(const fa_handle* h, const double* pts, const int64_t* offset
     Ws ws;
     ws.U = reinterpret_cast<double*>(b); b += align256(np * sizeof(double));
     ws.D = reinterpret_cast<double*>(b); b += align256(np * sizeof(double));
-    ws.IH = reinterpret_cast<double*>(b); b += align256(np * sizeof(double));
-    ws.CV = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.F0 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.F1 = reinterpret_cast<double2*>(b); b += align256(np * sizeof(double2));
     ws.M = ws.F1;  // M_i overwrites y'_i: step D reads each y'_i just before it writes M_i

@@ -94,7 +94,7 @@ def test_noalloc_rejects_sizes_whose_scratch_would_wrap():
 def test_noalloc_rejects_batches_beyond_its_scratch():
     L = _lib.load()
     dev = torch.device("cuda", 0)
-    n_pts = 2_000_000  # 72 bytes per node > 64 MiB; nothing is launched
+    n_pts = 2_000_000  # 48 bytes per node > 64 MiB; nothing is launched
     pts = torch.zeros(4, dtype=torch.complex128, device=dev)
     offs = torch.tensor([0, 4], dtype=torch.int64, device=dev)
     z = torch.empty((1, 256), dtype=torch.complex128, device=dev)
