@@ -12,7 +12,13 @@
 //      argmax_s |c(s)|^2 (smallest s on exact ties) -- the loop over t0 of
 //      Algorithm 2, where the per-shift Kabsch SVD collapses to |c(s)|.
 //   4. c(s*) by its O(N) sum, theta = arg c(s*), energy of Eq. disc-energy by
-//      its definition (Algorithm 1 in closed form at the winning shift).
+//      its definition (Algorithm 1 in closed form at the winning shift).  The
+//      sum for c(s*) runs in float-float (about 2^-46 of the summed
+//      magnitudes: theta far inside its 1e-10 bound, and the energy, summed
+//      in FP64 at that angle, moves only at second order in the angle's error)
+//      for pairs whose largest coordinate lies in [2^-40, 2^40], in FP64
+//      otherwise; the energy stays FP64, whose 53 bits the difference of two
+//      nearly aligned curves needs.
 //
 // The path is bound by the FP64 pipe (about 2 DFMA per clock per SM on this
 // part), so the design minimises FP64 instructions: twiddles come from a
@@ -21,6 +27,7 @@
 // their FP64 adds on one warp only.
 #include "fa_internal.cuh"
 #include "align_common.cuh"
+#include "df.cuh"
 #include "fft_stages.cuh"
 
 namespace fa {
@@ -34,6 +41,9 @@ namespace {
 #endif
 template <int T>
 constexpr int align_min_blocks() { return T <= 256 ? FA_ALIGN_MIN_BLOCKS : 1; }
+
+// biased exponent field of a double (integer instructions)
+__device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
 
 template <int LOGN, typename ZT>
 __global__ void __launch_bounds__(Geo<LOGN>::T, align_min_blocks<Geo<LOGN>::T>())
@@ -52,6 +62,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::T, align_min_blocks<Geo<LOGN>::T>()
     long long* sk = reinterpret_cast<long long*>(sums + G);  // [G*W]
     int* si = reinterpret_cast<int*>(sk + G * Gm::W);        // [G*W]
     int* bad = si + G * Gm::W;                               // [G]
+    int* emx = bad + G;  // [G] largest biased exponent of the pair's coordinates
 
     const int g = threadIdx.x / Q;
     const int t = threadIdx.x % Q;
@@ -60,20 +71,24 @@ __global__ void __launch_bounds__(Geo<LOGN>::T, align_min_blocks<Geo<LOGN>::T>()
     const ZT* p1 = z1 + (valid ? pair : 0) * N;
     const ZT* p2 = z2 + (valid ? pair : 0) * N;
 
-    if (t == 0) bad[g] = 0;
+    if (t == 0) { bad[g] = 0; emx[g] = 0; }
     __syncthreads();
     bool nf = false;
+    int ex = 0;
     double2 a[4], b[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         a[r] = valid ? ld_z(p1, t + r * Q) : make_double2(0.0, 0.0);
         b[r] = valid ? ld_z(p2, t + r * Q) : make_double2(0.0, 0.0);
         nf |= !finite2(a[r]) || !finite2(b[r]);
+        ex = max(ex, max(max(bexp(a[r].x), bexp(a[r].y)), max(bexp(b[r].x), bexp(b[r].y))));
         X1[t + r * Q] = a[r];
         X2[t + r * Q] = b[r];
     }
     if (nf) bad[g] = 1;
+    atomicMax(&emx[g], ex);
     __syncthreads();
+    const bool dfc = emx[g] > 1023 - 40 && emx[g] < 1023 + 40;  // the same for the whole group
 
     fft_two<LOGN>(X1, X2, t, W);
     double2 y[4];
@@ -94,10 +109,22 @@ __global__ void __launch_bounds__(Geo<LOGN>::T, align_min_blocks<Geo<LOGN>::T>()
     // c(s*) by its O(N) definition (inputs re-read from L1/L2)
     double2 c = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        b[r] = valid ? ld_z(p2, (t + r * Q + sbest) & (N - 1)) : make_double2(0.0, 0.0);
-        c.x = fma(a[r].x, b[r].x, fma(a[r].y, b[r].y, c.x));
-        c.y = fma(a[r].y, b[r].x, fma(-a[r].x, b[r].y, c.y));
+    for (int r = 0; r < 4; ++r) b[r] = valid ? ld_z(p2, (t + r * Q + sbest) & (N - 1)) : make_double2(0.0, 0.0);
+    if (dfc) {
+        cdf cd{{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const cdf u = split_c(a[r]), v = split_c(b[r]);
+            cd.re = df_add(cd.re, df_dot2<+1>(u.re, v.re, u.im, v.im));
+            cd.im = df_add(cd.im, df_dot2<-1>(u.im, v.re, u.re, v.im));
+        }
+        c = make_double2(df_to_double(cd.re), df_to_double(cd.im));
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            c.x = fma(a[r].x, b[r].x, fma(a[r].y, b[r].y, c.x));
+            c.y = fma(a[r].y, b[r].x, fma(-a[r].x, b[r].y, c.y));
+        }
     }
     __syncthreads();  // the last stage's shared-memory reads are done: X1 is free
     group_sum<Q>(c, X1, sums, g, t);
@@ -142,7 +169,7 @@ int launch_one(const fa_handle* h, const void* z1, const void* z2, int64_t P, in
     using Gm = Geo<LOGN>;
     const size_t smem = (size_t)Gm::G * 2 * Gm::N * sizeof(double2) + 2 * Gm::G * sizeof(double2) +
                         (size_t)Gm::G * Gm::W * (sizeof(long long) + sizeof(int)) +
-                        Gm::G * sizeof(int);
+                        2 * Gm::G * sizeof(int);
     auto kern = align_fft_kernel<LOGN, ZT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

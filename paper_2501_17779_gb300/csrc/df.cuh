@@ -82,6 +82,20 @@ __device__ __forceinline__ dfl df_rcp(dfl x)
     return fast_two_sum(r0, __fmul_rn(r0, e));
 }
 
+// float -> double from the bits (zero and subnormal floats give 0): no FP64
+// conversion instruction
+__device__ __forceinline__ double df_widen(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned ef = (u >> 23) & 0xff;
+    if (ef == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(ef - 127 + 1023) << 52) |
+                                            ((unsigned long long)(u & 0x7fffff) << 29)));
+}
+// h + l in FP64 (one FP64 add)
+__device__ __forceinline__ double df_to_double(dfl x) { return df_widen(x.h) + df_widen(x.l); }
+
 __device__ __forceinline__ dfl df_neg(dfl x) { return {-x.h, -x.l}; }
 __device__ __forceinline__ dfl df_twice(dfl x) { return {__fmul_rn(2.0f, x.h), __fmul_rn(2.0f, x.l)}; }
 
