@@ -39,7 +39,9 @@
 // (cp.async.bulk, completion on an mbarrier) the pre-tiled DFT blocks as far
 // ahead as the stages allow; warps 8-11 read the
 // finished accumulators and keep each pair's best 8 shifts, while the MMAs of
-// the next column block run into the other accumulator.  All waits are
+// the next column block run into the other accumulator.  The epilogue warps run
+// their own tile loop (the others synchronise per tile on a named barrier), so
+// the last column block of a tile is read while the next tile's MMAs start.  All waits are
 // bounded; a wait that runs out sets an error flag that turns every output of
 // the call into NaN.
 #include <cuda_bf16.h>
@@ -264,9 +266,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint64_t* mma_done = a_full + kStages;                                             // [kStages]
     uint64_t* acc_full = mma_done + kStages;                                           // [2]
     uint64_t* tmem_empty = acc_full + 2;                                               // [2]
-    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(tmem_empty + 2);
+    uint64_t* tinfo = tmem_empty + 2;                                                  // [2]
+    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(tinfo + 2);
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_taddr + 1);
-    long long* s_tile = reinterpret_cast<long long*>(s_taddr + 2);
+    volatile long long* s_tile = reinterpret_cast<volatile long long*>(s_taddr + 2);
+    volatile long long* s_tring = s_tile + 1;                                          // [2]
+    float* escr = reinterpret_cast<float*>(const_cast<long long*>(s_tring + 2));      // [4][32][33]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int prow = tid / LPR, sub = tid % LPR;  // producers: row in a pass, frequency pair
 
@@ -279,6 +284,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int b = 0; b < 2; ++b) {
             umma::mbar_init(&acc_full[b], 1);
             umma::mbar_init(&tmem_empty[b], kTcT);
+            umma::mbar_init(&tinfo[b], 1);
         }
         *s_abort = 0;
         umma::fence_mbar_init();
@@ -296,103 +302,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         atomicExch(err, 1);
     };
 
-    for (;;) {
-        if (tid == 0) *s_tile = (long long)atomicAdd(next, 1ull);
-        __syncthreads();
-        const int64_t t = *s_tile;
-        if (t >= total_tiles || *s_abort) break;
-        // tile -> (i, j-tile): largest i with tiles_before(i) <= t
-        int64_t lo = 0, hi = M - 2;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (ceil_sum128(M - 1) - ceil_sum128(M - 1 - mid) <= t) lo = mid; else hi = mid - 1;
-        }
-        const int64_t i = lo;
-        const int64_t j0 = i + 1 + 128 * (t - (ceil_sum128(M - 1) - ceil_sum128(M - 1 - i)));
-        if (warp < kEpiWarp0)
-            for (int k = tid; k < N; k += kTcProducers) {
-                // curve i's spectrum times the cross-spectrum scale (a power of
-                // two: the products below round exactly as if scaled after)
-                const float2 v = spec[i * N + k];
-                zi_s[k] = make_float2(v.x * kPScale, v.y * kPScale);
+    if (warp >= kEpiWarp0 && warp < kIssuerWarp) {
+        // ---- epilogue warps: their own tile loop, one tile behind at most.
+        // The tile comes through a two-slot ring (tinfo: one arrival per tile
+        // from thread 0); the issuer cannot run more than two column blocks
+        // ahead of this loop (it waits for tmem_empty), so a slot is never
+        // rewritten before it is read.
+        float* xs = escr + (size_t)(warp - kEpiWarp0) * 32 * 33 + lane * 33;
+        for (int64_t tau = 0;; ++tau) {
+            if (!umma::mbar_wait(&tinfo[tau & 1], (uint32_t)(tau >> 1) & 1)) { fail(); break; }
+            const int64_t t = s_tring[tau & 1];
+            if (t >= total_tiles) break;
+            // tile -> (i, j-tile): largest i with tiles_before(i) <= t
+            int64_t lo = 0, hi = M - 2;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (ceil_sum128(M - 1) - ceil_sum128(M - 1 - mid) <= t) lo = mid; else hi = mid - 1;
             }
-        __syncthreads();
-
-        if (warp < kEpiWarp0) {
-            // ---- producers ----
-            // Operand rows are formed LPR lanes per pair, two frequencies per
-            // lane (one 16-byte load), so that a warp's load covers LPR * 16
-            // contiguous bytes of each of 32 / LPR rows; pass q handles rows
-            // q RPP + tid / LPR.
-            const float4* zrow[NPASS];
-#pragma unroll
-            for (int q = 0; q < NPASS; ++q) {
-                const int64_t j = j0 + q * RPP + prow;
-                zrow[q] = reinterpret_cast<const float4*>(spec + (j < M ? j : i) * N) + sub;
-            }
-            // this thread's spectrum values of the next two chunks
-            float4 zb[NPASS], zb2[NPASS];
-#pragma unroll
-            for (int q = 0; q < NPASS; ++q) {
-                zb[q] = zrow[q][0];
-                zb2[q] = zrow[q][(1 % NK) * (KF / 2)];
-            }
-            const float4* zi4 = reinterpret_cast<const float4*>(zi_s) + sub;
-            // this thread's byte offsets in an operand stage, one per pass
-            uint32_t soff[NPASS];
-#pragma unroll
-            for (int q = 0; q < NPASS; ++q) soff[q] = umma::tile_off(q * RPP + prow, sub * 4 * T::ES, kRowB);
-            // One K chunk: wait for its stage, form and store this thread's
-            // operand pieces from zbuf, signal, then load the chunk two ahead
-            // into zbuf (K chunks wrap to the first ones for the next column
-            // block).  The loads come after the proxy fence, which would
-            // otherwise wait for them.
-            auto produce = [&](int kc, float4 (&zbuf)[NPASS]) -> bool {
-                const int st = (int)(g % kStages);
-                const uint32_t use = (uint32_t)(g / kStages);
-                uint8_t* sa = smem + st * STAGE;
-                if (*s_abort) return false;
-                if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) { fail(); return false; }
-                // frequencies kc KF + 2 sub, + 1 of curve i (pre-scaled)
-                const float4 a = zi4[kc * (KF / 2)];
-#pragma unroll
-                for (int q = 0; q < NPASS; ++q) {
-                    const float4 b = zbuf[q];
-                    const float v0 = __fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y));
-                    const float v1 = __fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y));
-                    const float v2 = __fmaf_rn(a.z, b.z, __fmul_rn(a.w, b.w));
-                    const float v3 = __fmaf_rn(a.w, b.z, -__fmul_rn(a.z, b.w));
-                    if constexpr (T::ES == 2) {
-                        uint32_t h01, l01, h23, l23;
-                        to_pieces2<V>(v0, v1, h01, l01);
-                        to_pieces2<V>(v2, v3, h23, l23);
-                        *reinterpret_cast<uint2*>(sa + soff[q]) = make_uint2(h01, h23);
-                        *reinterpret_cast<uint2*>(sa + A_PIECE + soff[q]) = make_uint2(l01, l23);
-                    } else {
-                        uint32_t ph[4], pl[4];
-                        to_pieces<V>(v0, ph[0], pl[0]);
-                        to_pieces<V>(v1, ph[1], pl[1]);
-                        to_pieces<V>(v2, ph[2], pl[2]);
-                        to_pieces<V>(v3, ph[3], pl[3]);
-                        *reinterpret_cast<uint4*>(sa + soff[q]) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                        if (T::NP > 1)
-                            *reinterpret_cast<uint4*>(sa + A_PIECE + soff[q]) =
-                                make_uint4(pl[0], pl[1], pl[2], pl[3]);
-                    }
-                }
-                umma::fence_async_smem();
-                umma::mbar_arrive(&a_full[st]);
-                const int fn = ((kc + 2) % NK) * (KF / 2);
-#pragma unroll
-                for (int q = 0; q < NPASS; ++q) zbuf[q] = zrow[q][fn];
-                ++g;
-                return true;
-            };
-            // two chunks per trip: the buffers trade roles without copies
-            bool ok = true;
-            for (int cb = 0; cb < NCB && ok; ++cb)
-                for (int kc = 0; kc < NK && ok; kc += 2) ok = produce(kc, zb) && produce(kc + 1, zb2);
-        } else if (warp < kIssuerWarp) {
+            const int64_t i = lo;
+            const int64_t j0 = i + 1 + 128 * (t - (ceil_sum128(M - 1) - ceil_sum128(M - 1 - i)));
             // ---- epilogue: TMEM lane = pair row ----
             const int row = (warp - kEpiWarp0) * 32 + lane;
             float best[kCand];
@@ -423,22 +351,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     top = m;
                     const float thr = fmaxf(best[kCand - 1], __fmul_rn(top, 1.0f - T::MARGIN));
+                    // the values that may enter, staged in this lane's row of
+                    // shared memory and inserted in shift order: the warp
+                    // iterates as often as its busiest lane, not once per
+                    // value some lane needs
+                    unsigned msk = 0u;
 #pragma unroll
                     for (int q = 0; q < 32; ++q) {
-                        float x = re[q];
-                        if (x > best[kCand - 1] && x >= thr) {
-                            int sx = cb * 128 + c0 + q;
+                        xs[q] = re[q];
+                        msk |= (re[q] > best[kCand - 1] && re[q] >= thr) ? (1u << q) : 0u;
+                    }
+                    while (msk) {
+                        const int q = __ffs(msk) - 1;
+                        msk &= msk - 1;
+                        float x = xs[q];
+                        int sx = cb * 128 + c0 + q;
 #pragma unroll
-                            for (int r = 0; r < kCand; ++r) {
-                                if (x > best[r]) {
-                                    const float tv = best[r];
-                                    const int ts = bs[r];
-                                    best[r] = x; bs[r] = sx;
-                                    x = tv; sx = ts;
-                                }
+                        for (int r = 0; r < kCand; ++r) {
+                            if (x > best[r]) {
+                                const float tv = best[r];
+                                const int ts = bs[r];
+                                best[r] = x; bs[r] = sx;
+                                x = tv; sx = ts;
                             }
                         }
                     }
+                    __syncwarp();  // converged again for the next tcgen05.ld
                 }
                 umma::tc_fence_before();
                 umma::mbar_arrive(&tmem_empty[buf]);
@@ -460,60 +398,170 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 w.w = (uint32_t)bs[6] | ((uint32_t)bs[7] << 16);
                 *reinterpret_cast<uint4*>(cand + ((size_t)i * M + j) * kCand) = w;
             }
-        } else if (warp == kIssuerWarp && lane == 0) {
-            // ---- the MMA issuer: chunk c as soon as its operands are in.
-            // Chunk c of the tile is column block c / NK, K chunk c % NK.
-            constexpr int NC = NCB * NK;
-            for (int c = 0; c < NC && !*s_abort; ++c, ++g) {
-                const int kc = c % NK;
-                const int buf = (int)(cbg & 1);
-                const int st = (int)(g % kStages);
-                const uint32_t use = (uint32_t)(g / kStages);
-                if (kc == 0 && cbg >= 2 &&
-                    !umma::mbar_wait(&tmem_empty[buf], (uint32_t)((cbg >> 1) - 1) & 1)) {
-                    fail();
-                    break;
+            if (!ok) break;
+        }
+    } else {
+        // ---- producers, MMA issuer and copier: tiles from the counter,
+        // synchronised among themselves by a named barrier (the epilogue warps
+        // keep their own pace); thread 0 alone decides when to stop, so that
+        // every one of these warps leaves the loop together
+        constexpr unsigned kMain = kTcThreads - 32 * (kIssuerWarp - kEpiWarp0);
+        auto main_sync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(kMain) : "memory"); };
+        for (int64_t tau = 0;; ++tau) {
+            if (tid == 0) {
+                const long long tt = *s_abort ? (long long)total_tiles : (long long)atomicAdd(next, 1ull);
+                *s_tile = tt;
+                s_tring[tau & 1] = tt;
+                umma::mbar_arrive(&tinfo[tau & 1]);
+            }
+            main_sync();
+            const int64_t t = *s_tile;
+            if (t >= total_tiles) break;
+            // tile -> (i, j-tile): largest i with tiles_before(i) <= t
+            int64_t lo = 0, hi = M - 2;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (ceil_sum128(M - 1) - ceil_sum128(M - 1 - mid) <= t) lo = mid; else hi = mid - 1;
+            }
+            const int64_t i = lo;
+            const int64_t j0 = i + 1 + 128 * (t - (ceil_sum128(M - 1) - ceil_sum128(M - 1 - i)));
+            if (warp < kEpiWarp0)
+                for (int k = tid; k < N; k += kTcProducers) {
+                    // curve i's spectrum times the cross-spectrum scale (a power of
+                    // two: the products below round exactly as if scaled after)
+                    const float2 v = spec[i * N + k];
+                    zi_s[k] = make_float2(v.x * kPScale, v.y * kPScale);
                 }
-                if (!umma::mbar_wait(&b_full[st], use & 1) || !umma::mbar_wait(&a_full[st], use & 1)) {
-                    fail();
-                    break;
+            main_sync();
+            if (warp < kEpiWarp0) {
+                // ---- producers ----
+                // Operand rows are formed LPR lanes per pair, two frequencies per
+                // lane (one 16-byte load), so that a warp's load covers LPR * 16
+                // contiguous bytes of each of 32 / LPR rows; pass q handles rows
+                // q RPP + tid / LPR.
+                const float4* zrow[NPASS];
+#pragma unroll
+                for (int q = 0; q < NPASS; ++q) {
+                    const int64_t j = j0 + q * RPP + prow;
+                    zrow[q] = reinterpret_cast<const float4*>(spec + (j < M ? j : i) * N) + sub;
                 }
-                umma::tc_fence_after();
-                const uint32_t a0 = umma::smem_u32(smem + st * STAGE);
-                const uint32_t b0 = a0 + (uint32_t)(A_PIECE * T::NP);
-                constexpr int PA[3] = {0, 0, 1}, PB[3] = {0, 1, 0};
+                // this thread's spectrum values of the next two chunks
+                float4 zb[NPASS], zb2[NPASS];
 #pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
+                for (int q = 0; q < NPASS; ++q) {
+                    zb[q] = zrow[q][0];
+                    zb2[q] = zrow[q][(1 % NK) * (KF / 2)];
+                }
+                const float4* zi4 = reinterpret_cast<const float4*>(zi_s) + sub;
+                // this thread's byte offsets in an operand stage, one per pass
+                uint32_t soff[NPASS];
 #pragma unroll
-                    for (int tt = 0; tt < NT; ++tt) {
-                        const uint64_t ad = umma::sdesc(a0 + (uint32_t)(PA[tt] * A_PIECE) + ks * 256,
-                                                        128, kRowB * 8);
-                        const uint64_t bd = umma::sdesc(b0 + (uint32_t)(PB[tt] * B_PIECE) + ks * 256,
-                                                        128, kRowB * 8);
-                        const uint32_t acc = (kc > 0 || ks > 0 || tt > 0) ? 1u : 0u;
-                        if constexpr (T::TF32) umma::mma_tf32(tmem + buf * 256, ad, bd, ID, acc);
-                        else umma::mma_f16(tmem + buf * 256, ad, bd, ID, acc);
+                for (int q = 0; q < NPASS; ++q) soff[q] = umma::tile_off(q * RPP + prow, sub * 4 * T::ES, kRowB);
+                // One K chunk: wait for its stage, form and store this thread's
+                // operand pieces from zbuf, signal, then load the chunk two ahead
+                // into zbuf (K chunks wrap to the first ones for the next column
+                // block).  The loads come after the proxy fence, which would
+                // otherwise wait for them.
+                auto produce = [&](int kc, float4 (&zbuf)[NPASS]) -> bool {
+                    const int st = (int)(g % kStages);
+                    const uint32_t use = (uint32_t)(g / kStages);
+                    uint8_t* sa = smem + st * STAGE;
+                    if (*s_abort) return false;
+                    if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) { fail(); return false; }
+                    // frequencies kc KF + 2 sub, + 1 of curve i (pre-scaled)
+                    const float4 a = zi4[kc * (KF / 2)];
+#pragma unroll
+                    for (int q = 0; q < NPASS; ++q) {
+                        const float4 b = zbuf[q];
+                        const float v0 = __fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y));
+                        const float v1 = __fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y));
+                        const float v2 = __fmaf_rn(a.z, b.z, __fmul_rn(a.w, b.w));
+                        const float v3 = __fmaf_rn(a.w, b.z, -__fmul_rn(a.z, b.w));
+                        if constexpr (T::ES == 2) {
+                            uint32_t h01, l01, h23, l23;
+                            to_pieces2<V>(v0, v1, h01, l01);
+                            to_pieces2<V>(v2, v3, h23, l23);
+                            *reinterpret_cast<uint2*>(sa + soff[q]) = make_uint2(h01, h23);
+                            *reinterpret_cast<uint2*>(sa + A_PIECE + soff[q]) = make_uint2(l01, l23);
+                        } else {
+                            uint32_t ph[4], pl[4];
+                            to_pieces<V>(v0, ph[0], pl[0]);
+                            to_pieces<V>(v1, ph[1], pl[1]);
+                            to_pieces<V>(v2, ph[2], pl[2]);
+                            to_pieces<V>(v3, ph[3], pl[3]);
+                            *reinterpret_cast<uint4*>(sa + soff[q]) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                            if (T::NP > 1)
+                                *reinterpret_cast<uint4*>(sa + A_PIECE + soff[q]) =
+                                    make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                        }
+                    }
+                    umma::fence_async_smem();
+                    umma::mbar_arrive(&a_full[st]);
+                    const int fn = ((kc + 2) % NK) * (KF / 2);
+#pragma unroll
+                    for (int q = 0; q < NPASS; ++q) zbuf[q] = zrow[q][fn];
+                    ++g;
+                    return true;
+                };
+                // two chunks per trip: the buffers trade roles without copies
+                bool ok = true;
+                for (int cb = 0; cb < NCB && ok; ++cb)
+                    for (int kc = 0; kc < NK && ok; kc += 2) ok = produce(kc, zb) && produce(kc + 1, zb2);
+            } else if (warp == kIssuerWarp && lane == 0) {
+                // ---- the MMA issuer: chunk c as soon as its operands are in.
+                // Chunk c of the tile is column block c / NK, K chunk c % NK.
+                constexpr int NC = NCB * NK;
+                for (int c = 0; c < NC && !*s_abort; ++c, ++g) {
+                    const int kc = c % NK;
+                    const int buf = (int)(cbg & 1);
+                    const int st = (int)(g % kStages);
+                    const uint32_t use = (uint32_t)(g / kStages);
+                    if (kc == 0 && cbg >= 2 &&
+                        !umma::mbar_wait(&tmem_empty[buf], (uint32_t)((cbg >> 1) - 1) & 1)) {
+                        fail();
+                        break;
+                    }
+                    if (!umma::mbar_wait(&b_full[st], use & 1) || !umma::mbar_wait(&a_full[st], use & 1)) {
+                        fail();
+                        break;
+                    }
+                    umma::tc_fence_after();
+                    const uint32_t a0 = umma::smem_u32(smem + st * STAGE);
+                    const uint32_t b0 = a0 + (uint32_t)(A_PIECE * T::NP);
+                    constexpr int PA[3] = {0, 0, 1}, PB[3] = {0, 1, 0};
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+                        for (int tt = 0; tt < NT; ++tt) {
+                            const uint64_t ad = umma::sdesc(a0 + (uint32_t)(PA[tt] * A_PIECE) + ks * 256,
+                                                            128, kRowB * 8);
+                            const uint64_t bd = umma::sdesc(b0 + (uint32_t)(PB[tt] * B_PIECE) + ks * 256,
+                                                            128, kRowB * 8);
+                            const uint32_t acc = (kc > 0 || ks > 0 || tt > 0) ? 1u : 0u;
+                            if constexpr (T::TF32) umma::mma_tf32(tmem + buf * 256, ad, bd, ID, acc);
+                            else umma::mma_f16(tmem + buf * 256, ad, bd, ID, acc);
+                        }
+                    }
+                    umma::mma_commit(&mma_done[st]);
+                    if (kc == NK - 1) {
+                        umma::mma_commit(&acc_full[buf]);
+                        ++cbg;
                     }
                 }
-                umma::mma_commit(&mma_done[st]);
-                if (kc == NK - 1) {
-                    umma::mma_commit(&acc_full[buf]);
-                    ++cbg;
+            } else if (warp == kCopyWarp && lane == 0) {
+                // ---- the DFT-block copier: block c (= chunk c of the tile) into
+                // the stage of chunk c as soon as the MMAs of chunk c - kStages are
+                // done with it, so copies run up to kStages chunks ahead
+                constexpr int NC = NCB * NK;
+                for (int c = 0; c < NC && !*s_abort; ++c, ++g) {
+                    const int st = (int)(g % kStages);
+                    const uint32_t use = (uint32_t)(g / kStages);
+                    if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) { fail(); break; }
+                    mbar_expect_tx(&b_full[st], B_BYTES);
+                    bulk_g2s(smem + st * STAGE + A_PIECE * T::NP, tab + (size_t)c * B_BYTES, B_BYTES,
+                             &b_full[st]);
+                    ++copied;
                 }
-            }
-        } else if (warp == kCopyWarp && lane == 0) {
-            // ---- the DFT-block copier: block c (= chunk c of the tile) into
-            // the stage of chunk c as soon as the MMAs of chunk c - kStages are
-            // done with it, so copies run up to kStages chunks ahead
-            constexpr int NC = NCB * NK;
-            for (int c = 0; c < NC && !*s_abort; ++c, ++g) {
-                const int st = (int)(g % kStages);
-                const uint32_t use = (uint32_t)(g / kStages);
-                if (use > 0 && !umma::mbar_wait(&mma_done[st], (use - 1) & 1)) { fail(); break; }
-                mbar_expect_tx(&b_full[st], B_BYTES);
-                bulk_g2s(smem + st * STAGE + A_PIECE * T::NP, tab + (size_t)c * B_BYTES, B_BYTES,
-                         &b_full[st]);
-                ++copied;
             }
         }
     }
@@ -798,7 +846,8 @@ int launch_tc(const fa_handle* h, const void* z, int64_t M, void* ws, int8_t* st
     rc = cuda_error(cudaGetLastError(), "all-pairs tc: setup launch");
     if (rc != FA_OK) return rc;
     constexpr size_t STAGE = (size_t)(128 + 256) * kRowB * T::NP;
-    const size_t smem = kStages * STAGE + (size_t)N * 8 + (3 * kStages + 4) * 8 + 32;
+    const size_t smem = kStages * STAGE + (size_t)N * 8 + (3 * kStages + 6) * 8 + 48 +
+                        (size_t)4 * 32 * 33 * sizeof(float);
     auto kern = tc_search_kernel<V, LOGN>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "all-pairs tc: cudaFuncSetAttribute");
