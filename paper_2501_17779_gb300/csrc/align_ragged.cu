@@ -92,26 +92,33 @@ __global__ void ragged_order_kernel(const int64_t* __restrict__ off, int64_t P, 
 
 // y_q[t] = W_L^{qt} sum_{r<R} x[t + rB] W_R^{qr} into X, where x is the padded
 // sequence of one curve: x[k] = z[k] for k < n (KIND 0), or z[k mod n] for
-// k < 2n (KIND 1, the periodic extension), zero beyond.
+// k < 2n (KIND 1, the periodic extension), zero beyond.  Only the nonzero
+// inputs are added (terms r < ceil(lim / B), and within them k < lim: both
+// conditions are uniform over all but one warp), and y_q[t] = 0 for t >= lim
+// skips the twiddle.
 template <int T, int KIND, typename ZT>
 __device__ void load_dif(double2* X, const ZT* __restrict__ z, int n, int L, int B, int R, int q,
                          const double2* __restrict__ WL, int tl)
 {
     const int lim = (KIND == 0) ? n : 2 * n;
+    const int rmax = min(R, (lim + B - 1) / B);
     for (int t = tl; t < B; t += T) {
         double2 acc = make_double2(0.0, 0.0);
-        for (int r = 0; r < R; ++r) {
-            const int k = t + r * B;
-            double2 x = make_double2(0.0, 0.0);
-            if (k < lim) x = ld_z(z, (KIND == 0 || k < n) ? k : k - n);
-            // times W_R^{qr} = (-i)^{4qr/R}, R in {1, 2, 4}
-            const int e = (q * r * (4 / R)) & 3;  // power of -i
-            if (e == 0) { acc.x += x.x; acc.y += x.y; }
-            else if (e == 1) { acc.x += x.y; acc.y -= x.x; }
-            else if (e == 2) { acc.x -= x.x; acc.y -= x.y; }
-            else { acc.x -= x.y; acc.y += x.x; }
+        if (t < lim) {
+            acc = ld_z(z, (KIND == 0 || t < n) ? t : t - n);
+            for (int r = 1; r < rmax; ++r) {
+                const int k = t + r * B;
+                if (k >= lim) break;
+                const double2 x = ld_z(z, (KIND == 0 || k < n) ? k : k - n);
+                // times W_R^{qr} = (-i)^{4qr/R}, R in {2, 4}
+                const int e = (q * r * (4 / R)) & 3;  // power of -i
+                if (e == 0) { acc.x += x.x; acc.y += x.y; }
+                else if (e == 1) { acc.x += x.y; acc.y -= x.x; }
+                else if (e == 2) { acc.x -= x.x; acc.y -= x.y; }
+                else { acc.x -= x.y; acc.y += x.x; }
+            }
+            if (q > 0) acc = cmul(acc, __ldg(WL + q * t));
         }
-        if (q > 0) acc = cmul(acc, __ldg(WL + q * t));
         X[t] = acc;
     }
 }
@@ -275,21 +282,39 @@ __global__ void __launch_bounds__(T)
                     for (int m = tl; m < B; m += T) Fs[q * B + m] = X[m];
                 __syncthreads();
             }
-            // L c(s) = sum_q W_L^{qs} F_q[s mod B] for s < n; F_{R-1} is still in X
-            for (int s = tl; s < nn; s += T) {
-                const int sm = s & (B - 1);
-                double2 c = X[sm];
-                if (R > 1) {
-                    c = cmul(c, __ldg(WL + (((R - 1) * s) & (L - 1))));
-                    for (int q = 0; q < R - 1; ++q) {
-                        double2 f = Fs[q * B + sm];
-                        if (q > 0) f = cmul(f, __ldg(WL + ((q * s) & (L - 1))));
-                        c.x += f.x;
-                        c.y += f.y;
-                    }
-                }
+            // L c(s) = sum_q W_L^{qs} F_q[s mod B] for s < n (F_{R-1} is still
+            // in X), as the matching radix-R decimation-in-time step: for m < B,
+            // G_q = W_L^{qm} F_q[m] and L c(m + jB) = sum_q W_R^{qj} G_q, only
+            // for the j with m + jB < n
+            auto take = [&](double2 c, int s) {
                 const long long kq = __double_as_longlong(fma(c.x, c.x, c.y * c.y));
                 if (key_better(kq, s, key, idx)) { key = kq; idx = s; }
+            };
+            const int mlim = min(B, nn);
+            if (R == 1) {
+                for (int s = tl; s < nn; s += T) take(X[s], s);
+            } else if (R == 2) {
+                for (int m = tl; m < mlim; m += T) {
+                    const double2 g0 = Fs[m], g1 = cmul(X[m], __ldg(WL + m));
+                    take(make_double2(g0.x + g1.x, g0.y + g1.y), m);
+                    if (m + B < nn) take(make_double2(g0.x - g1.x, g0.y - g1.y), m + B);
+                }
+            } else {
+                for (int m = tl; m < mlim; m += T) {
+                    const double2 g0 = Fs[m];
+                    const double2 g1 = cmul(Fs[B + m], __ldg(WL + m));
+                    const double2 g2 = cmul(Fs[2 * B + m], __ldg(WL + 2 * m));
+                    const double2 g3 = cmul(X[m], __ldg(WL + 3 * m));
+                    const double2 a0 = make_double2(g0.x + g2.x, g0.y + g2.y);
+                    const double2 a1 = make_double2(g0.x - g2.x, g0.y - g2.y);
+                    const double2 b0 = make_double2(g1.x + g3.x, g1.y + g3.y);
+                    const double2 b1 = make_double2(g1.x - g3.x, g1.y - g3.y);
+                    // W_4^{qj} = (-i)^{qj}: j = 0: a0 + b0; 1: a1 - i b1; 2: a0 - b0; 3: a1 + i b1
+                    take(make_double2(a0.x + b0.x, a0.y + b0.y), m);
+                    if (m + B < nn) take(make_double2(a1.x + b1.y, a1.y - b1.x), m + B);
+                    if (m + 2 * B < nn) take(make_double2(a0.x - b0.x, a0.y - b0.y), m + 2 * B);
+                    if (m + 3 * B < nn) take(make_double2(a1.x - b1.y, a1.y + b1.x), m + 3 * B);
+                }
             }
         } else {
             // both spectra of each pair in shared memory (L <= BMAX / (2G))
