@@ -22,10 +22,15 @@
 //      tridiagonal system in the P interface values, solved by parallel
 //      cyclic reduction with warp shuffles.
 //   D. a backward sweep writes M for every node.
-//   E. the spline is evaluated at t_k = k/N_out (each lane a contiguous block
-//      of outputs; interval search by integer compares on the knots; the
-//      closed-polygon perimeter of the outputs is summed in the same loop),
-//      then the outputs are centred at their mean and divided by it.
+//   E. the spline is evaluated at t_k = k/N_out, then the outputs are centred
+//      at their mean and divided by the closed-polygon perimeter of the
+//      outputs (both summed in the same loop).  For N_out <= 1024 the
+//      interval of every output comes from a per-warp table in shared memory:
+//      B counts each knot S_l at the first output whose target reaches it,
+//      a prefix sum turns the counts into intervals, and 32 consecutive
+//      outputs are evaluated at a time (coalesced stores, independent loads).
+//      Larger N_out: each lane a contiguous block of outputs, its intervals
+//      by bisection and stepping over the knots.
 // Per-node intermediates (arc lengths, chord lengths, the forward sweep's
 // records, M: 48 B per node) live in a caller- or handle-provided workspace
 // (global memory, L1/L2 resident while a warp works on its curve).  The chord
@@ -248,6 +253,44 @@ __device__ __forceinline__ double2 chord_vec(const double2* __restrict__ p, int 
     return d2(b.x - a.x, b.y - a.y);
 }
 
+// arc-length target L t_k of output k (t_k = k / N_out); (double)k from the
+// exact float of k < 2^20 by bits (no FP64 conversion)
+__device__ __forceinline__ double arc_target(int k, bool pow2, double LN, double L, int Nout)
+{
+    const double kd = k > 0 ? widen_f32(__int2float_rn(k)) : 0.0;
+    return pow2 ? kd * LN : L * (kd / (double)Nout);
+}
+
+// the spline on interval l (knots S_l <= st < S_{l+1}) at arc length st
+__device__ __forceinline__ double2 eval_interval(const double2* __restrict__ p,
+                                                 const double* U, const double* D,
+                                                 const double2* M, int l, int n, double st)
+{
+    const int ln = (l + 1 == n) ? 0 : l + 1;
+    const double2 pl = __ldg(p + l), pn = __ldg(p + ln);
+    const double2 cv = d2(pn.x - pl.x, pn.y - pl.y);  // p_{l+1} - p_l
+    const double2 Ml = M[l], Mn = M[ln];
+    const double d = D[l];
+    const double u = st - U[l];      // arc length into the interval
+    const double b = u * rcp_nr(d);  // (t - u_l) / h_l
+    // cubic weights a(a^2 - 1) h6 and b(b^2 - 1) h6 (a = 1 - b, h6 =
+    // h^2 M / 6 / M' = d^2 with M' = M / (6 L^2)) from
+    // w = b(b - 1) h6 = -ab h6 = u (u - d): the second is w(1 + b), the
+    // first w(2 - b) = 3w - w(1 + b)  (4 FP64 instructions instead of 8)
+    const double w = u * (u - d);
+    const double cb = fma(w, b, w);
+    const double ca = fma(w, 3.0, -cb);
+    return d2(fma(ca, Ml.x, fma(cb, Mn.x, fma(b, cv.x, pl.x))),
+              fma(ca, Ml.y, fma(cb, Mn.y, fma(b, cv.y, pl.y))));
+}
+
+// Output counts of up to kEvalCap outputs per warp in shared memory, one
+// padding word per 32 so that a lane walking its own block of 32 consecutive
+// entries hits a bank of its own.
+constexpr int kEvalCap = 1024;
+constexpr int kCntStride = kEvalCap + kEvalCap / 32;
+__device__ __forceinline__ int pidx(int k) { return k + (k >> 5); }
+
 __device__ __forceinline__ double shfl_d(double v, int src, int width)
 {
     return __shfl_sync(0xffffffffu, v, src, width);
@@ -280,7 +323,8 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
                                                const int64_t* __restrict__ offsets,
                                                int64_t n_pts, int Nout, int flags,
                                                void* __restrict__ zout,
-                                               int8_t* __restrict__ status, const Ws& ws)
+                                               int8_t* __restrict__ status, const Ws& ws,
+                                               int* __restrict__ cnt)
 {
     const int64_t o = offsets[curve];
     const int64_t o1 = offsets[curve + 1];
@@ -386,6 +430,56 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     const bool dfsolve = eLb > 1023 - 800 && eLb < 1023 + 800 && eLb - dminw < 100;
     const int ks = 1023 - eLb;
 
+    // ---- output-interval counts (taken in B, used by E) ----------------------
+    // For N_out <= kEvalCap each knot S_l is counted at kf(l), the first output
+    // k with L t_k >= S_l (none when kf = N_out); the prefix sums of the counts
+    // give, for every output, the number of knots at or below its target, so
+    // E reads each output's interval from the table instead of searching.
+    const bool pow2 = (Nout & (Nout - 1)) == 0;
+    const double invN = 1.0 / (double)Nout;
+    const double LN = L * invN;  // arc length per output step
+    const bool table = Nout <= kEvalCap;
+    if (table)
+        for (int k = lane; k < Nout; k += 32) cnt[pidx(k)] = 0;
+    __syncwarp();
+    // kf = ceil(S_l N / L) from an FP32 estimate x (relative error below
+    // 4 * 2^-23, so |x - S_l N / L| < 4e-4 for N_out <= 1024) whenever x is
+    // at least 1e-3 away from an integer; otherwise from the targets themselves
+    // (the bit patterns of nonnegative doubles order like their values):
+    // checks around the estimate, bisection over [0, N_out] if it is off
+    const int eLx = (int)((__double_as_longlong(L) >> 52) & 0x7ff) - 1023;
+    const bool est = eLx > -100 && eLx < 120;
+    const float nl = est ? __fdiv_rn(__int2float_rn(Nout), seed_f32(L)) : 0.0f;
+    auto count_knot = [&](double Sl) {
+        const long long sb = __double_as_longlong(Sl);
+        int e = 0;
+        bool exact = false;
+        if (est && sb > 0 && f32_range(Sl)) {
+            const float x = __fmul_rn(seed_f32(Sl), nl);
+            const float xf = floorf(x);
+            const float fr = __fsub_rn(x, xf);
+            e = min(__float2int_rz(xf), Nout - 1) + 1;
+            exact = fr > 1e-3f && fr < 0.999f;
+            if (!exact) e = min(max(__float2int_ru(x), 0), Nout);
+        }
+        if (!exact) {
+            const bool lo_ok =
+                e == 0 || __double_as_longlong(arc_target(e - 1, pow2, LN, L, Nout)) < sb;
+            const bool hi_ok =
+                e == Nout || __double_as_longlong(arc_target(e, pow2, LN, L, Nout)) >= sb;
+            if (!(lo_ok && hi_ok)) {
+                int lo = 0, hi = Nout;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__double_as_longlong(arc_target(mid, pow2, LN, L, Nout)) >= sb) hi = mid;
+                    else lo = mid + 1;
+                }
+                e = lo;
+            }
+        }
+        if (e < Nout) atomicAdd(cnt + pidx(e), 1);
+    };
+
     // ---- B: forward sweep over the interior ---------------------------------
     // The system is solved for M' = M / (6 L^2) (right-hand sides tau_l -
     // tau_{l-1}); the evaluation uses h^2 M' = h^2 M / (6 L^2).  The first
@@ -424,6 +518,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             const double hn = Dr[i + 1], ihn = rcp_nr(hn);  // i + 1 <= ej < n
             const double2 cvn = chord_vec(p, i + 1, n);
             Ur[i] = S;
+            if (table) count_knot(S);
             S += h;
             const double2 tau = scl2(cv, ih);
             const double2 R = sub2(tau, tprev);
@@ -448,6 +543,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         // interface node e_j (the loop, which runs at least once, leaves h,
         // ih and cv holding chord e_j's values)
         Ur[ej] = S;
+        if (table) count_knot(S);
         const double2 tau = scl2(cv, ih);
         Re = sub2(tau, tprev);
         Ae = hprev;
@@ -472,6 +568,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
             const double hn64 = Dr[i + 1];  // i + 1 <= ej < n
             const double2 cvn = chord_vec(p, i + 1, n);
             Ur[i] = S;
+            if (table) count_knot(S);
             S += h64;
             const dfl h = split_scaled(h64, ks);
             const cdf tau = tau_dfh(cv, h, ks);
@@ -493,6 +590,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         }
         yLd = yp; gLd = gp; kLd = cp;
         Ur[ej] = S;
+        if (table) count_knot(S);
         const dfl Ced = split_scaled(h64, ks);
         const cdf Red = csub(tau_dfh(cv, Ced, ks), tprev);
         // the interface data in FP64 for the reduced system (scaled units)
@@ -582,17 +680,10 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     __syncwarp();
 
     // ---- E: evaluation at t_k = k / N_out ------------------------------------
-    const bool pow2 = (Nout & (Nout - 1)) == 0;
-    const double invN = 1.0 / (double)Nout;
-    const double LN = L * invN;                  // arc length per output step
-    const int per = (Nout + 31) / 32;
-    const int k0 = lane * per;
-    const int k1 = min(k0 + per, Nout);
     double2* raw = F32OUT ? (ws.Z + zbase) : (static_cast<double2*>(zout) + zbase);
     double2 ssum = d2(0, 0);
     const bool unit = (flags & FA_UNIT_LENGTH) != 0;
     double per_len = 0.0;
-    double2 Sfirst = d2(0, 0), Sprev = d2(0, 0);
     // The node sum (for the mean) and the perimeter of the outputs are
     // accumulated in float-float (about 48 significant bits; FP64 is the
     // scarce unit) when every coordinate and the perimeter lie in a range
@@ -603,62 +694,97 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     const int eL = (int)((__double_as_longlong(L) >> 52) & 0x7ff) - 1023;
     const bool dfsum = __reduce_max_sync(0xffffffffu, emax) < 1023u + 60u && eL > -40 && eL < 40;
     dfl sx{0.f, 0.f}, sy{0.f, 0.f}, per_df{0.f, 0.f};
-    if (k0 < k1) {
-        // arc-length target of output k: L t_k with t_k = k / N_out
-        const double s0 = pow2 ? k0 * LN : L * ((double)k0 / (double)Nout);
-        const long long sb0 = __double_as_longlong(s0);
-        // last l with S_l <= L t (S_0 = 0); arc lengths are >= 0, so their bits
-        // order like their values
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__double_as_longlong(U[mid]) <= sb0) lo = mid; else hi = mid - 1;
+    // one output into the mean's sum; one chord |a - b| into the perimeter
+    // (the chord's components in FP64, exact differences of nearby values;
+    // its length and both sums in float-float when dfsum)
+    auto add_node = [&](double2 S) {
+        if (dfsum) {
+            const cdf Sd = split_c(S);
+            sx = df_add(sx, Sd.re);
+            sy = df_add(sy, Sd.im);
+        } else {
+            ssum = add2(ssum, S);
         }
-        int l = lo;
-        for (int k = k0; k < k1; ++k) {
-            // (double)k without an FP64 conversion: k < 2^20 is exact in FP32
-            const double kd = k > 0 ? widen_f32(__int2float_rn(k)) : 0.0;
-            const double st = pow2 ? kd * LN : L * (kd / (double)Nout);
-            const long long sb = __double_as_longlong(st);
-            while (l + 1 < n && __double_as_longlong(U[l + 1]) <= sb) ++l;
-            const int ln = (l + 1 == n) ? 0 : l + 1;
-            const double2 pl = __ldg(p + l), pn = __ldg(p + ln);
-            const double2 cv = d2(pn.x - pl.x, pn.y - pl.y);  // p_{l+1} - p_l
-            const double2 Ml = M[l], Mn = M[ln];
-            const double d = D[l];
-            const double u = st - U[l];  // arc length into the interval
-            const double b = u * rcp_nr(d);  // (t - u_l) / h_l
-            // cubic weights a(a^2 - 1) h6 and b(b^2 - 1) h6 (a = 1 - b, h6 =
-            // h^2 M / 6 / M' = d^2 with M' = M / (6 L^2)) from
-            // w = b(b - 1) h6 = -ab h6 = u (u - d): the second is w(1 + b), the
-            // first w(2 - b) = 3w - w(1 + b)  (4 FP64 instructions instead of 8)
-            const double w = u * (u - d);
-            const double cb = fma(w, b, w);
-            const double ca = fma(w, 3.0, -cb);
-            const double2 S = d2(fma(ca, Ml.x, fma(cb, Mn.x, fma(b, cv.x, pl.x))),
-                                 fma(ca, Ml.y, fma(cb, Mn.y, fma(b, cv.y, pl.y))));
-            raw[k] = S;
-            if (dfsum) {
-                // the chord's components in FP64 (exact differences of nearby
-                // values), its length and both sums in float-float
-                const cdf Sd = split_c(S);
-                sx = df_add(sx, Sd.re);
-                sy = df_add(sy, Sd.im);
+    };
+    auto add_chord = [&](double2 a, double2 b) {
+        if (dfsum) {
+            per_df = df_add(per_df, df_chord(sub2(a, b)));
+        } else {
+            const double dx = a.x - b.x, dy = a.y - b.y;
+            const double q = fma(dx, dx, dy * dy);
+            per_len += __double_as_longlong(q) > 0 ? sqrt_nr(q) : 0.0;
+        }
+    };
+    int k0 = 0, k1 = 0;
+    double2 Sfirst = d2(0, 0), Sprev = d2(0, 0);
+    if (table) {
+        // the interval of every output from the counts taken in B: l_k =
+        // (number of knots S_l <= L t_k) - 1, the last knot at or below the
+        // target (the knots are nondecreasing); then 32 consecutive outputs at
+        // a time are evaluated with independent, nearly coalesced loads
+        // inclusive prefix sums: lane i sums its block of consecutive k, a
+        // warp scan gives the block's offset, the block is rewritten as l_k
+        const int per = (Nout + 31) >> 5;
+        const int q0 = min(lane * per, Nout), q1 = min(q0 + per, Nout);
+        int run = 0;
+        for (int k = q0; k < q1; ++k) run += cnt[pidx(k)];
+        int incl = run;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        int acc = incl - run - 1;
+        for (int k = q0; k < q1; ++k) {
+            acc += cnt[pidx(k)];
+            cnt[pidx(k)] = acc;
+        }
+        __syncwarp();
+        // outputs g + lane; the chord to output k - 1 comes from the lane
+        // below, or for lane 0 from the previous group's last output
+        double2 S = d2(0, 0), Sc = d2(0, 0), S0 = d2(0, 0);
+        for (int g = 0; g < Nout; g += 32) {
+            const int k = g + lane;
+            if (k < Nout) {
+                S = eval_interval(p, U, D, M, cnt[pidx(k)], n, arc_target(k, pow2, LN, L, Nout));
+                raw[k] = S;
+                add_node(S);
+            }
+            const double2 Sb = d2(__shfl_up_sync(0xffffffffu, S.x, 1),
+                                  __shfl_up_sync(0xffffffffu, S.y, 1));
+            if (unit && k < Nout && k > 0) add_chord(S, lane == 0 ? Sc : Sb);
+            Sc = shfl_d2(S, 31, 32);
+            if (g == 0) S0 = S;
+        }
+        if (unit) {  // the closing chord, output N_out - 1 to output 0 (lane 0)
+            const double2 Sl = shfl_d2(S, (Nout - 1) & 31, 32);
+            if (lane == 0) add_chord(S0, Sl);
+        }
+    } else {
+        // each lane a contiguous block of outputs, its first interval by
+        // bisection over the knots, the following ones by stepping
+        const int per = (Nout + 31) / 32;
+        k0 = lane * per;
+        k1 = min(k0 + per, Nout);
+        if (k0 < k1) {
+            const long long sb0 = __double_as_longlong(arc_target(k0, pow2, LN, L, Nout));
+            // last l with S_l <= L t (S_0 = 0)
+            int lo = 0, hi = n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__double_as_longlong(U[mid]) <= sb0) lo = mid; else hi = mid - 1;
+            }
+            int l = lo;
+            for (int k = k0; k < k1; ++k) {
+                const double st = arc_target(k, pow2, LN, L, Nout);
+                const long long sb = __double_as_longlong(st);
+                while (l + 1 < n && __double_as_longlong(U[l + 1]) <= sb) ++l;
+                const double2 S = eval_interval(p, U, D, M, l, n, st);
+                raw[k] = S;
+                add_node(S);
                 if (unit) {
-                    if (k > k0) per_df = df_add(per_df, df_chord(sub2(S, Sprev)));
+                    if (k > k0) add_chord(S, Sprev);
                     else Sfirst = S;
-                    Sprev = S;
-                }
-            } else {
-                ssum = add2(ssum, S);
-                if (unit) {
-                    if (k > k0) {
-                        const double dx = S.x - Sprev.x, dy = S.y - Sprev.y;
-                        const double q = fma(dx, dx, dy * dy);
-                        per_len += __double_as_longlong(q) > 0 ? sqrt_nr(q) : 0.0;
-                    } else {
-                        Sfirst = S;
-                    }
                     Sprev = S;
                 }
             }
@@ -668,7 +794,7 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
         ssum = d2(widen_any(sx.h) + widen_any(sx.l), widen_any(sy.h) + widen_any(sy.l));
         per_len = widen_any(per_df.h) + widen_any(per_df.l);
     }
-    if (unit) {
+    if (!table && unit) {
         // the chord from this lane's last output to the next one: the next
         // lane's first (output k1), or output 0 after the last output
         const double2 Snext = shfl_d2(Sfirst, k1 < Nout ? lane + 1 : 0, 32);
@@ -715,14 +841,16 @@ __global__ void __launch_bounds__(kWarps * 32, FA_RESAMPLE_MIN_BLOCKS)
                     int64_t C, int64_t n_pts, int Nout, int flags, void* __restrict__ zout,
                     int8_t* __restrict__ status, Ws ws, unsigned long long* __restrict__ next)
 {
+    __shared__ int s_cnt[kWarps * kCntStride];  // each warp's output-interval table
     const int lane = threadIdx.x & 31;
+    int* cnt = s_cnt + (threadIdx.x >> 5) * kCntStride;
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) c = atomicAdd(next, 1ull);
         c = __shfl_sync(0xffffffffu, c, 0);
         if (c >= (unsigned long long)C) break;
         resample_curve<F32OUT>((int64_t)c, lane, pts, offsets, n_pts, Nout, flags, zout, status,
-                               ws);
+                               ws, cnt);
         __syncwarp();
     }
 }

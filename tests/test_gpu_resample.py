@@ -27,8 +27,11 @@ def _csr(curves):
     return np.concatenate(curves).astype(np.complex128), offs
 
 
-@pytest.mark.parametrize("N", [256, 1024, 1000, 37])
+@pytest.mark.parametrize("N", [256, 1024, 1000, 37, 7, 2048])
 def test_resample_parity(N):
+    """Output counts up to 1024 take the per-warp interval table (N = 7 and
+    37: one partial group of 32 outputs, or one full and one partial; 1000:
+    not a power of two), larger ones the per-lane search (2048)."""
     pts, offs = synth.raw_curves(N, C=40, n_min=500, n_max=2000)
     z, st = _gpu_resample(pts, offs, N)
     zo, sto = oracle.resample(pts, offs, N)
