@@ -325,7 +325,8 @@ __device__ __forceinline__ double rcp_fast(double x)
 // (2H > n) is left; back substitution then solves rows h, 3h, 5h, .. from
 // their solved neighbours at r +- h, for h = H/2 .. 1.  About 2n row updates in
 // all, against n log2 n for parallel cyclic reduction (~9 k FP64 instructions
-// instead of ~39 k at n = 255; the LM step 13 % faster on the gallery pairs).
+// instead of ~39 k at n = 255; the elastic kernel 13 % faster on the gallery
+// pairs).
 // Every level reads only rows the level does not write: one barrier per level.
 template <int T>
 __device__ void cr3(int n, double* lo, double* di, double* up, double* x, double* y1, double* y2)
