@@ -442,9 +442,10 @@ __device__ __forceinline__ void resample_curve(int64_t curve, int lane,
     if (table)
         for (int k = lane; k < Nout; k += 32) cnt[pidx(k)] = 0;
     __syncwarp();
-    // kf = ceil(S_l N / L) from an FP32 estimate x (relative error below
-    // 4 * 2^-23, so |x - S_l N / L| < 4e-4 for N_out <= 1024) whenever x is
-    // at least 1e-3 away from an integer; otherwise from the targets themselves
+    // kf = ceil(S_l N / L) from an FP32 estimate x (two truncations to 24
+    // bits and two roundings: relative error below 3 * 2^-23, so
+    // |x - S_l N / L| < 4e-4 for N_out <= 1024) whenever x is at least 1e-3
+    // away from an integer; otherwise from the targets themselves
     // (the bit patterns of nonnegative doubles order like their values):
     // checks around the estimate, bisection over [0, N_out] if it is off
     const int eLx = (int)((__double_as_longlong(L) >> 52) & 0x7ff) - 1023;
