@@ -22,8 +22,9 @@
 // decreasing L (longest first keeps the tail short), and the persistent CTAs
 // pop items from it with one atomic counter.  Every step is a plain launch or
 // a memset on the caller's stream, so the sequence can be captured in a CUDA
-// graph.  The CTA size (256, 512 or 1024 threads) is the tunable, chosen by
-// fa_align_pairs_ragged_autotune from timed runs on the caller's batch.
+// graph.  Each bucket's plan (CTA size, pairs per CTA, or a cluster of CTAs
+// per pair) is the tunable, chosen by fa_align_pairs_ragged_autotune from
+// timed runs on the caller's batch.
 #include <cooperative_groups.h>
 
 #include <algorithm>

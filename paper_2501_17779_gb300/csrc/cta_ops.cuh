@@ -15,7 +15,7 @@ namespace fa {
 template <int T, int BMAX>
 __device__ void fft_rt_g(double2* X, int logb, const double2* __restrict__ Wf, int tid)
 {
-    constexpr int MAX4 = BMAX / 4 / T > 0 ? BMAX / 4 / T : 1;  // radix-4 butterflies per thread
+    constexpr int MAX4 = (BMAX / 4 + T - 1) / T;  // radix-4 butterflies per thread (at most)
     const int B = 1 << logb, Q = B >> 2, H = B >> 1;
     double2 v[MAX4][4];  // one register block for both stage kinds
     int ns = 1;

@@ -194,7 +194,7 @@ def test_ragged_plan_rejects_what_does_not_fit():
     with pytest.raises(RuntimeError):
         api.set_ragged_plan(5, 256, 2)    # 128 threads per 32-point pair
     with pytest.raises(RuntimeError):
-        api.set_ragged_plan(8, 384, 1)    # not compiled
+        api.set_ragged_plan(8, 640, 1)    # not compiled
     with pytest.raises(RuntimeError):
         api.set_ragged_plan(13, 512, -4)  # a cluster of 4 needs L = 16384
     with pytest.raises(RuntimeError):
